@@ -1,0 +1,294 @@
+/*
+ * bc.h -- C ABI of libbcgb300, the GB300 (sm_103a) ghost-fill library.
+ *
+ * The library applies every boundary condition of a block-structured grid as
+ * one affine sparse operator (arxiv 2605.14780, Sec. III-B):
+ *
+ *     y_G = A x_D + b
+ *
+ * where x_D is the data region of all blocks, y_G their ghost region, and A
+ * has columns in the data region only.  The operator is described by a list
+ * of basic sub-matrices (Sec. IV-A, Table II), each covering a box of ghost
+ * cells of one block (its is_valid region) with one row pattern (its
+ * iterator): zero padding, tabulated constants (pure-function boundary),
+ * index maps (halo copies, circular and symmetric maps, rotated maps of
+ * Alg. 1), interpolation rows (user Itp, or cubed-sphere panel edges
+ * generated on the GPU) and user CSR rows (Table III: F_NNZ/F_COL/F_DATA).
+ *
+ * Memory model
+ *   * Fields are caller-owned device memory.  Each (block, component) pair is
+ *     a "slot"; slot s = slot_base(block) + comp, slot_base being the prefix
+ *     sum of ncomp over the blocks in order.  The slot pointer addresses the
+ *     element (i, j, k) = (-h0, -h1, -h2) of level 0; element (i, j, k, level)
+ *     lives at  ptr + (i+h0)*stride[0] + (j+h1)*stride[1] + (k+h2)*stride[2]
+ *                    + level*level_stride.
+ *   * The apply entry points take a DEVICE array of slot pointers (like the
+ *     pointer arrays of batched BLAS calls).  It is read by the kernels at
+ *     run time, so it may be rewritten between calls, and a CUDA graph
+ *     captured around an apply keeps working when the array is updated in
+ *     stream order.
+ *   * A plan owns its device tables; every host array passed to
+ *     bc_plan_create is copied and may be freed afterwards.
+ *   * bc_apply, bc_apply_form and bc_apply_adjoint allocate nothing, never
+ *     synchronise the host, and only enqueue kernels on the given stream.
+ *
+ * Errors
+ *   Every entry point returns a bc_status.  The message of the last error of
+ *   the calling thread is returned by bc_last_error().  Invalid descriptions
+ *   are rejected by bc_plan_create before any device work.  Launch errors are
+ *   returned at once; faults inside a kernel surface at the next
+ *   synchronisation of the stream.
+ */
+#ifndef BC_GB300_H
+#define BC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bc_status {
+  BC_OK = 0,
+  BC_ERR_INVALID_ARG = 1,     /* malformed description or argument          */
+  BC_ERR_OVERLAP = 2,         /* two sub-matrices cover one ghost value      */
+  BC_ERR_COLUMN_NOT_DATA = 3, /* a column is not a data cell (Sec. III-B)    */
+  BC_ERR_UNCOVERED = 4,       /* strict cover: a ghost value has no row      */
+  BC_ERR_HALO_TOO_WIDE = 5,   /* a map's ghost depth exceeds the data extent */
+  BC_ERR_OUT_OF_RANGE = 6,    /* a row is not a ghost cell of its block      */
+  BC_ERR_NOMEM = 7,           /* a host or device allocation failed          */
+  BC_ERR_CUDA = 8,            /* a CUDA runtime call failed                  */
+  BC_ERR_UNSUPPORTED = 9,     /* valid, but outside what this build handles  */
+  BC_ERR_TIMEOUT = 10,        /* reserved: a bounded device wait gave up     */
+  BC_ERR_GEOMETRY = 11        /* cubed-sphere geometry check failed          */
+} bc_status;
+
+typedef enum bc_dtype { BC_F32 = 0, BC_F64 = 1 } bc_dtype;
+
+/* Kinds of basic sub-matrix (Sec. III-B, Table III). */
+typedef enum bc_kind {
+  BC_ZERO = 0,   /* A_ij = 0, b_i = 0                                      */
+  BC_CONST = 1,  /* A_ij = 0, b_i = values[i]  (pure-function boundary)    */
+  BC_MAP = 2,    /* one unit entry at an affine image of the ghost index   */
+  BC_INTERP = 3, /* p-point row along an axis of a source block            */
+  BC_CSR = 4     /* user CSR rows                                           */
+} bc_kind;
+
+typedef enum bc_geometry {
+  BC_GEOM_USER = 0,        /* interpolation tables given by the caller     */
+  BC_GEOM_CUBED_SPHERE = 1 /* generated on the GPU for gnomonic panels     */
+} bc_geometry;
+
+/* Execution forms of the forward apply. */
+typedef enum bc_form {
+  BC_FORM_BATCHED = 0,  /* all work items in one launch (the default)      */
+  BC_FORM_TYPEWIDE = 1, /* one launch per sub-matrix kind                  */
+  BC_FORM_PER_BC = 2    /* one launch per basic sub-matrix                 */
+} bc_form;
+
+/* One block of the grid.  2-D blocks use n[2] = 1, h[2] = 0. */
+typedef struct bc_block {
+  int32_t n[3];         /* data extents per axis, axis 0 fastest          */
+  int32_t h[3];         /* ghost width per axis (same on both sides)      */
+  int32_t nlevels;      /* vertical levels; every row repeats per level   */
+  int32_t ncomp;        /* components, each a slot of its own (<= 32)     */
+  int64_t stride[3];    /* element strides of the three axes (> 0)        */
+  int64_t level_stride; /* element stride between levels (> 0 if L > 1)  */
+} bc_block;
+
+typedef struct bc_grid {
+  int32_t dtype;          /* bc_dtype of every field                      */
+  int32_t nblocks;
+  const bc_block* blocks; /* host array [nblocks]                          */
+} bc_grid;
+
+/*
+ * One basic sub-matrix: the rows of the ghost cells in the box [lo, hi) of
+ * `block` (cell coordinates of the data region; ghosts are negative or
+ * >= n), for the listed components.  Unused fields are ignored; set them to
+ * zero.  All pointers are host pointers and are copied.
+ *
+ * BC_ZERO   -- no further fields.
+ * BC_CONST  -- values[ncomps * volume]: component-major, then the box cells
+ *              with axis 0 fastest; rounded to the plan's dtype.
+ * BC_MAP    -- the ghost g of component c reads component c of src_block at
+ *              src[d] = sign[d] * g[perm[d]] + offset[d]  (perm a permutation
+ *              of 0..2, sign +-1): halo copy, circular and symmetric maps
+ *              (Sec. III-B fmap), and the rotated map of Alg. 1.
+ * BC_INTERP -- row of cell q reads p consecutive data cells of one source
+ *              block along one axis, y = sum_k w[q][k] x[node_k].
+ *              geometry = BC_GEOM_USER: itp_src_block[vol], itp_start[vol*3]
+ *              (data cell of node 0), itp_axis[vol] (axis the nodes step
+ *              along, +1 each) and itp_w[vol*p] give each row.
+ *              geometry = BC_GEOM_CUBED_SPHERE: `block` is one of the six
+ *              panels cs_panels[0..5] (equal n, h, levels), every box cell
+ *              must be an edge ghost (exactly one index out of range), and
+ *              the GPU computes the neighbour panel, depth row, stencil and
+ *              Lagrange weights in FP64 at plan creation.
+ *              rot_comp = {cu, cv} (or {-1, -1}) names two listed components
+ *              that form a covariant vector: for them the interpolated pair
+ *              is multiplied by the 2x2 matrix M (user: itp_rot[vol*4],
+ *              row-major; cubed sphere: generated) -- interpolate, then
+ *              rotate.  All other listed components use the plain row.
+ * BC_CSR    -- row r = (listed comp r / volume, box cell r % volume) has the
+ *              entries row_ptr[r] .. row_ptr[r+1]-1 with columns
+ *              (col_block, col_comp, col_ijk[3]) and values val; rhs[r] (or
+ *              NULL for zero) is added.  Rows repeat per level and read the
+ *              same level of their column blocks.
+ */
+typedef struct bc_submatrix {
+  int32_t kind;
+  int32_t block;
+  int32_t lo[3];
+  int32_t hi[3];
+  int32_t ncomps;
+  const int32_t* comps;
+  /* BC_CONST */
+  const double* values;
+  /* BC_MAP */
+  int32_t src_block;
+  int32_t perm[3];
+  int32_t sign[3];
+  int32_t offset[3];
+  /* BC_INTERP */
+  int32_t p;
+  int32_t geometry;
+  int32_t rot_comp[2];
+  int32_t cs_panels[6];
+  const int32_t* itp_src_block;
+  const int32_t* itp_start;
+  const int32_t* itp_axis;
+  const double* itp_w;
+  const double* itp_rot;
+  /* BC_CSR */
+  const int64_t* row_ptr;
+  const int32_t* col_block;
+  const int32_t* col_comp;
+  const int32_t* col_ijk;
+  const double* val;
+  const double* rhs;
+} bc_submatrix;
+
+/* Plan options; a zero-filled struct (or NULL) selects the defaults. */
+typedef struct bc_plan_opts {
+  int32_t cells_per_item;  /* cells of one work item (default 256)          */
+  int32_t levels_per_item; /* levels of one work item (default 16)          */
+  int32_t threads;         /* threads per CTA (default 256)                 */
+  int32_t ctas_per_sm;     /* persistent CTAs per SM; 0 = one CTA per item  */
+  int32_t strict_cover;    /* 1: every ghost value must be covered          */
+  int32_t no_adjoint;      /* 1: skip the transpose tables                  */
+  int32_t reserved[2];
+} bc_plan_opts;
+
+typedef struct bc_plan bc_plan;
+
+/* Plan statistics (byte counts use the plan's element size S). */
+typedef struct bc_stats {
+  int64_t ghost_values;       /* rows of A over all levels                  */
+  int64_t ghost_values_kind[5];
+  int64_t nitems;             /* forward work items                         */
+  int64_t nitems_adjoint;     /* adjoint gather items                       */
+  int64_t nsubmatrices;
+  int64_t nslots;
+  int64_t bytes_fwd;          /* algorithmic bytes of one forward apply     */
+  int64_t bytes_adj;          /* algorithmic bytes of one adjoint apply     */
+  int64_t table_bytes;        /* device table bytes                         */
+  int64_t transpose_nnz;      /* entries of the stored A^T (one level)      */
+  int32_t element_size;
+  int32_t form_threads;
+  int32_t form_ctas_per_sm;
+  int32_t cells_per_item;
+  int32_t levels_per_item;
+  int32_t reserved[3];
+} bc_stats;
+
+/*
+ * Build a plan from the grid and nsubs basic sub-matrices.  Checks the
+ * description (boxes inside the ghost region, disjoint coverage, data-only
+ * columns, fmap depth, finite weights), runs the FP64 cubed-sphere geometry
+ * kernel when needed, builds the work list and the transpose of A, and
+ * uploads everything to the current device.  Synchronous.  On error *out is
+ * NULL and nothing is leaked.
+ */
+bc_status bc_plan_create(const bc_grid* grid, const bc_submatrix* subs,
+                         int32_t nsubs, const bc_plan_opts* opts,
+                         bc_plan** out);
+
+/* Number of slots (sum of ncomp) the slot-pointer arrays must hold. */
+int32_t bc_plan_nslots(const bc_plan* plan);
+
+/*
+ * Forward apply in place: every covered ghost value of every slot becomes
+ * (A x_D + b)_i.  slot_ptrs is a DEVICE array of nslots device pointers.
+ * stream is a cudaStream_t (NULL = legacy default stream).  Copies, zero
+ * rows and constants are written bit-exactly.  Equivalent to
+ * bc_apply_form(plan, slot_ptrs, BC_FORM_BATCHED, stream).
+ */
+bc_status bc_apply(bc_plan* plan, void* const* slot_ptrs, void* stream);
+
+/* Forward apply in one of the bc_form execution forms (same result bits). */
+bc_status bc_apply_form(bc_plan* plan, void* const* slot_ptrs, int32_t form,
+                        void* stream);
+
+/*
+ * Adjoint of the in-place forward apply, in place on the cotangent fields
+ * given by slot_ptrs (device array): x_D_bar = y_D_bar + A^T y_G_bar, then
+ * every covered ghost value is set to 0; uncovered ghosts are left as they
+ * are.  Deterministic: each data value sums its entries in ascending order
+ * of (ghost slot, ghost offset), without atomics.  Two launches (gather,
+ * then zero).  Fails with BC_ERR_UNSUPPORTED if the plan was built with
+ * no_adjoint.
+ */
+bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs,
+                           void* stream);
+
+/*
+ * End-to-end apply on host fields: for every slot, copy host_ptrs[s] (host
+ * memory, pinned for asynchronous copies) to dev_ptrs[s] (device memory;
+ * host array of device pointers), apply (slot_ptrs: the same device
+ * pointers as a device array), and copy every slot back to the host.
+ * Adjacent slots whose host and device spans are both contiguous are copied
+ * together.  Asynchronous on `stream`; the caller synchronises.
+ */
+bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs,
+                        void* const* dev_ptrs, void* const* slot_ptrs,
+                        void* stream);
+
+/*
+ * Time the candidate work-item shapes and launch forms on the caller's
+ * fields (slot_ptrs, device array) and keep the fastest for BC_FORM_BATCHED.
+ * Overwrites the covered ghosts (with the operator's own result).  Allocates
+ * a temporary L2-flush buffer; synchronises the stream.
+ */
+bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs,
+                           void* stream);
+
+/* Fill *out with the plan's counters. */
+bc_status bc_plan_stats(const bc_plan* plan, bc_stats* out);
+
+/*
+ * Export the rows of A and b at level 0 as CSR over (slot, element offset
+ * from the slot pointer).  Call first with NULL arrays to get *nrows and
+ * *nnz, then with arrays of those sizes.  Rows are sorted by (slot, offset)
+ * and the entries of a row are in the order the forward kernels sum them.
+ * Values are the plan's FP64 copies (before rounding to the plan's dtype).
+ */
+bc_status bc_plan_export_csr(const bc_plan* plan, int64_t* nrows,
+                             int64_t* nnz, int32_t* row_slot,
+                             int64_t* row_off, int64_t* row_ptr,
+                             int32_t* col_slot, int64_t* col_off,
+                             double* val, double* rhs);
+
+/* Release the plan and its device tables (NULL is a no-op). */
+void bc_plan_destroy(bc_plan* plan);
+
+const char* bc_status_string(bc_status status);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* bc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BC_GB300_H */

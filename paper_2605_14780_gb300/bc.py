@@ -1,0 +1,356 @@
+"""ctypes binding of the ``libbcgb300`` C ABI (``include/bc.h``).
+
+Argument marshalling only: plans, the forward apply ``y_G = A x_D + b``
+(arxiv 2605.14780, Sec. III-B) and its adjoint all run in the library's
+sm_103a kernels.  PyTorch supplies device memory and streams.  There is no
+fallback: if the compiled library is missing, :func:`load_library` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+LIB_NAME = "libbcgb300.so"
+LIB_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib")
+
+BC_F32, BC_F64 = 0, 1
+BC_FORM_BATCHED, BC_FORM_TYPEWIDE, BC_FORM_PER_BC = 0, 1, 2
+STATUS = {0: "BC_OK", 1: "BC_ERR_INVALID_ARG", 2: "BC_ERR_OVERLAP",
+          3: "BC_ERR_COLUMN_NOT_DATA", 4: "BC_ERR_UNCOVERED",
+          5: "BC_ERR_HALO_TOO_WIDE", 6: "BC_ERR_OUT_OF_RANGE",
+          7: "BC_ERR_NOMEM", 8: "BC_ERR_CUDA", 9: "BC_ERR_UNSUPPORTED",
+          10: "BC_ERR_TIMEOUT", 11: "BC_ERR_GEOMETRY"}
+
+c_i32, c_i64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+P_i32 = ctypes.POINTER(c_i32)
+P_i64 = ctypes.POINTER(c_i64)
+P_dbl = ctypes.POINTER(c_dbl)
+
+
+class BcBlock(ctypes.Structure):
+    _fields_ = [("n", c_i32 * 3), ("h", c_i32 * 3), ("nlevels", c_i32),
+                ("ncomp", c_i32), ("stride", c_i64 * 3), ("level_stride", c_i64)]
+
+
+class BcGrid(ctypes.Structure):
+    _fields_ = [("dtype", c_i32), ("nblocks", c_i32),
+                ("blocks", ctypes.POINTER(BcBlock))]
+
+
+class BcSubmatrix(ctypes.Structure):
+    _fields_ = [("kind", c_i32), ("block", c_i32), ("lo", c_i32 * 3),
+                ("hi", c_i32 * 3), ("ncomps", c_i32), ("comps", P_i32),
+                ("values", P_dbl),
+                ("src_block", c_i32), ("perm", c_i32 * 3), ("sign", c_i32 * 3),
+                ("offset", c_i32 * 3),
+                ("p", c_i32), ("geometry", c_i32), ("rot_comp", c_i32 * 2),
+                ("cs_panels", c_i32 * 6),
+                ("itp_src_block", P_i32), ("itp_start", P_i32),
+                ("itp_axis", P_i32), ("itp_w", P_dbl), ("itp_rot", P_dbl),
+                ("row_ptr", P_i64), ("col_block", P_i32), ("col_comp", P_i32),
+                ("col_ijk", P_i32), ("val", P_dbl), ("rhs", P_dbl)]
+
+
+class BcPlanOpts(ctypes.Structure):
+    _fields_ = [("cells_per_item", c_i32), ("levels_per_item", c_i32),
+                ("threads", c_i32), ("ctas_per_sm", c_i32),
+                ("strict_cover", c_i32), ("no_adjoint", c_i32),
+                ("reserved", c_i32 * 2)]
+
+
+class BcStats(ctypes.Structure):
+    _fields_ = [("ghost_values", c_i64), ("ghost_values_kind", c_i64 * 5),
+                ("nitems", c_i64), ("nitems_adjoint", c_i64),
+                ("nsubmatrices", c_i64), ("nslots", c_i64),
+                ("bytes_fwd", c_i64), ("bytes_adj", c_i64),
+                ("table_bytes", c_i64), ("transpose_nnz", c_i64),
+                ("element_size", c_i32), ("form_threads", c_i32),
+                ("form_ctas_per_sm", c_i32), ("cells_per_item", c_i32),
+                ("levels_per_item", c_i32), ("reserved", c_i32 * 3)]
+
+
+#: every function the header declares, with (restype, argtypes)
+SIGNATURES = {
+    "bc_plan_create": (c_i32, [ctypes.POINTER(BcGrid), ctypes.POINTER(BcSubmatrix),
+                               c_i32, ctypes.POINTER(BcPlanOpts),
+                               ctypes.POINTER(c_vp)]),
+    "bc_plan_nslots": (c_i32, [c_vp]),
+    "bc_apply": (c_i32, [c_vp, c_vp, c_vp]),
+    "bc_apply_form": (c_i32, [c_vp, c_vp, c_i32, c_vp]),
+    "bc_apply_adjoint": (c_i32, [c_vp, c_vp, c_vp]),
+    "bc_apply_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "bc_plan_autotune": (c_i32, [c_vp, c_vp, c_vp]),
+    "bc_plan_stats": (c_i32, [c_vp, ctypes.POINTER(BcStats)]),
+    "bc_plan_export_csr": (c_i32, [c_vp, P_i64, P_i64, P_i32, P_i64, P_i64,
+                                   P_i32, P_i64, P_dbl, P_dbl]),
+    "bc_plan_destroy": (None, [c_vp]),
+    "bc_status_string": (ctypes.c_char_p, [c_i32]),
+    "bc_last_error": (ctypes.c_char_p, []),
+}
+
+_LIB = None
+
+
+def library_path():
+    return os.path.join(LIB_DIR, LIB_NAME)
+
+
+def load_library():
+    """Load the compiled library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{LIB_NAME} is not built ({path} missing); run "
+            "paper_2605_14780_gb300.build.build_library() first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class BCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = STATUS.get(status, str(status))
+
+
+def _check(st):
+    if st != 0:
+        lib = load_library()
+        raise BCError(st, lib.bc_last_error().decode())
+
+
+def _ptr(arr, ctype):
+    return arr.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+class Plan:
+    """A compiled ghost-fill operator.
+
+    ``blocks``: list of dicts ``n, h, nlevels, ncomp, stride, level_stride``
+    (element strides); ``subs``: list of sub-matrix dicts as produced by
+    :mod:`paper_2605_14780_gb300.specs`; ``dtype``: ``"f32"`` or ``"f64"``.
+    """
+
+    def __init__(self, blocks, subs, dtype, opts=None):
+        lib = load_library()
+        self._lib = lib
+        self.dtype = dtype
+        self.blocks = blocks
+        keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(np.asarray(a, dt))
+            keep.append(a)
+            return a
+
+        cb = (BcBlock * max(1, len(blocks)))()
+        for k, b in enumerate(blocks):
+            cb[k].n[:] = list(b["n"])
+            cb[k].h[:] = list(b["h"])
+            cb[k].nlevels = b["nlevels"]
+            cb[k].ncomp = b["ncomp"]
+            cb[k].stride[:] = list(b["stride"])
+            cb[k].level_stride = b["level_stride"]
+        grid = BcGrid(BC_F64 if dtype == "f64" else BC_F32, len(blocks), cb)
+        cs = (BcSubmatrix * max(1, len(subs)))()
+        for k, s in enumerate(subs):
+            m = cs[k]
+            m.kind = s["kind"]
+            m.block = s["block"]
+            m.lo[:] = list(s["lo"])
+            m.hi[:] = list(s["hi"])
+            comps = arr(s["comps"], np.int32)
+            m.ncomps = len(comps)
+            m.comps = _ptr(comps, c_i32)
+            if s.get("values") is not None:
+                m.values = _ptr(arr(s["values"], np.float64), c_dbl)
+            m.src_block = s.get("src_block", 0)
+            m.perm[:] = list(s.get("perm", (0, 1, 2)))
+            m.sign[:] = list(s.get("sign", (1, 1, 1)))
+            m.offset[:] = list(s.get("offset", (0, 0, 0)))
+            m.p = s.get("p", 0)
+            m.geometry = s.get("geometry", 0)
+            m.rot_comp[:] = list(s.get("rot_comp", (-1, -1)))
+            m.cs_panels[:] = list(s.get("cs_panels", (0, 0, 0, 0, 0, 0)))
+            for key, dt, ct in (("itp_src_block", np.int32, c_i32),
+                                ("itp_start", np.int32, c_i32),
+                                ("itp_axis", np.int32, c_i32),
+                                ("itp_w", np.float64, c_dbl),
+                                ("itp_rot", np.float64, c_dbl),
+                                ("row_ptr", np.int64, c_i64),
+                                ("col_block", np.int32, c_i32),
+                                ("col_comp", np.int32, c_i32),
+                                ("col_ijk", np.int32, c_i32),
+                                ("val", np.float64, c_dbl),
+                                ("rhs", np.float64, c_dbl)):
+                if s.get(key) is not None:
+                    setattr(m, key, _ptr(arr(s[key], dt), ct))
+        o = BcPlanOpts()
+        for key, v in (opts or {}).items():
+            setattr(o, key, v)
+        handle = c_vp()
+        st = lib.bc_plan_create(ctypes.byref(grid), cs, len(subs),
+                                ctypes.byref(o), ctypes.byref(handle))
+        _check(st)
+        self._h = handle
+        self.nslots = lib.bc_plan_nslots(handle)
+
+    # -- lifecycle -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- queries -----------------------------------------------------------
+    def stats(self):
+        s = BcStats()
+        _check(self._lib.bc_plan_stats(self._h, ctypes.byref(s)))
+        out = {}
+        for name, _ in BcStats._fields_:
+            v = getattr(s, name)
+            out[name] = list(v) if hasattr(v, "__len__") else int(v)
+        return out
+
+    def export_csr(self):
+        nr, nz = c_i64(), c_i64()
+        nul = lambda t: ctypes.POINTER(t)()  # noqa: E731
+        _check(self._lib.bc_plan_export_csr(
+            self._h, ctypes.byref(nr), ctypes.byref(nz), nul(c_i32), nul(c_i64),
+            nul(c_i64), nul(c_i32), nul(c_i64), nul(c_dbl), nul(c_dbl)))
+        R, E = nr.value, nz.value
+        rs = np.zeros(R, np.int32)
+        ro = np.zeros(R, np.int64)
+        rp = np.zeros(R + 1, np.int64)
+        cs = np.zeros(max(E, 1), np.int32)
+        co = np.zeros(max(E, 1), np.int64)
+        va = np.zeros(max(E, 1), np.float64)
+        rh = np.zeros(max(R, 1), np.float64)
+        _check(self._lib.bc_plan_export_csr(
+            self._h, ctypes.byref(nr), ctypes.byref(nz), _ptr(rs, c_i32),
+            _ptr(ro, c_i64), _ptr(rp, c_i64), _ptr(cs, c_i32), _ptr(co, c_i64),
+            _ptr(va, c_dbl), _ptr(rh, c_dbl)))
+        return {"row_slot": rs, "row_off": ro, "row_ptr": rp,
+                "col_slot": cs[:E], "col_off": co[:E], "val": va[:E],
+                "rhs": rh[:R]}
+
+    # -- execution -----------------------------------------------------------
+    def apply(self, slot_table, form=BC_FORM_BATCHED, stream=None):
+        """Forward apply; ``slot_table`` is a device int64 tensor of slot
+        pointers (see :func:`slot_table`)."""
+        _check(self._lib.bc_apply_form(self._h, c_vp(slot_table.data_ptr()),
+                                       int(form), _stream_handle(stream)))
+
+    def adjoint(self, slot_table, stream=None):
+        _check(self._lib.bc_apply_adjoint(self._h, c_vp(slot_table.data_ptr()),
+                                          _stream_handle(stream)))
+
+    def apply_host(self, host_ptrs, dev_ptrs, slot_table, stream=None):
+        H = (c_vp * len(host_ptrs))(*host_ptrs)
+        D = (c_vp * len(dev_ptrs))(*dev_ptrs)
+        _check(self._lib.bc_apply_host(self._h, H, D, c_vp(slot_table.data_ptr()),
+                                       _stream_handle(stream)))
+
+    def autotune(self, slot_table, stream=None):
+        _check(self._lib.bc_plan_autotune(self._h, c_vp(slot_table.data_ptr()),
+                                          _stream_handle(stream)))
+
+
+def slot_pointers(tensors):
+    """Slot pointers of per-block tensors shaped ``(C, L, F2, F1, F0)``: one
+    per (block, component), addressing the component's first element."""
+    ptrs = []
+    for t in tensors:
+        for c in range(t.shape[0]):
+            ptrs.append(t[c].data_ptr())
+    return ptrs
+
+
+def slot_table(tensors, device=None):
+    """Device int64 tensor of :func:`slot_pointers`."""
+    import torch
+    ptrs = slot_pointers(tensors)
+    dev = device or tensors[0].device
+    return torch.tensor(ptrs, dtype=torch.int64, device=dev)
+
+
+def block_descriptors(tensors, blocks):
+    """C-ABI block descriptors with the strides of the given tensors."""
+    out = []
+    for t, b in zip(tensors, blocks):
+        out.append({"n": tuple(b["n"]), "h": tuple(b["h"]),
+                    "nlevels": b["nlevels"], "ncomp": b["ncomp"],
+                    "stride": (t.stride(4), t.stride(3), t.stride(2)),
+                    "level_stride": t.stride(1)})
+    return out
+
+
+def plan_for_workload(w, tensors=None, opts=None):
+    """Plan of a :mod:`synth` workload (strides of ``tensors`` if given,
+    contiguous ``(C, L, F2, F1, F0)`` otherwise)."""
+    from . import specs
+    if tensors is not None:
+        blocks = block_descriptors(tensors, w["blocks"])
+    else:
+        blocks = [specs.contiguous_block(b) for b in w["blocks"]]
+    return Plan(blocks, specs.submatrices(w), w["dtype"], opts)
+
+
+class BCFill:
+    """``torch.autograd.Function`` of the in-place ghost fill of one plan.
+
+    Forward: ghosts <- A x_D + b in place (the inputs are marked dirty).
+    Backward: x_D_bar = y_D_bar + A^T y_G_bar and x_G_bar = 0 on covered
+    ghosts, computed in place on a copy of the incoming cotangents.
+    """
+
+    _fn = None
+
+    @classmethod
+    def function(cls):
+        if cls._fn is None:
+            import torch
+
+            class _Fill(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, plan, *fields):
+                    table = slot_table(fields)
+                    plan.apply(table)
+                    ctx.plan = plan
+                    ctx.mark_dirty(*fields)
+                    return fields
+
+                @staticmethod
+                def backward(ctx, *grads):
+                    gs = [g.contiguous().clone() for g in grads]
+                    table = slot_table(gs)
+                    ctx.plan.adjoint(table)
+                    return (None, *gs)
+
+            cls._fn = _Fill
+        return cls._fn
+
+    @classmethod
+    def apply(cls, plan, *fields):
+        return cls.function().apply(plan, *fields)

@@ -1,0 +1,64 @@
+"""Build ``libbcgb300.so`` in-tree with nvcc for sm_103a.
+
+Three translation units compiled in parallel, then linked with the static
+CUDA runtime into ``paper_2605_14780_gb300/_lib/libbcgb300.so``.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+OUT_DIR = os.path.join(HERE, "_lib")
+SOURCES = ["plan.cpp", "kernels.cu", "geometry.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+         "-I", os.path.join(ROOT, "include")]
+
+
+def nvcc():
+    exe = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(exe):
+        raise RuntimeError("nvcc not found")
+    return exe
+
+
+def _compile(src, obj, extra):
+    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+    return r.stderr
+
+
+def build_library(force=False, extra_flags=()):
+    """Compile and link the library; returns its path."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    lib = os.path.join(OUT_DIR, "libbcgb300.so")
+    srcs = [os.path.join(CSRC, s) for s in SOURCES] + [
+        os.path.join(CSRC, "bc_internal.h"), os.path.join(ROOT, "include", "bc.h")]
+    if not force and os.path.exists(lib):
+        newest = max(os.path.getmtime(s) for s in srcs)
+        if os.path.getmtime(lib) >= newest and not extra_flags:
+            return lib
+    objs = [os.path.join(OUT_DIR, s.replace(".", "_") + ".o") for s in SOURCES]
+    with ThreadPoolExecutor(len(SOURCES)) as ex:
+        list(ex.map(lambda a: _compile(a[0], a[1], list(extra_flags)),
+                    zip(SOURCES, objs)))
+    cmd = [nvcc(), *ARCH, "-shared", "-o", lib + ".tmp", *objs,
+           "-cudart", "static"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(lib + ".tmp", lib)
+    for o in objs:
+        os.remove(o)
+    return lib
+
+
+if __name__ == "__main__":
+    print(build_library(force=True))

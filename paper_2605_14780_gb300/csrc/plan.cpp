@@ -1,0 +1,1303 @@
+// Host side of libbcgb300: validation of the basic sub-matrices, the work
+// list, the transpose of A, device tables and the C ABI of include/bc.h.
+//
+// A plan turns the user's basic sub-matrices (arxiv 2605.14780, Sec. IV-A,
+// Table II) into
+//   * explicit level-0 rows of A and b (FP64), kept on the host for the
+//     transpose and for bc_plan_export_csr;
+//   * kind-specific device tables (constants, interpolation stencils and
+//     rotations, CSR rows) in the plan's dtype;
+//   * a work list of rectangular cell runs x level ranges (the disjoint
+//     convex pieces of Sec. IV-C), executed by the kernels of kernels.cu;
+//   * the transpose of A (rows = data values read by some ghost, entries in
+//     ascending ghost order) and its own work list, for the adjoint.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bc.h"
+#include "bc_internal.h"
+
+using namespace bcg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+bc_status fail(bc_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+bc_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? BC_ERR_NOMEM : BC_ERR_CUDA,
+              "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct Sub {
+  int kind = 0, block = 0;
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, W[3] = {0, 0, 0};
+  int vol = 0;
+  std::vector<int> comps;
+  int src_block = -1;
+  int perm[3] = {0, 1, 2}, sign[3] = {1, 1, 1}, offset[3] = {0, 0, 0};
+  int p = 0, geometry = 0, rot_u = -1, rot_v = -1;
+  int table = 0;  // CONST/CSR: first row of comp 0; INTERP: first cell row
+};
+
+struct ExplicitRows {
+  std::vector<int32_t> slot;
+  std::vector<int64_t> off;
+  std::vector<int64_t> ptr{0};
+  std::vector<int32_t> cslot;
+  std::vector<int64_t> coff;
+  std::vector<double> val;
+  std::vector<double> rhs;
+  void begin_row(int32_t s, int64_t o, double b) {
+    slot.push_back(s);
+    off.push_back(o);
+    rhs.push_back(b);
+  }
+  void entry(int32_t s, int64_t o, double v) {
+    cslot.push_back(s);
+    coff.push_back(o);
+    val.push_back(v);
+  }
+  void end_row() { ptr.push_back((int64_t)val.size()); }
+};
+
+struct DevBuf {
+  void* base = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() {
+    if (base) cudaFree(base);
+  }
+};
+
+}  // namespace
+
+struct bc_plan {
+  int dtype = 0, esize = 4;
+  std::vector<bc_block> blocks;
+  std::vector<int32_t> slot_base, slot_block;
+  std::vector<int64_t> slot_ls;
+  int nslots = 0;
+  std::vector<Sub> subs;
+  ExplicitRows rows;  // level 0, in sub-matrix order
+  // host tables (FP64 copies)
+  std::vector<int4> itp_idx;
+  std::vector<double> itp_w, itp_m;
+  std::vector<int64_t> csr_ptr{0};
+  std::vector<int32_t> csr_slot, csr_off;
+  std::vector<double> csr_val, csr_rhs;
+  std::vector<double> const_val;
+  // transpose
+  std::vector<int32_t> arow_slot, arow_off;
+  std::vector<int64_t> adj_ptr{0};
+  std::vector<int32_t> aent_slot, aent_off;
+  std::vector<double> aent_w;
+  bool has_adjoint = false;
+  // work lists
+  std::vector<Item> items, adj_items, adj_zero;
+  std::vector<int> sub_begin, sub_end;
+  int type_begin[5] = {0, 0, 0, 0, 0}, type_end[5] = {0, 0, 0, 0, 0};
+  // device
+  DevBuf tables, work;
+  Ctx ctx{};
+  Item* d_items = nullptr;
+  Item* d_adj = nullptr;
+  Item* d_adj_zero = nullptr;
+  unsigned* d_counter = nullptr;
+  int num_sms = 1;
+  bc_plan_opts opts{};
+  bc_stats stats{};
+};
+
+namespace {
+
+int64_t cell_offset(const bc_block& b, int i, int j, int k) {
+  return (int64_t)(i + b.h[0]) * b.stride[0] + (int64_t)(j + b.h[1]) * b.stride[1] +
+         (int64_t)(k + b.h[2]) * b.stride[2];
+}
+
+bool in_data(const bc_block& b, int i, int j, int k) {
+  return i >= 0 && i < b.n[0] && j >= 0 && j < b.n[1] && k >= 0 && k < b.n[2];
+}
+
+bc_status validate_grid(const bc_grid* g, bc_plan* P) {
+  if (!g) return fail(BC_ERR_INVALID_ARG, "grid is NULL");
+  if (g->dtype != BC_F32 && g->dtype != BC_F64)
+    return fail(BC_ERR_INVALID_ARG, "unknown dtype %d", g->dtype);
+  if (g->nblocks <= 0 || !g->blocks)
+    return fail(BC_ERR_INVALID_ARG, "grid has no blocks");
+  P->dtype = g->dtype;
+  P->esize = g->dtype == BC_F64 ? 8 : 4;
+  P->blocks.assign(g->blocks, g->blocks + g->nblocks);
+  int64_t slots = 0;
+  for (int b = 0; b < g->nblocks; ++b) {
+    const bc_block& B = P->blocks[b];
+    for (int d = 0; d < 3; ++d) {
+      if (B.n[d] < 1) return fail(BC_ERR_INVALID_ARG, "block %d: n[%d] < 1", b, d);
+      if (B.h[d] < 0) return fail(BC_ERR_INVALID_ARG, "block %d: h[%d] < 0", b, d);
+      if (B.stride[d] < 1)
+        return fail(BC_ERR_INVALID_ARG, "block %d: stride[%d] < 1", b, d);
+    }
+    if (B.nlevels < 1 || B.ncomp < 1 || B.ncomp > 32)
+      return fail(BC_ERR_INVALID_ARG, "block %d: bad nlevels/ncomp", b);
+    if (B.nlevels > 1 && B.level_stride < 1)
+      return fail(BC_ERR_INVALID_ARG, "block %d: level_stride < 1", b);
+    const int64_t maxoff = cell_offset(B, B.n[0] + B.h[0] - 1, B.n[1] + B.h[1] - 1,
+                                       B.n[2] + B.h[2] - 1);
+    if (maxoff >= (int64_t(1) << 31))
+      return fail(BC_ERR_UNSUPPORTED,
+                  "block %d: one level of one component spans >= 2^31 elements", b);
+    P->slot_base.push_back((int32_t)slots);
+    for (int c = 0; c < B.ncomp; ++c) {
+      P->slot_block.push_back(b);
+      P->slot_ls.push_back(B.nlevels > 1 ? B.level_stride : 0);
+    }
+    slots += B.ncomp;
+    if (slots > (1 << 24)) return fail(BC_ERR_UNSUPPORTED, "too many slots");
+  }
+  P->nslots = (int)slots;
+  return BC_OK;
+}
+
+// -- coverage bitmap ----------------------------------------------------------
+struct Coverage {
+  std::vector<std::vector<uint8_t>> map;  // per slot, over the full box
+  const std::vector<bc_block>* blocks;
+  const std::vector<int32_t>* slot_block;
+  size_t index(const bc_block& B, int i, int j, int k) const {
+    const size_t F0 = B.n[0] + 2 * B.h[0], F1 = B.n[1] + 2 * B.h[1];
+    return ((size_t)(k + B.h[2]) * F1 + (size_t)(j + B.h[1])) * F0 + (size_t)(i + B.h[0]);
+  }
+  bool mark(int slot, int i, int j, int k) {
+    const bc_block& B = (*blocks)[(*slot_block)[slot]];
+    auto& m = map[slot];
+    if (m.empty()) {
+      const size_t F = (size_t)(B.n[0] + 2 * B.h[0]) * (B.n[1] + 2 * B.h[1]) *
+                       (B.n[2] + 2 * B.h[2]);
+      m.assign(F, 0);
+    }
+    uint8_t& c = m[index(B, i, j, k)];
+    if (c) return false;
+    c = 1;
+    return true;
+  }
+};
+
+template <typename F>
+void for_box(const Sub& s, F f) {
+  int q = 0;
+  for (int k = s.lo[2]; k < s.hi[2]; ++k)
+    for (int j = s.lo[1]; j < s.hi[1]; ++j)
+      for (int i = s.lo[0]; i < s.hi[0]; ++i) f(q++, i, j, k);
+}
+
+bc_status read_sub(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
+  s.kind = m.kind;
+  s.block = m.block;
+  if (m.kind < BC_ZERO || m.kind > BC_CSR)
+    return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: unknown kind %d", idx, m.kind);
+  if (m.block < 0 || m.block >= (int)P->blocks.size())
+    return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: bad block %d", idx, m.block);
+  const bc_block& B = P->blocks[m.block];
+  int64_t vol = 1;
+  for (int d = 0; d < 3; ++d) {
+    s.lo[d] = m.lo[d];
+    s.hi[d] = m.hi[d];
+    if (m.hi[d] <= m.lo[d])
+      return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: empty box on axis %d", idx, d);
+    if (m.lo[d] < -B.h[d] || m.hi[d] > B.n[d] + B.h[d])
+      return fail(BC_ERR_OUT_OF_RANGE, "sub-matrix %d: box leaves the full region", idx);
+    s.W[d] = m.hi[d] - m.lo[d];
+    vol *= s.W[d];
+  }
+  if (vol > (int64_t(1) << 30))
+    return fail(BC_ERR_UNSUPPORTED, "sub-matrix %d: box too large", idx);
+  s.vol = (int)vol;
+  if (m.ncomps < 1 || !m.comps)
+    return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: no components", idx);
+  for (int c = 0; c < m.ncomps; ++c) {
+    const int cc = m.comps[c];
+    if (cc < 0 || cc >= B.ncomp)
+      return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: bad component %d", idx, cc);
+    if (std::find(s.comps.begin(), s.comps.end(), cc) != s.comps.end())
+      return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: repeated component", idx);
+    s.comps.push_back(cc);
+  }
+  return BC_OK;
+}
+
+bc_status add_zero_const(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
+  const bc_block& B = P->blocks[s.block];
+  if (s.kind == BC_CONST) {
+    if (!m.values) return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: values is NULL", idx);
+    s.table = (int)P->const_val.size();
+    for (size_t c = 0; c < s.comps.size(); ++c)
+      for (int q = 0; q < s.vol; ++q) {
+        const double v = m.values[c * s.vol + q];
+        if (!std::isfinite(v))
+          return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: non-finite value", idx);
+        P->const_val.push_back(v);
+      }
+  }
+  for (size_t c = 0; c < s.comps.size(); ++c) {
+    const int slot = P->slot_base[s.block] + s.comps[c];
+    for_box(s, [&](int q, int i, int j, int k) {
+      P->rows.begin_row(slot, cell_offset(B, i, j, k),
+                        s.kind == BC_CONST ? P->const_val[s.table + c * s.vol + q] : 0.0);
+      P->rows.end_row();
+    });
+  }
+  return BC_OK;
+}
+
+bc_status add_map(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
+  const bc_block& B = P->blocks[s.block];
+  if (m.src_block < 0 || m.src_block >= (int)P->blocks.size())
+    return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: bad src_block", idx);
+  s.src_block = m.src_block;
+  const bc_block& S = P->blocks[m.src_block];
+  bool seen[3] = {false, false, false};
+  for (int d = 0; d < 3; ++d) {
+    if (m.perm[d] < 0 || m.perm[d] > 2 || seen[m.perm[d]])
+      return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: perm is not a permutation", idx);
+    seen[m.perm[d]] = true;
+    if (m.sign[d] != 1 && m.sign[d] != -1)
+      return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: sign must be +-1", idx);
+    s.perm[d] = m.perm[d];
+    s.sign[d] = m.sign[d];
+    s.offset[d] = m.offset[d];
+  }
+  if (S.nlevels != B.nlevels)
+    return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: source has another level count", idx);
+  for (int c : s.comps)
+    if (c >= S.ncomp)
+      return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: source lacks component %d", idx, c);
+  // the image of a box is a box: check its extent on every source axis
+  for (int d = 0; d < 3; ++d) {
+    const int e = s.perm[d];
+    const int64_t a = (int64_t)s.sign[d] * s.lo[e] + s.offset[d];
+    const int64_t b = (int64_t)s.sign[d] * (s.hi[e] - 1) + s.offset[d];
+    const int64_t mn = std::min(a, b), mx = std::max(a, b);
+    if (mn < 0 || mx >= S.n[d]) {
+      const bool reflect = (m.src_block == s.block && e == d);
+      return fail(reflect ? BC_ERR_HALO_TOO_WIDE : BC_ERR_COLUMN_NOT_DATA,
+                  "sub-matrix %d: map image leaves the source data on axis %d", idx, d);
+    }
+  }
+  for (int c : s.comps) {
+    const int slot = P->slot_base[s.block] + c;
+    const int sslot = P->slot_base[s.src_block] + c;
+    for_box(s, [&](int, int i, int j, int k) {
+      const int g[3] = {i, j, k};
+      int src[3];
+      for (int d = 0; d < 3; ++d) src[d] = s.sign[d] * g[s.perm[d]] + s.offset[d];
+      P->rows.begin_row(slot, cell_offset(B, i, j, k), 0.0);
+      P->rows.entry(sslot, cell_offset(S, src[0], src[1], src[2]), 1.0);
+      P->rows.end_row();
+    });
+  }
+  return BC_OK;
+}
+
+bc_status add_csr(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
+  const bc_block& B = P->blocks[s.block];
+  if (!m.row_ptr || !m.col_block || !m.col_comp || !m.col_ijk || !m.val)
+    return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: CSR arrays missing", idx);
+  const int64_t nrows = (int64_t)s.comps.size() * s.vol;
+  if (m.row_ptr[0] != 0) return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: row_ptr[0] != 0", idx);
+  for (int64_t r = 0; r < nrows; ++r)
+    if (m.row_ptr[r + 1] < m.row_ptr[r])
+      return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: row_ptr not monotone", idx);
+  s.table = (int)(P->csr_ptr.size() - 1);
+  for (size_t c = 0; c < s.comps.size(); ++c) {
+    const int slot = P->slot_base[s.block] + s.comps[c];
+    bc_status st = BC_OK;
+    for_box(s, [&](int q, int i, int j, int k) {
+      if (st != BC_OK) return;
+      const int64_t r = (int64_t)c * s.vol + q;
+      const double b = m.rhs ? m.rhs[r] : 0.0;
+      if (!std::isfinite(b)) {
+        st = fail(BC_ERR_INVALID_ARG, "sub-matrix %d: non-finite rhs", idx);
+        return;
+      }
+      P->rows.begin_row(slot, cell_offset(B, i, j, k), b);
+      for (int64_t e = m.row_ptr[r]; e < m.row_ptr[r + 1]; ++e) {
+        const int cb = m.col_block[e], cc = m.col_comp[e];
+        const int ci = m.col_ijk[3 * e], cj = m.col_ijk[3 * e + 1], ck = m.col_ijk[3 * e + 2];
+        if (cb < 0 || cb >= (int)P->blocks.size() || cc < 0 || cc >= P->blocks[cb].ncomp) {
+          st = fail(BC_ERR_INVALID_ARG, "sub-matrix %d: bad column block/component", idx);
+          return;
+        }
+        const bc_block& C = P->blocks[cb];
+        if (!in_data(C, ci, cj, ck)) {
+          st = fail(BC_ERR_COLUMN_NOT_DATA, "sub-matrix %d: column (%d,%d,%d) of block %d is not data",
+                    idx, ci, cj, ck, cb);
+          return;
+        }
+        if (C.nlevels != B.nlevels) {
+          st = fail(BC_ERR_INVALID_ARG, "sub-matrix %d: column block has another level count", idx);
+          return;
+        }
+        if (!std::isfinite(m.val[e])) {
+          st = fail(BC_ERR_INVALID_ARG, "sub-matrix %d: non-finite value", idx);
+          return;
+        }
+        const int cs = P->slot_base[cb] + cc;
+        const int64_t co = cell_offset(C, ci, cj, ck);
+        P->rows.entry(cs, co, m.val[e]);
+        P->csr_slot.push_back(cs);
+        P->csr_off.push_back((int32_t)co);
+        P->csr_val.push_back(m.val[e]);
+      }
+      P->rows.end_row();
+      P->csr_rhs.push_back(b);
+      P->csr_ptr.push_back((int64_t)P->csr_val.size());
+    });
+    if (st != BC_OK) return st;
+  }
+  return BC_OK;
+}
+
+// INTERP rows are appended after the geometry is known (cubed sphere: after
+// the GPU kernel); this records the stencil tables.
+bc_status read_interp(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
+  if (m.p < 1 || m.p > kPMax)
+    return fail(BC_ERR_UNSUPPORTED, "sub-matrix %d: p must be in 1..%d", idx, kPMax);
+  s.p = m.p;
+  s.geometry = m.geometry;
+  s.rot_u = m.rot_comp[0];
+  s.rot_v = m.rot_comp[1];
+  const bool rot = s.rot_u >= 0 || s.rot_v >= 0;
+  if (rot) {
+    auto has = [&](int c) { return std::find(s.comps.begin(), s.comps.end(), c) != s.comps.end(); };
+    if (s.rot_u < 0 || s.rot_v < 0 || s.rot_u == s.rot_v || !has(s.rot_u) || !has(s.rot_v))
+      return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: rot_comp must name two listed components", idx);
+  }
+  s.table = (int)P->itp_idx.size();
+  P->itp_idx.resize(P->itp_idx.size() + s.vol);
+  P->itp_w.resize(P->itp_w.size() + (size_t)s.vol * kPMax, 0.0);
+  P->itp_m.resize(P->itp_m.size() + (size_t)s.vol * 4, 0.0);
+  if (m.geometry == BC_GEOM_USER) {
+    if (!m.itp_src_block || !m.itp_start || !m.itp_axis || !m.itp_w || (rot && !m.itp_rot))
+      return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: interpolation tables missing", idx);
+    const bc_block& B = P->blocks[s.block];
+    for (int q = 0; q < s.vol; ++q) {
+      const int sb = m.itp_src_block[q], ax = m.itp_axis[q];
+      if (sb < 0 || sb >= (int)P->blocks.size() || ax < 0 || ax > 2)
+        return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: bad source block/axis", idx);
+      const bc_block& S = P->blocks[sb];
+      if (S.nlevels != B.nlevels)
+        return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: source has another level count", idx);
+      for (int c : s.comps)
+        if (c >= S.ncomp) return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: source lacks a component", idx);
+      int st[3] = {m.itp_start[3 * q], m.itp_start[3 * q + 1], m.itp_start[3 * q + 2]};
+      int en[3] = {st[0], st[1], st[2]};
+      en[ax] += m.p - 1;
+      if (!in_data(S, st[0], st[1], st[2]) || !in_data(S, en[0], en[1], en[2]))
+        return fail(BC_ERR_COLUMN_NOT_DATA, "sub-matrix %d: stencil leaves the source data", idx);
+      const int64_t off = cell_offset(S, st[0], st[1], st[2]);
+      P->itp_idx[s.table + q] = make_int4(P->slot_base[sb], (int)off, (int)S.stride[ax], 0);
+      for (int k = 0; k < m.p; ++k) {
+        const double w = m.itp_w[(size_t)q * m.p + k];
+        if (!std::isfinite(w)) return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: non-finite weight", idx);
+        P->itp_w[(size_t)(s.table + q) * kPMax + k] = w;
+      }
+      double* M = &P->itp_m[(size_t)(s.table + q) * 4];
+      if (rot) {
+        for (int e = 0; e < 4; ++e) {
+          M[e] = m.itp_rot[(size_t)q * 4 + e];
+          if (!std::isfinite(M[e])) return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: non-finite rotation", idx);
+        }
+      } else {
+        M[0] = M[3] = 1.0;
+      }
+    }
+  } else if (m.geometry == BC_GEOM_CUBED_SPHERE) {
+    int panel = -1;
+    for (int t = 0; t < 6; ++t) {
+      const int pb = m.cs_panels[t];
+      if (pb < 0 || pb >= (int)P->blocks.size())
+        return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: bad panel block", idx);
+      if (pb == s.block) panel = t;
+      const bc_block& A = P->blocks[pb];
+      const bc_block& B0 = P->blocks[m.cs_panels[0]];
+      if (A.n[0] != A.n[1] || A.n[0] != B0.n[0] || A.n[2] != 1 || A.h[0] != A.h[1] ||
+          A.h[0] != B0.h[0] || A.nlevels != B0.nlevels || A.ncomp != B0.ncomp ||
+          A.stride[0] != B0.stride[0] || A.stride[1] != B0.stride[1])
+        return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: panels must be equal N x N 2-D blocks", idx);
+    }
+    if (panel < 0) return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: block is not a panel", idx);
+    if (m.p > P->blocks[s.block].n[0])
+      return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: stencil wider than the panel", idx);
+  } else {
+    return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: unknown geometry", idx);
+  }
+  return BC_OK;
+}
+
+void append_interp_rows(bc_plan* P, const Sub& s) {
+  const bc_block& B = P->blocks[s.block];
+  for (int c : s.comps) {
+    if (c == s.rot_v) continue;  // the pair is emitted with its u component
+    const bool pair = (c == s.rot_u);
+    for (int comp_row = 0; comp_row < (pair ? 2 : 1); ++comp_row) {
+      const int crow = pair ? (comp_row == 0 ? s.rot_u : s.rot_v) : c;
+      const int slot = P->slot_base[s.block] + crow;
+      for_box(s, [&](int q, int i, int j, int k) {
+        const int4 ix = P->itp_idx[s.table + q];
+        const double* w = &P->itp_w[(size_t)(s.table + q) * kPMax];
+        const double* M = &P->itp_m[(size_t)(s.table + q) * 4];
+        const int pe = (ix.w & kFlagSnap) ? 1 : s.p;
+        P->rows.begin_row(slot, cell_offset(B, i, j, k), 0.0);
+        if (!pair) {
+          for (int n = 0; n < pe; ++n)
+            P->rows.entry(ix.x + c, (int64_t)ix.y + (int64_t)n * ix.z, w[n]);
+        } else {
+          const double ma = M[comp_row * 2 + 0], mb = M[comp_row * 2 + 1];
+          for (int n = 0; n < pe; ++n)
+            P->rows.entry(ix.x + s.rot_u, (int64_t)ix.y + (int64_t)n * ix.z, ma * w[n]);
+          for (int n = 0; n < pe; ++n)
+            P->rows.entry(ix.x + s.rot_v, (int64_t)ix.y + (int64_t)n * ix.z, mb * w[n]);
+        }
+        P->rows.end_row();
+      });
+    }
+  }
+}
+
+bc_status run_cubed_sphere(bc_plan* P, const std::vector<const bc_submatrix*>& cs_subs,
+                           const std::vector<int>& cs_idx) {
+  if (cs_subs.empty()) return BC_OK;
+  // all cubed-sphere sub-matrices of one plan must share the panel set
+  const bc_submatrix& m0 = *cs_subs[0];
+  CsPanels pan{};
+  const bc_block& B0 = P->blocks[m0.cs_panels[0]];
+  pan.N = B0.n[0];
+  pan.h = B0.h[0];
+  pan.p = m0.p;
+  pan.rotate = 0;
+  for (int t = 0; t < 6; ++t) {
+    const bc_block& A = P->blocks[m0.cs_panels[t]];
+    pan.slot_base[t] = P->slot_base[m0.cs_panels[t]];
+    pan.s0[t] = A.stride[0];
+    pan.s1[t] = A.stride[1];
+  }
+  std::vector<int4> cells;
+  for (size_t u = 0; u < cs_subs.size(); ++u) {
+    const bc_submatrix& m = *cs_subs[u];
+    for (int t = 0; t < 6; ++t)
+      if (m.cs_panels[t] != m0.cs_panels[t])
+        return fail(BC_ERR_UNSUPPORTED, "cubed-sphere sub-matrices must share one panel set");
+    if (m.p != m0.p) return fail(BC_ERR_UNSUPPORTED, "cubed-sphere sub-matrices must share p");
+    const Sub& s = P->subs[cs_idx[u]];
+    if (s.rot_u >= 0) pan.rotate = 1;
+    int panel = 0;
+    for (int t = 0; t < 6; ++t)
+      if (m.cs_panels[t] == s.block) panel = t;
+    for_box(s, [&](int q, int i, int j, int) { cells.push_back(make_int4(panel, i, j, s.table + q)); });
+  }
+  const size_t nrow = P->itp_idx.size();
+  int4 *d_cells = nullptr, *d_idx = nullptr;
+  double *d_w = nullptr, *d_m = nullptr;
+  unsigned* d_err = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(d_cells);
+    cudaFree(d_idx);
+    cudaFree(d_w);
+    cudaFree(d_m);
+    cudaFree(d_err);
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&d_cells, cells.size() * sizeof(int4))) != cudaSuccess ||
+      (e = cudaMalloc(&d_idx, nrow * sizeof(int4))) != cudaSuccess ||
+      (e = cudaMalloc(&d_w, nrow * kPMax * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&d_m, nrow * 4 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&d_err, sizeof(unsigned))) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "cubed-sphere geometry allocation");
+  }
+  unsigned herr = 0;
+  if ((e = cudaMemcpy(d_cells, cells.data(), cells.size() * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(d_idx, P->itp_idx.data(), nrow * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(d_w, P->itp_w.data(), nrow * kPMax * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(d_m, P->itp_m.data(), nrow * 4 * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(d_err, 0, sizeof(unsigned))) != cudaSuccess ||
+      (e = launch_cs_geometry(pan, d_cells, (int)cells.size(), d_idx, d_w, d_m, d_err, 0)) != cudaSuccess ||
+      (e = cudaMemcpy(P->itp_idx.data(), d_idx, nrow * sizeof(int4), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(P->itp_w.data(), d_w, nrow * kPMax * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(P->itp_m.data(), d_m, nrow * 4 * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(&herr, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "cubed-sphere geometry kernel");
+  }
+  cleanup();
+  if (herr & CS_ERR_NOT_EDGE)
+    return fail(BC_ERR_GEOMETRY, "cubed sphere: a box cell is not an edge ghost");
+  if (herr & CS_ERR_NEIGHBOUR)
+    return fail(BC_ERR_GEOMETRY, "cubed sphere: neighbour panel check failed");
+  if (herr & CS_ERR_DEPTH)
+    return fail(BC_ERR_GEOMETRY, "cubed sphere: ghost point is off the neighbour rows");
+  if (herr & CS_ERR_RANGE)
+    return fail(BC_ERR_GEOMETRY, "cubed sphere: stencil outside the neighbour data");
+  return BC_OK;
+}
+
+// -- work lists ----------------------------------------------------------------
+void item_common(const bc_plan* P, const Sub& s, int comp, Item& it) {
+  const bc_block& B = P->blocks[s.block];
+  it.dst_slot = P->slot_base[s.block] + comp;
+  it.dst_slot2 = -1;
+  it.W0 = s.W[0];
+  it.W1 = s.W[1];
+  it.vol = s.vol;
+  it.dst_org = cell_offset(B, s.lo[0], s.lo[1], s.lo[2]);
+  it.dst_s0 = B.stride[0];
+  it.dst_s1 = B.stride[1];
+  it.dst_s2 = B.stride[2];
+  it.dst_ls = B.nlevels > 1 ? B.level_stride : 0;
+}
+
+void emit_cells(std::vector<Item>& out, const Item& proto, int ncells, int nlev, int cells_per,
+                int lev_per) {
+  for (int l0 = 0; l0 < nlev; l0 += lev_per)
+    for (int q0 = 0; q0 < ncells; q0 += cells_per) {
+      Item it = proto;
+      it.mode = MODE_CELL;
+      it.q0 = q0;
+      it.ncell = std::min(cells_per, ncells - q0);
+      it.l0 = l0;
+      it.nlev = std::min(lev_per, nlev - l0);
+      out.push_back(it);
+    }
+}
+
+void emit_flat(std::vector<Item>& out, const Item& proto, int ncells, int nlev, int per) {
+  const int64_t total = (int64_t)ncells * nlev;
+  for (int64_t f0 = 0; f0 < total; f0 += per) {
+    Item it = proto;
+    it.mode = MODE_FLAT;
+    it.q0 = (int)f0;
+    it.ncell = (int)std::min<int64_t>(per, total - f0);
+    it.l0 = 0;
+    it.nlev = nlev;
+    out.push_back(it);
+  }
+}
+
+void build_items(bc_plan* P) {
+  const int threads = P->opts.threads;
+  const int cells_per = std::min(P->opts.cells_per_item, threads);
+  const int lev_per = P->opts.levels_per_item;
+  std::vector<std::pair<int, std::vector<Item>>> per_sub(P->subs.size());
+  for (size_t si = 0; si < P->subs.size(); ++si) {
+    const Sub& s = P->subs[si];
+    const bc_block& B = P->blocks[s.block];
+    std::vector<Item>& out = per_sub[si].second;
+    per_sub[si].first = s.kind;
+    for (size_t ci = 0; ci < s.comps.size(); ++ci) {
+      const int c = s.comps[ci];
+      Item it{};
+      item_common(P, s, c, it);
+      switch (s.kind) {
+        case BC_ZERO:
+        case BC_CONST:
+        case BC_MAP: {
+          it.kind = s.kind == BC_ZERO ? IK_ZERO : (s.kind == BC_CONST ? IK_CONST : IK_MAP);
+          it.table = s.table + (int)ci * s.vol;
+          if (s.kind == BC_MAP) {
+            const bc_block& S = P->blocks[s.src_block];
+            it.src_slot = P->slot_base[s.src_block] + c;
+            int img[3];
+            const int lo[3] = {s.lo[0], s.lo[1], s.lo[2]};
+            for (int d = 0; d < 3; ++d) img[d] = s.sign[d] * lo[s.perm[d]] + s.offset[d];
+            it.src_org = cell_offset(S, img[0], img[1], img[2]);
+            int64_t st[3] = {0, 0, 0};
+            for (int d = 0; d < 3; ++d) st[s.perm[d]] = s.sign[d] * S.stride[d];
+            it.src_s0 = st[0];
+            it.src_s1 = st[1];
+            it.src_s2 = st[2];
+            it.src_ls = S.nlevels > 1 ? S.level_stride : 0;
+          }
+          if (B.nlevels < kLevelUnroll)
+            emit_flat(out, it, s.vol, B.nlevels, threads * kFlatUnroll);
+          else
+            emit_cells(out, it, s.vol, B.nlevels, cells_per, lev_per);
+          break;
+        }
+        case BC_INTERP: {
+          if (c == s.rot_v) break;
+          it.table = s.table;
+          it.p = s.p;
+          it.comp = c;
+          if (c == s.rot_u) {
+            it.kind = IK_INTERP_PAIR;
+            it.comp2 = s.rot_v;
+            it.dst_slot2 = P->slot_base[s.block] + s.rot_v;
+          } else {
+            it.kind = IK_INTERP;
+          }
+          emit_cells(out, it, s.vol, B.nlevels, cells_per, lev_per);
+          break;
+        }
+        case BC_CSR: {
+          it.kind = IK_CSR;
+          it.table = s.table + (int)ci * s.vol;
+          emit_cells(out, it, s.vol, B.nlevels, cells_per, lev_per);
+          break;
+        }
+      }
+    }
+  }
+  // order: by kind, then sub-matrix (per-sub and per-kind ranges contiguous)
+  P->items.clear();
+  P->sub_begin.assign(P->subs.size(), 0);
+  P->sub_end.assign(P->subs.size(), 0);
+  for (int kind = 0; kind < 5; ++kind) {
+    P->type_begin[kind] = (int)P->items.size();
+    for (size_t si = 0; si < P->subs.size(); ++si) {
+      if (per_sub[si].first != kind) continue;
+      P->sub_begin[si] = (int)P->items.size();
+      P->items.insert(P->items.end(), per_sub[si].second.begin(), per_sub[si].second.end());
+      P->sub_end[si] = (int)P->items.size();
+    }
+    P->type_end[kind] = (int)P->items.size();
+  }
+  // adjoint: the zero pass over every covered ghost value
+  P->adj_zero.clear();
+  for (const Item& f : P->items) {
+    Item z = f;
+    z.kind = IK_ZERO;
+    z.dst_slot2 = -1;
+    P->adj_zero.push_back(z);
+    if (f.kind == IK_INTERP_PAIR) {
+      z.dst_slot = f.dst_slot2;
+      P->adj_zero.push_back(z);
+    }
+  }
+  // adjoint gather items over the transpose rows, grouped by level count
+  P->adj_items.clear();
+  const int nar = (int)P->arow_slot.size();
+  int r0 = 0;
+  while (r0 < nar) {
+    const int L = P->blocks[P->slot_block[P->arow_slot[r0]]].nlevels;
+    int r1 = r0;
+    while (r1 < nar && r1 - r0 < cells_per &&
+           P->blocks[P->slot_block[P->arow_slot[r1]]].nlevels == L)
+      ++r1;
+    for (int l0 = 0; l0 < L; l0 += lev_per) {
+      Item it{};
+      it.kind = IK_ADJ;
+      it.mode = MODE_CELL;
+      it.q0 = r0;
+      it.ncell = r1 - r0;
+      it.l0 = l0;
+      it.nlev = std::min(lev_per, L - l0);
+      P->adj_items.push_back(it);
+    }
+    r0 = r1;
+  }
+}
+
+void build_transpose(bc_plan* P) {
+  const ExplicitRows& R = P->rows;
+  struct E {
+    int32_t cs;
+    int64_t co;
+    int32_t rs;
+    int64_t ro;
+    double w;
+  };
+  std::vector<E> ents;
+  ents.reserve(R.val.size());
+  for (size_t r = 0; r < R.slot.size(); ++r)
+    for (int64_t e = R.ptr[r]; e < R.ptr[r + 1]; ++e)
+      ents.push_back({R.cslot[e], R.coff[e], R.slot[r], R.off[r], R.val[e]});
+  std::stable_sort(ents.begin(), ents.end(), [](const E& a, const E& b) {
+    if (a.cs != b.cs) return a.cs < b.cs;
+    if (a.co != b.co) return a.co < b.co;
+    if (a.rs != b.rs) return a.rs < b.rs;
+    return a.ro < b.ro;
+  });
+  P->arow_slot.clear();
+  P->arow_off.clear();
+  P->adj_ptr.assign(1, 0);
+  P->aent_slot.clear();
+  P->aent_off.clear();
+  P->aent_w.clear();
+  for (size_t e = 0; e < ents.size(); ++e) {
+    if (e == 0 || ents[e].cs != ents[e - 1].cs || ents[e].co != ents[e - 1].co) {
+      if (e) P->adj_ptr.push_back((int64_t)P->aent_w.size());
+      P->arow_slot.push_back(ents[e].cs);
+      P->arow_off.push_back((int32_t)ents[e].co);
+    }
+    P->aent_slot.push_back(ents[e].rs);
+    P->aent_off.push_back((int32_t)ents[e].ro);
+    P->aent_w.push_back(ents[e].w);
+  }
+  if (!ents.empty()) P->adj_ptr.push_back((int64_t)P->aent_w.size());
+  P->has_adjoint = true;
+}
+
+// -- device upload -------------------------------------------------------------
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  }
+};
+
+template <typename T>
+void put_dtype(std::vector<char>& host, size_t off, const std::vector<double>& v) {
+  T* d = reinterpret_cast<T*>(host.data() + off);
+  for (size_t i = 0; i < v.size(); ++i) d[i] = (T)v[i];
+}
+
+template <typename V>
+void put_raw(std::vector<char>& host, size_t off, const std::vector<V>& v) {
+  if (!v.empty()) std::memcpy(host.data() + off, v.data(), v.size() * sizeof(V));
+}
+
+bc_status upload_tables(bc_plan* P) {
+  const size_t S = P->esize;
+  Layout L;
+  const size_t o_ls = L.take(P->slot_ls.size() * 8);
+  const size_t o_idx = L.take(P->itp_idx.size() * sizeof(int4));
+  const size_t o_w = L.take(P->itp_w.size() * S);
+  const size_t o_m = L.take(P->itp_m.size() * S);
+  const size_t o_cp = L.take(P->csr_ptr.size() * 8);
+  const size_t o_cs = L.take(P->csr_slot.size() * 4);
+  const size_t o_co = L.take(P->csr_off.size() * 4);
+  const size_t o_cv = L.take(P->csr_val.size() * S);
+  const size_t o_cr = L.take(P->csr_rhs.size() * S);
+  const size_t o_k = L.take(P->const_val.size() * S);
+  const size_t o_as = L.take(P->arow_slot.size() * 4);
+  const size_t o_ao = L.take(P->arow_off.size() * 4);
+  const size_t o_ap = L.take(P->adj_ptr.size() * 8);
+  const size_t o_es = L.take(P->aent_slot.size() * 4);
+  const size_t o_eo = L.take(P->aent_off.size() * 4);
+  const size_t o_ew = L.take(P->aent_w.size() * S);
+  std::vector<char> host(L.off + 256, 0);
+  put_raw(host, o_ls, P->slot_ls);
+  put_raw(host, o_idx, P->itp_idx);
+  put_raw(host, o_cp, P->csr_ptr);
+  put_raw(host, o_cs, P->csr_slot);
+  put_raw(host, o_co, P->csr_off);
+  put_raw(host, o_as, P->arow_slot);
+  put_raw(host, o_ao, P->arow_off);
+  put_raw(host, o_ap, P->adj_ptr);
+  put_raw(host, o_es, P->aent_slot);
+  put_raw(host, o_eo, P->aent_off);
+  if (P->dtype == BC_F64) {
+    put_dtype<double>(host, o_w, P->itp_w);
+    put_dtype<double>(host, o_m, P->itp_m);
+    put_dtype<double>(host, o_cv, P->csr_val);
+    put_dtype<double>(host, o_cr, P->csr_rhs);
+    put_dtype<double>(host, o_k, P->const_val);
+    put_dtype<double>(host, o_ew, P->aent_w);
+  } else {
+    put_dtype<float>(host, o_w, P->itp_w);
+    put_dtype<float>(host, o_m, P->itp_m);
+    put_dtype<float>(host, o_cv, P->csr_val);
+    put_dtype<float>(host, o_cr, P->csr_rhs);
+    put_dtype<float>(host, o_k, P->const_val);
+    put_dtype<float>(host, o_ew, P->aent_w);
+  }
+  cudaError_t e = cudaMalloc(&P->tables.base, host.size());
+  if (e != cudaSuccess) {
+    P->tables.base = nullptr;
+    return cuda_fail(e, "device tables");
+  }
+  P->tables.bytes = host.size();
+  e = cudaMemcpy(P->tables.base, host.data(), host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "device tables upload");
+  char* b = static_cast<char*>(P->tables.base);
+  Ctx& c = P->ctx;
+  c.slot_ls = reinterpret_cast<const int64_t*>(b + o_ls);
+  c.itp_idx = reinterpret_cast<const int4*>(b + o_idx);
+  c.itp_w = b + o_w;
+  c.itp_m = b + o_m;
+  c.csr_ptr = reinterpret_cast<const int64_t*>(b + o_cp);
+  c.csr_slot = reinterpret_cast<const int32_t*>(b + o_cs);
+  c.csr_off = reinterpret_cast<const int32_t*>(b + o_co);
+  c.csr_val = b + o_cv;
+  c.csr_rhs = b + o_cr;
+  c.const_val = b + o_k;
+  c.arow_slot = reinterpret_cast<const int32_t*>(b + o_as);
+  c.arow_off = reinterpret_cast<const int32_t*>(b + o_ao);
+  c.adj_ptr = reinterpret_cast<const int64_t*>(b + o_ap);
+  c.aent_slot = reinterpret_cast<const int32_t*>(b + o_es);
+  c.aent_off = reinterpret_cast<const int32_t*>(b + o_eo);
+  c.aent_w = b + o_ew;
+  return BC_OK;
+}
+
+bc_status upload_work(bc_plan* P) {
+  if (P->work.base) {
+    cudaFree(P->work.base);
+    P->work.base = nullptr;
+  }
+  Layout L;
+  const size_t o_i = L.take(P->items.size() * sizeof(Item));
+  const size_t o_a = L.take(P->adj_items.size() * sizeof(Item));
+  const size_t o_z = L.take(P->adj_zero.size() * sizeof(Item));
+  const size_t o_c = L.take(2 * sizeof(unsigned));
+  std::vector<char> host(L.off + 256, 0);
+  put_raw(host, o_i, P->items);
+  put_raw(host, o_a, P->adj_items);
+  put_raw(host, o_z, P->adj_zero);
+  cudaError_t e = cudaMalloc(&P->work.base, host.size());
+  if (e != cudaSuccess) {
+    P->work.base = nullptr;
+    return cuda_fail(e, "device work list");
+  }
+  P->work.bytes = host.size();
+  e = cudaMemcpy(P->work.base, host.data(), host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "device work list upload");
+  char* b = static_cast<char*>(P->work.base);
+  P->d_items = reinterpret_cast<Item*>(b + o_i);
+  P->d_adj = reinterpret_cast<Item*>(b + o_a);
+  P->d_adj_zero = reinterpret_cast<Item*>(b + o_z);
+  P->d_counter = reinterpret_cast<unsigned*>(b + o_c);
+  return BC_OK;
+}
+
+void compute_stats(bc_plan* P) {
+  bc_stats& st = P->stats;
+  std::memset(&st, 0, sizeof(st));
+  const int64_t S = P->esize;
+  const ExplicitRows& R = P->rows;
+  auto L_of_slot = [&](int s) { return (int64_t)P->blocks[P->slot_block[s]].nlevels; };
+  // per-row kind, from the sub-matrices in order
+  size_t r = 0;
+  int64_t bytes = 0;
+  std::vector<std::pair<int32_t, int64_t>> csr_cols;
+  for (const Sub& s : P->subs) {
+    const int64_t L = P->blocks[s.block].nlevels;
+    const int64_t nrows = (int64_t)s.comps.size() * s.vol;
+    const int64_t vals = nrows * L;
+    st.ghost_values += vals;
+    st.ghost_values_kind[s.kind] += vals;
+    switch (s.kind) {
+      case BC_ZERO: bytes += vals * S; break;
+      case BC_CONST: bytes += vals * S + nrows * S; break;
+      case BC_MAP: bytes += 2 * vals * S; break;
+      case BC_INTERP: {
+        const bool rot = s.rot_u >= 0;
+        bytes += 2 * vals * S + (int64_t)s.vol * (16 + s.p * S + (rot ? 4 * S : 0));
+        break;
+      }
+      case BC_CSR: {
+        bytes += vals * S;
+        for (int64_t q = 0; q < nrows; ++q, ++r) {
+          bytes += 8 + S;
+          for (int64_t e = R.ptr[r]; e < R.ptr[r + 1]; ++e) {
+            bytes += 8 + S;
+            csr_cols.push_back({R.cslot[e], R.coff[e]});
+          }
+        }
+        continue;
+      }
+    }
+    r += nrows;
+  }
+  std::sort(csr_cols.begin(), csr_cols.end());
+  csr_cols.erase(std::unique(csr_cols.begin(), csr_cols.end()), csr_cols.end());
+  for (auto& cc : csr_cols) bytes += L_of_slot(cc.first) * S;
+  st.bytes_fwd = bytes;
+  int64_t abytes = 4 * st.ghost_values * S;
+  abytes += (int64_t)P->arow_slot.size() * 16 + (int64_t)P->aent_w.size() * (8 + S);
+  st.bytes_adj = abytes;
+  st.nitems = (int64_t)P->items.size();
+  st.nitems_adjoint = (int64_t)P->adj_items.size();
+  st.nsubmatrices = (int64_t)P->subs.size();
+  st.nslots = P->nslots;
+  st.table_bytes = (int64_t)P->tables.bytes + (int64_t)P->work.bytes;
+  st.transpose_nnz = (int64_t)P->aent_w.size();
+  st.element_size = P->esize;
+  st.form_threads = P->opts.threads;
+  st.form_ctas_per_sm = P->opts.ctas_per_sm;
+  st.cells_per_item = P->opts.cells_per_item;
+  st.levels_per_item = P->opts.levels_per_item;
+}
+
+bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
+  std::memset(&o, 0, sizeof(o));
+  if (in) o = *in;
+  if (o.threads == 0) o.threads = 256;
+  if (o.threads != 128 && o.threads != 256 && o.threads != 512)
+    return fail(BC_ERR_INVALID_ARG, "threads must be 128, 256 or 512");
+  if (o.cells_per_item == 0) o.cells_per_item = o.threads;
+  if (o.levels_per_item == 0) o.levels_per_item = 16;
+  if (o.cells_per_item < 1 || o.levels_per_item < 1 || o.ctas_per_sm < 0)
+    return fail(BC_ERR_INVALID_ARG, "bad work-item options");
+  return BC_OK;
+}
+
+bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_t nsubs,
+                           const bc_plan_opts* opts, bc_plan* P) {
+  bc_status st = normalise_opts(opts, P->opts);
+  if (st != BC_OK) return st;
+  if ((st = validate_grid(grid, P)) != BC_OK) return st;
+  if (nsubs < 0 || (nsubs > 0 && !subs)) return fail(BC_ERR_INVALID_ARG, "bad sub-matrix list");
+  Coverage cov;
+  cov.map.resize(P->nslots);
+  cov.blocks = &P->blocks;
+  cov.slot_block = &P->slot_block;
+  std::vector<const bc_submatrix*> cs_subs;
+  std::vector<int> cs_idx;
+  P->subs.resize(nsubs);
+  // pass 1: validation, coverage, tables of every kind but cubed-sphere rows
+  for (int si = 0; si < nsubs; ++si) {
+    const bc_submatrix& m = subs[si];
+    Sub& s = P->subs[si];
+    if ((st = read_sub(P, m, si, s)) != BC_OK) return st;
+    const bc_block& B = P->blocks[s.block];
+    bool ok = true, ghost = true;
+    for (int c : s.comps) {
+      const int slot = P->slot_base[s.block] + c;
+      for_box(s, [&](int, int i, int j, int k) {
+        if (in_data(B, i, j, k)) ghost = false;
+        else if (!cov.mark(slot, i, j, k)) ok = false;
+      });
+    }
+    if (!ghost) return fail(BC_ERR_OUT_OF_RANGE, "sub-matrix %d: box contains data cells", si);
+    if (!ok) return fail(BC_ERR_OVERLAP, "sub-matrix %d overlaps an earlier sub-matrix", si);
+    switch (m.kind) {
+      case BC_ZERO:
+      case BC_CONST: st = add_zero_const(P, m, si, s); break;
+      case BC_MAP: st = add_map(P, m, si, s); break;
+      case BC_CSR: st = add_csr(P, m, si, s); break;
+      case BC_INTERP:
+        st = read_interp(P, m, si, s);
+        if (st == BC_OK && m.geometry == BC_GEOM_CUBED_SPHERE) {
+          cs_subs.push_back(&m);
+          cs_idx.push_back(si);
+        }
+        break;
+    }
+    if (st != BC_OK) return st;
+  }
+  if (P->opts.strict_cover) {
+    for (int slot = 0; slot < P->nslots; ++slot) {
+      const bc_block& B = P->blocks[P->slot_block[slot]];
+      const size_t F = (size_t)(B.n[0] + 2 * B.h[0]) * (B.n[1] + 2 * B.h[1]) * (B.n[2] + 2 * B.h[2]);
+      const size_t D = (size_t)B.n[0] * B.n[1] * B.n[2];
+      const auto& mm = cov.map[slot];
+      const size_t covered = mm.empty() ? 0 : (size_t)std::count(mm.begin(), mm.end(), (uint8_t)1);
+      if (covered != F - D)
+        return fail(BC_ERR_UNCOVERED, "slot %d: %zu ghost cells have no row", slot, F - D - covered);
+    }
+  }
+  // device from here on
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "device attributes");
+  if ((st = run_cubed_sphere(P, cs_subs, cs_idx)) != BC_OK) return st;
+  // explicit rows of interpolation sub-matrices, in sub-matrix order
+  {
+    ExplicitRows all;
+    ExplicitRows& R = P->rows;
+    size_t r = 0;
+    for (Sub& s : P->subs) {
+      if (s.kind == BC_INTERP) {
+        ExplicitRows tmp;
+        std::swap(tmp, P->rows);
+        P->rows = ExplicitRows();
+        append_interp_rows(P, s);
+        std::swap(tmp, P->rows);
+        for (size_t t = 0; t < tmp.slot.size(); ++t) {
+          all.begin_row(tmp.slot[t], tmp.off[t], tmp.rhs[t]);
+          for (int64_t q = tmp.ptr[t]; q < tmp.ptr[t + 1]; ++q)
+            all.entry(tmp.cslot[q], tmp.coff[q], tmp.val[q]);
+          all.end_row();
+        }
+      } else {
+        const size_t nrows = s.comps.size() * (size_t)s.vol;
+        for (size_t t = r; t < r + nrows; ++t) {
+          all.begin_row(R.slot[t], R.off[t], R.rhs[t]);
+          for (int64_t q = R.ptr[t]; q < R.ptr[t + 1]; ++q) all.entry(R.cslot[q], R.coff[q], R.val[q]);
+          all.end_row();
+        }
+        r += nrows;
+      }
+    }
+    P->rows = std::move(all);
+  }
+  if (!P->opts.no_adjoint) build_transpose(P);
+  build_items(P);
+  if ((st = upload_tables(P)) != BC_OK) return st;
+  if ((st = upload_work(P)) != BC_OK) return st;
+  compute_stats(P);
+  return BC_OK;
+}
+
+bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t s) {
+  Ctx c = P->ctx;
+  c.slots = slots;
+  cudaError_t e = cudaSuccess;
+  const int T = P->opts.threads;
+  if (form == BC_FORM_BATCHED) {
+    if (P->opts.ctas_per_sm > 0)
+      e = launch_persistent(P->dtype, c, P->d_items, (int)P->items.size(), T,
+                            P->opts.ctas_per_sm * P->num_sms, P->d_counter, s);
+    else
+      e = launch_items(P->dtype, c, P->d_items, (int)P->items.size(), T, s);
+  } else if (form == BC_FORM_TYPEWIDE) {
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+      e = launch_items(P->dtype, c, P->d_items + P->type_begin[k],
+                       P->type_end[k] - P->type_begin[k], T, s);
+  } else if (form == BC_FORM_PER_BC) {
+    for (size_t si = 0; si < P->subs.size() && e == cudaSuccess; ++si)
+      e = launch_items(P->dtype, c, P->d_items + P->sub_begin[si],
+                       P->sub_end[si] - P->sub_begin[si], T, s);
+  } else {
+    return fail(BC_ERR_INVALID_ARG, "unknown form %d", form);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+  return BC_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+bc_status bc_plan_create(const bc_grid* grid, const bc_submatrix* subs, int32_t nsubs,
+                         const bc_plan_opts* opts, bc_plan** out) {
+  if (!out) return fail(BC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  g_last_error.clear();
+  bc_plan* P = new (std::nothrow) bc_plan();
+  if (!P) return fail(BC_ERR_NOMEM, "host allocation of the plan");
+  bc_status st;
+  try {
+    st = plan_create_impl(grid, subs, nsubs, opts, P);
+  } catch (const std::bad_alloc&) {
+    st = fail(BC_ERR_NOMEM, "host allocation while building the plan");
+  }
+  if (st != BC_OK) {
+    delete P;
+    return st;
+  }
+  *out = P;
+  return BC_OK;
+}
+
+int32_t bc_plan_nslots(const bc_plan* plan) { return plan ? plan->nslots : 0; }
+
+bc_status bc_apply_form(bc_plan* plan, void* const* slot_ptrs, int32_t form, void* stream) {
+  if (!plan) return fail(BC_ERR_INVALID_ARG, "plan is NULL");
+  if (!slot_ptrs && plan->nslots > 0) return fail(BC_ERR_INVALID_ARG, "slot_ptrs is NULL");
+  return launch_forward(plan, slot_ptrs, form, static_cast<cudaStream_t>(stream));
+}
+
+bc_status bc_apply(bc_plan* plan, void* const* slot_ptrs, void* stream) {
+  return bc_apply_form(plan, slot_ptrs, BC_FORM_BATCHED, stream);
+}
+
+bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs, void* stream) {
+  if (!plan) return fail(BC_ERR_INVALID_ARG, "plan is NULL");
+  if (!plan->has_adjoint) return fail(BC_ERR_UNSUPPORTED, "plan was built without the transpose");
+  if (!slot_ptrs && plan->nslots > 0) return fail(BC_ERR_INVALID_ARG, "slot_ptrs is NULL");
+  Ctx c = plan->ctx;
+  c.slots = slot_ptrs;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int T = plan->opts.threads;
+  cudaError_t e = launch_items(plan->dtype, c, plan->d_adj, (int)plan->adj_items.size(), T, s);
+  if (e == cudaSuccess)
+    e = launch_items(plan->dtype, c, plan->d_adj_zero, (int)plan->adj_zero.size(), T, s);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+  return BC_OK;
+}
+
+bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs, void* const* dev_ptrs,
+                        void* const* slot_ptrs, void* stream) {
+  if (!plan || !host_ptrs || !dev_ptrs || !slot_ptrs)
+    return fail(BC_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // span of every slot, merged when host and device runs are both contiguous
+  struct Run {
+    char* h;
+    char* d;
+    size_t n;
+  };
+  std::vector<Run> runs;
+  for (int slot = 0; slot < plan->nslots; ++slot) {
+    const bc_block& B = plan->blocks[plan->slot_block[slot]];
+    const int64_t last = cell_offset(B, B.n[0] + B.h[0] - 1, B.n[1] + B.h[1] - 1, B.n[2] + B.h[2] - 1) +
+                         (int64_t)(B.nlevels - 1) * (B.nlevels > 1 ? B.level_stride : 0);
+    const size_t n = (size_t)(last + 1) * plan->esize;
+    char* h = static_cast<char*>(host_ptrs[slot]);
+    char* d = static_cast<char*>(dev_ptrs[slot]);
+    if (!runs.empty() && runs.back().h + runs.back().n == h && runs.back().d + runs.back().n == d)
+      runs.back().n += n;
+    else
+      runs.push_back({h, d, n});
+  }
+  cudaError_t e = cudaSuccess;
+  for (const Run& r : runs)
+    if ((e = cudaMemcpyAsync(r.d, r.h, r.n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(e, "host-to-device copy");
+  bc_status st = launch_forward(plan, slot_ptrs, BC_FORM_BATCHED, s);
+  if (st != BC_OK) return st;
+  for (const Run& r : runs)
+    if ((e = cudaMemcpyAsync(r.h, r.d, r.n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return cuda_fail(e, "device-to-host copy");
+  return BC_OK;
+}
+
+bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) {
+  if (!plan || !slot_ptrs) return fail(BC_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0, l2 = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+  const size_t flush_bytes = std::max<size_t>((size_t)l2 * 2, size_t(64) << 20);
+  void* flush = nullptr;
+  cudaError_t e = cudaMalloc(&flush, flush_bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune flush buffer");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bc_plan_opts keep = plan->opts;
+  bc_plan_opts best = keep;
+  float best_ms = 1e30f;
+  // time one candidate: median of 6 cold-L2 launches after 2 warm-ups
+  auto time_candidate = [&](float& med) -> bc_status {
+    build_items(plan);
+    bc_status st = upload_work(plan);
+    if (st != BC_OK) return st;
+    std::vector<float> ts;
+    for (int rep = 0; rep < 8; ++rep) {
+      cudaMemsetAsync(flush, rep & 0xff, flush_bytes, s);
+      cudaEventRecord(e0, s);
+      if ((st = launch_forward(plan, slot_ptrs, BC_FORM_BATCHED, s)) != BC_OK) return st;
+      cudaEventRecord(e1, s);
+      cudaError_t ee = cudaEventSynchronize(e1);
+      if (ee != cudaSuccess) return cuda_fail(ee, "autotune timing");
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep >= 2) ts.push_back(ms);
+    }
+    std::sort(ts.begin(), ts.end());
+    med = ts[ts.size() / 2];
+    return BC_OK;
+  };
+  const int threads_c[] = {128, 256, 512};
+  const int levels_c[] = {8, 16, 32, 64};
+  const int ctas_c[] = {0, 2, 4, 8};
+  bc_status st = BC_OK;
+  for (int T : threads_c) {
+    for (int Lp : levels_c) {
+      for (int cps : ctas_c) {
+        if (cps * T > 2048 || st != BC_OK) continue;
+        plan->opts.threads = T;
+        plan->opts.cells_per_item = T;
+        plan->opts.levels_per_item = Lp;
+        plan->opts.ctas_per_sm = cps;
+        float med = 0;
+        st = time_candidate(med);
+        if (st == BC_OK && med < best_ms) {
+          best_ms = med;
+          best = plan->opts;
+        }
+      }
+    }
+  }
+  plan->opts = st == BC_OK ? best : keep;
+  build_items(plan);
+  bc_status st2 = upload_work(plan);
+  if (st == BC_OK) st = st2;
+  compute_stats(plan);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(flush);
+  return st;
+}
+
+bc_status bc_plan_stats(const bc_plan* plan, bc_stats* out) {
+  if (!plan || !out) return fail(BC_ERR_INVALID_ARG, "NULL argument");
+  *out = plan->stats;
+  return BC_OK;
+}
+
+bc_status bc_plan_export_csr(const bc_plan* plan, int64_t* nrows, int64_t* nnz, int32_t* row_slot,
+                             int64_t* row_off, int64_t* row_ptr, int32_t* col_slot,
+                             int64_t* col_off, double* val, double* rhs) {
+  if (!plan || !nrows || !nnz) return fail(BC_ERR_INVALID_ARG, "NULL argument");
+  const ExplicitRows& R = plan->rows;
+  *nrows = (int64_t)R.slot.size();
+  *nnz = (int64_t)R.val.size();
+  if (!row_slot) return BC_OK;
+  if (!row_off || !row_ptr || !col_slot || !col_off || !val || !rhs)
+    return fail(BC_ERR_INVALID_ARG, "NULL output array");
+  std::vector<size_t> order(R.slot.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    if (R.slot[a] != R.slot[b]) return R.slot[a] < R.slot[b];
+    return R.off[a] < R.off[b];
+  });
+  int64_t e = 0;
+  row_ptr[0] = 0;
+  for (size_t t = 0; t < order.size(); ++t) {
+    const size_t r = order[t];
+    row_slot[t] = R.slot[r];
+    row_off[t] = R.off[r];
+    rhs[t] = R.rhs[r];
+    for (int64_t q = R.ptr[r]; q < R.ptr[r + 1]; ++q, ++e) {
+      col_slot[e] = R.cslot[q];
+      col_off[e] = R.coff[q];
+      val[e] = R.val[q];
+    }
+    row_ptr[t + 1] = e;
+  }
+  return BC_OK;
+}
+
+void bc_plan_destroy(bc_plan* plan) { delete plan; }
+
+const char* bc_status_string(bc_status status) {
+  switch (status) {
+    case BC_OK: return "BC_OK";
+    case BC_ERR_INVALID_ARG: return "BC_ERR_INVALID_ARG";
+    case BC_ERR_OVERLAP: return "BC_ERR_OVERLAP";
+    case BC_ERR_COLUMN_NOT_DATA: return "BC_ERR_COLUMN_NOT_DATA";
+    case BC_ERR_UNCOVERED: return "BC_ERR_UNCOVERED";
+    case BC_ERR_HALO_TOO_WIDE: return "BC_ERR_HALO_TOO_WIDE";
+    case BC_ERR_OUT_OF_RANGE: return "BC_ERR_OUT_OF_RANGE";
+    case BC_ERR_NOMEM: return "BC_ERR_NOMEM";
+    case BC_ERR_CUDA: return "BC_ERR_CUDA";
+    case BC_ERR_UNSUPPORTED: return "BC_ERR_UNSUPPORTED";
+    case BC_ERR_TIMEOUT: return "BC_ERR_TIMEOUT";
+    case BC_ERR_GEOMETRY: return "BC_ERR_GEOMETRY";
+  }
+  return "BC_ERR_UNKNOWN";
+}
+
+const char* bc_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+"""GPU adjoint (A^T) against the oracle's explicit transpose, FP64 central
+finite differences of the GPU forward, the dot-product test, and the
+autograd Function."""
+import numpy as np
+import pytest
+
+from gpu_util import TOL, bits, flat, run, to_device
+from oracle.operator import apply_adjoint, build_operator
+from paper_2605_14780_gb300 import bc, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _adjoint_gpu(w, cot, opts=None):
+    import torch
+    ts = to_device(w["fields"])
+    plan = bc.plan_for_workload(w, ts, opts)
+    cs = to_device(cot)
+    plan.adjoint(bc.slot_table(cs))
+    torch.cuda.synchronize()
+    return plan, [c.cpu().numpy() for c in cs]
+
+
+def _check_adjoint(w, cot, out, levels=None):
+    """Data values: |gpu - oracle| <= tol * (|y_j| + sum_i |A_ij y_i|);
+    covered ghosts exactly 0; uncovered ghosts and untouched data equal to
+    the cotangent bit for bit."""
+    op = build_operator(w, levels=levels)
+    ref = flat(apply_adjoint(op, cot))
+    got = flat(out).astype(np.float64)
+    y = flat(cot).astype(np.float64)
+    tol = TOL[w["dtype"]]
+    g = np.abs(y[op.rows])
+    scale = np.abs(y).copy()
+    scale[op.layout.data_rows()] += abs(op.A).T @ g
+    covered = np.zeros(y.size, bool)
+    covered[op.rows] = True
+    if levels is None:
+        assert np.all(got[covered] == 0.0)
+        chk = ~covered
+    else:
+        # only the sampled levels are exact in `ref`; compare their data rows
+        chk = np.zeros(y.size, bool)
+        dr = op.layout.data_rows()
+        touched = np.zeros(op.layout.n_data, bool)
+        touched[np.unique(op.A.indices)] = True
+        chk[dr[touched]] = True
+        chk &= _level_mask(w, levels)
+    err = np.abs(got[chk] - ref[chk])
+    assert np.all(err <= tol * scale[chk] + 0.0), np.max(err / (tol * scale[chk] + 1e-300))
+
+
+def _level_mask(w, levels):
+    parts = []
+    for a in w["fields"]:
+        m = np.zeros(a.shape, bool)
+        m[:, [lv for lv in levels if lv < a.shape[1]]] = True
+        parts.append(m.ravel())
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: synth.alg1_example(dtype="f64"),
+    lambda: synth.hpcg_block((7, 5, 6), "S", seed=3),
+    lambda: synth.hpcg_block((7, 5, 6), "P", seed=3, dtype="f32"),
+    lambda: synth.batching(nblocks=40, side_lo=3, side_hi=30, lev_lo=1,
+                           lev_hi=19, h=2, seed=2, dtype="f32"),
+    lambda: synth.cubed_sphere(9, 3, 6, 3, ("h", "u", "v"), "f64", seed=4),
+    lambda: synth.cubed_sphere(16, 3, 6, 10, ("h", "u", "v"), "f32", seed=4),
+])
+def test_adjoint_vs_oracle(make):
+    w = make()
+    cot = synth.cotangent_like(w, 77)
+    _, out = _adjoint_gpu(w, cot)
+    _check_adjoint(w, cot, out)
+
+
+def test_adjoint_full_768_sampled():
+    """The 6 x 768^2, (h, u, v) x 32-level FP32 adjoint, levels 2 and 29
+    compared with the oracle's explicit transpose."""
+    w = synth.adjoint_cubed_sphere()
+    cot = synth.cotangent_like(w, 5)
+    _, out = _adjoint_gpu(w, cot)
+    _check_adjoint(w, cot, out, levels=[2, 29])
+
+
+def _fd_setup(N=10, L=3):
+    w = synth.cubed_sphere(N, 3, 6, L, ("h", "u", "v"), "f64", seed=6)
+    for a in w["fields"]:
+        a[np.isnan(a)] = 0.0
+    return w
+
+
+def test_adjoint_central_fd_64_directions():
+    """x_bar . d == y_bar . (F(x + e d) - F(x - e d)) / 2e with the GPU
+    forward in FP64, 64 random data directions (exact for an affine map up to
+    rounding)."""
+    import torch
+    w = _fd_setup()
+    rng = np.random.default_rng(6)
+    cot = synth.cotangent_like(w, 66)
+    _, xbar = _adjoint_gpu(w, cot)
+    xbar = flat(xbar)
+    ts = to_device(w["fields"])
+    plan = bc.plan_for_workload(w, ts)
+    y = flat(cot).astype(np.float64)
+    mask = [np.zeros(a.shape, bool) for a in w["fields"]]
+    for m, blk in zip(mask, w["blocks"]):
+        n, h = blk["n"], blk["h"]
+        m[:, :, h[2]:h[2] + n[2], h[1]:h[1] + n[1], h[0]:h[0] + n[0]] = True
+    eps = 0.25
+    for _ in range(64):
+        dirs = [np.where(m, rng.uniform(-1, 1, m.shape), 0.0) for m in mask]
+        outs = []
+        for sgn in (1.0, -1.0):
+            xs = [torch.from_numpy(a + sgn * eps * d).cuda() for a, d in zip(w["fields"], dirs)]
+            plan.apply(bc.slot_table(xs))
+            torch.cuda.synchronize()
+            outs.append(flat([x.cpu().numpy() for x in xs]))
+        jd = (outs[0] - outs[1]) / (2 * eps)
+        lhs = np.dot(y, jd)
+        rhs = np.dot(xbar, flat(dirs))
+        mag = np.sum(np.abs(y * jd)) + np.sum(np.abs(xbar * flat(dirs)))
+        assert abs(lhs - rhs) <= 1e-13 * mag
+
+
+def test_dot_product_identity_gpu():
+    """<A x, y> == <x, A^T y> with both sides from the GPU (FP64),
+    compensated sums, relative 1e-13."""
+    import math
+    w = _fd_setup(12, 4)
+    rng = np.random.default_rng(1)
+    for a in w["fields"]:
+        a[...] = np.where(np.isnan(a), 0.0, a)
+    _, fx = run(w)
+    op = build_operator(w)
+    covered = np.zeros(sum(a.size for a in w["fields"]), bool)
+    covered[op.rows] = True
+    ax = flat(fx)[covered]
+    ycot = [rng.uniform(-1, 1, a.shape) for a in w["fields"]]
+    yv = flat(ycot)
+    ymask = np.where(covered, yv, 0.0)
+    ycot_g = [c for c in op.layout.unflatten_full(ymask, w["fields"])]
+    _, atyf = _adjoint_gpu(w, ycot_g)
+    aty = flat(atyf)
+    xd = np.zeros_like(aty)
+    dr = op.layout.data_rows()
+    xd[dr] = op.layout.data_vector(w["fields"])
+    lhs = math.fsum((ax * yv[covered]).tolist())
+    rhs = math.fsum((xd * aty).tolist())
+    mag = math.fsum(np.abs(ax * yv[covered]).tolist())
+    assert abs(lhs - rhs) <= 1e-13 * mag
+
+
+def test_autograd_function():
+    import torch
+    w = synth.cubed_sphere(8, 2, 4, 2, ("h", "u", "v"), "f64", seed=8)
+    for a in w["fields"]:
+        a[np.isnan(a)] = 0.0
+    ts = [t.requires_grad_(False) for t in to_device(w["fields"])]
+    plan = bc.plan_for_workload(w, ts)
+    leaves = [t.clone().requires_grad_(True) for t in ts]
+    xs = [l * 1.0 for l in leaves]
+    ys = bc.BCFill.apply(plan, *xs)
+    cot = synth.cotangent_like(w, 9)
+    loss = sum((y * torch.from_numpy(c).cuda()).sum() for y, c in zip(ys, cot))
+    loss.backward()
+    got = flat([l.grad.cpu().numpy() for l in leaves])
+    ref = flat(apply_adjoint(build_operator(w), cot))
+    assert np.max(np.abs(got - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+    # the forward result is the ghost-filled field
+    out = flat([y.detach().cpu().numpy() for y in ys])
+    _, fwd = run(w)
+    assert np.array_equal(bits(out), bits(flat(fwd)))

@@ -1,0 +1,245 @@
+"""GPU parity of the forward apply against the FP64 oracle, through the C ABI.
+
+Copies, zero and constant rows bit-exact; interpolation and CSR rows within
+1e-12 (FP64) / 2e-6 (FP32) of the row scale sum_e |a_ie x_e| + |b_i|.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import bits, compare, flat, run, to_device
+from oracle.operator import build_operator
+from paper_2605_14780_gb300 import bc, synth
+
+pytestmark = pytest.mark.gpu
+
+FORMS = [bc.BC_FORM_BATCHED, bc.BC_FORM_TYPEWIDE, bc.BC_FORM_PER_BC]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_alg1(dtype):
+    w = synth.alg1_example(dtype=dtype)
+    _, out = run(w)
+    compare(w, out)
+
+
+@pytest.mark.parametrize("variant", ["Z", "P", "S"])
+@pytest.mark.parametrize("n", [(6, 6, 6), (9, 7, 5), (1, 1, 1)])
+def test_hpcg_small(variant, n):
+    w = synth.hpcg_block(n, variant, seed=4)
+    _, out = run(w)
+    compare(w, out)
+
+
+@pytest.mark.parametrize("variant", ["Z", "P", "S"])
+def test_hpcg_128_full(variant):
+    """The 128^3 HPCG-like block, checked in full and through the 27-point
+    operator applied to the ghost-filled array."""
+    w = synth.hpcg_block(128, variant, seed=2)
+    _, out = run(w)
+    op, nexact, _ = compare(w, out)
+    assert nexact == len(op.rows) == 130 ** 3 - 128 ** 3
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("seed", [1, 2])
+def test_batching_small(dtype, seed):
+    w = synth.batching(nblocks=48, side_lo=3, side_hi=40, lev_lo=1, lev_hi=19,
+                       h=2, seed=seed, dtype=dtype)
+    _, out = run(w)
+    compare(w, out)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_forms_bit_identical(form):
+    w = synth.batching(nblocks=64, side_lo=4, side_hi=64, lev_lo=1, lev_hi=40,
+                       h=2, seed=7, dtype="f32")
+    _, ref = run(w, bc.BC_FORM_BATCHED)
+    _, out = run(w, form)
+    assert np.array_equal(bits(flat(out)), bits(flat(ref)))
+    compare(w, out)
+
+
+@pytest.mark.parametrize("opts", [
+    {"ctas_per_sm": 2, "threads": 128, "levels_per_item": 8},
+    {"ctas_per_sm": 4, "threads": 256, "levels_per_item": 64},
+    {"ctas_per_sm": 1, "threads": 512, "levels_per_item": 3, "cells_per_item": 37},
+])
+def test_persistent_and_item_shapes(opts):
+    """Persistent grid with an atomic work counter, repeated launches (the
+    counter must reset itself), odd item shapes."""
+    w = synth.batching(nblocks=64, side_lo=4, side_hi=64, lev_lo=1, lev_hi=40,
+                       h=2, seed=8, dtype="f32")
+    _, out = run(w, opts=opts, repeat=3)
+    compare(w, out)
+
+
+def test_batching_full_512():
+    """The 512-block batching workload in full."""
+    w = synth.batching()
+    _, out = run(w)
+    compare(w, out)
+
+
+@pytest.mark.parametrize("N,h,p", [(5, 2, 4), (8, 3, 6), (16, 2, 4), (7, 1, 2),
+                                   (9, 3, 8)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_cubed_sphere_scalar(N, h, p, dtype):
+    w = synth.cubed_sphere(N, h, p, 3, ("scalar",), dtype, seed=N)
+    _, out = run(w)
+    compare(w, out)
+
+
+@pytest.mark.parametrize("N,L", [(6, 1), (12, 9), (24, 8), (10, 17)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_cubed_sphere_vector(N, L, dtype):
+    w = synth.cubed_sphere(N, 3, 6, L, ("h", "u", "v"), dtype, seed=3)
+    _, out = run(w)
+    compare(w, out)
+
+
+def test_tiny_cubed_sphere_full():
+    """6 x 32^2, h = 2, p = 4, FP64 scalar, corners by CSR."""
+    w = synth.tiny_cubed_sphere()
+    plan, out = run(w)
+    compare(w, out)
+    assert plan.stats()["ghost_values"] == 6 * (36 * 36 - 32 * 32)
+
+
+def test_swe_cubed_sphere_sampled():
+    """6 x 384^2, h = 3, (h, u, v) x 32 levels FP32, p = 6: every ghost is
+    computed on the GPU; levels 0, 13 and 31 are compared with the oracle."""
+    w = synth.swe_cubed_sphere()
+    _, out = run(w)
+    compare(w, out, levels=[0, 13, 31])
+
+
+def test_adjoint_config_forward_sampled():
+    """6 x 768^2 forward, levels 5 and 30 compared."""
+    w = synth.adjoint_cubed_sphere()
+    _, out = run(w)
+    compare(w, out, levels=[5, 30])
+
+
+def test_export_csr_matches_oracle():
+    """The plan's own rows of A (incl. the GPU-generated FP64 geometry)
+    against the oracle's explicit A, entry by entry."""
+    w = synth.cubed_sphere(12, 3, 6, 2, ("h", "u", "v"), "f64", seed=5)
+    ts = to_device(w["fields"])
+    plan = bc.plan_for_workload(w, ts)
+    ex = plan.export_csr()
+    op = build_operator(w, levels=[0])
+    lay = op.layout
+    # slot s = (block, comp) -> row/col ids of level 0
+    slot_b, slot_c = [], []
+    for b, blk in enumerate(w["blocks"]):
+        for c in range(blk["ncomp"]):
+            slot_b.append(b)
+            slot_c.append(c)
+    slot_b, slot_c = np.array(slot_b), np.array(slot_c)
+    plane = lay.F.prod(axis=1)
+    rows = lay.full_base[slot_b[ex["row_slot"]]] + \
+        slot_c[ex["row_slot"]] * lay.L[slot_b[ex["row_slot"]]] * plane[slot_b[ex["row_slot"]]] + \
+        ex["row_off"]
+    assert np.array_equal(np.sort(rows), op.rows)
+    # columns: full offset -> data cell -> column id
+    cb = slot_b[ex["col_slot"]]
+    F = lay.F[cb]
+    h = lay.h[cb]
+    o = ex["col_off"]
+    i = o % F[:, 0] - h[:, 0]
+    j = (o // F[:, 0]) % F[:, 1] - h[:, 1]
+    k = o // (F[:, 0] * F[:, 1]) - h[:, 2]
+    cols = lay.col(cb, slot_c[ex["col_slot"]], 0, np.stack([i, j, k], 1))
+    import scipy.sparse as sp
+    order = np.argsort(rows)
+    A = sp.csr_matrix((ex["val"], cols, ex["row_ptr"]),
+                      shape=(len(rows), lay.n_data))[order]
+    A.sum_duplicates()
+    D = (A - op.A).tocoo()
+    assert A.nnz == op.A.nnz
+    assert np.max(np.abs(D.data)) <= 1e-13 if D.nnz else True
+
+
+def test_non_contiguous_layout():
+    """Levels innermost: element (c, l, k, j, i) at ((c*F2 + k)*F1 + j)*F0*L
+    + i*L + l; the plan takes the strides from the tensor views."""
+    import torch
+    w = synth.cubed_sphere(10, 2, 4, 5, ("h", "u", "v"), "f32", seed=9)
+    views = []
+    for a in w["fields"]:
+        C, L, F2, F1, F0 = a.shape
+        base = torch.from_numpy(np.ascontiguousarray(a.transpose(0, 2, 3, 4, 1))).cuda()
+        views.append(base.permute(0, 4, 1, 2, 3))
+    plan, _ = run(w, tensors=views)
+    out = [v.cpu().numpy() for v in views]
+    compare(w, out)
+
+
+def test_empty_plan():
+    w = synth.alg1_example()
+    w["bcs"] = []
+    plan, out = run(w)
+    assert np.array_equal(bits(flat(out)), bits(flat(w["fields"])))
+    assert plan.stats()["nitems"] == 0
+
+
+def test_graph_capture_replay():
+    import torch
+    w = synth.batching(nblocks=32, side_lo=4, side_hi=48, lev_lo=1, lev_hi=20,
+                       h=2, seed=12, dtype="f32")
+    ts = to_device(w["fields"])
+    plan = bc.plan_for_workload(w, ts, {"ctas_per_sm": 2})
+    table = bc.slot_table(ts)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan.apply(table, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.apply(table, stream=s)
+    for _ in range(100):
+        g.replay()
+    torch.cuda.synchronize()
+    compare(w, [t.cpu().numpy() for t in ts])
+
+
+def test_apply_host_roundtrip():
+    import torch
+    w = synth.batching(nblocks=16, side_lo=4, side_hi=32, lev_lo=1, lev_hi=9,
+                       h=2, seed=13, dtype="f32")
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in w["fields"]]
+    dev = [torch.empty_like(h, device="cuda") for h in host]
+    plan = bc.plan_for_workload(w, dev)
+    table = bc.slot_table(dev)
+    plan.apply_host(bc.slot_pointers(host), bc.slot_pointers(dev), table)
+    torch.cuda.synchronize()
+    compare(w, [h.numpy() for h in host])
+
+
+def test_copy_rows_preserve_nan_payload_and_signed_zero():
+    """Copies move bit patterns: a NaN payload and -0.0 in the source data
+    arrive unchanged in the ghosts that copy them."""
+    w = synth.hpcg_block((6, 5, 4), "P", seed=1, dtype="f32")
+    d = synth.data_view(w["fields"][0], w["blocks"][0])
+    pay = np.array([0x7fc12345], np.uint32).view(np.float32)[0]
+    d[0, 0, :, :, 5] = pay           # right x face: copied into the left ghosts
+    d[0, 0, :, :, 0] = -0.0
+    _, out = run(w)
+    g = out[0][0, 0]
+    assert np.all(bits(g[1:-1, 1:-1, 0]) == 0x7fc12345)
+    assert np.all(bits(g[1:-1, 1:-1, -1]) == 0x80000000)
+
+
+def test_autotune_keeps_results():
+    import torch
+    w = synth.batching(nblocks=64, side_lo=4, side_hi=64, lev_lo=1, lev_hi=40,
+                       h=2, seed=14, dtype="f32")
+    ts = to_device(w["fields"])
+    plan = bc.plan_for_workload(w, ts)
+    table = bc.slot_table(ts)
+    plan.autotune(table)
+    for t, a in zip(ts, w["fields"]):
+        t.copy_(torch.from_numpy(a))
+    plan.apply(table)
+    torch.cuda.synchronize()
+    compare(w, [t.cpu().numpy() for t in ts])
