@@ -182,9 +182,19 @@ def make_workload(name):
     raise ValueError(name)
 
 
-def field_copies(w, ncopies, device):
+def make_workload_named(name):
+    from paper_2605_14780_gb300 import synth
+    if name == "tiny":
+        return synth.tiny_cubed_sphere()
+    return make_workload(name)[0]
+
+
+def field_copies(w, ncopies, device, layout="level_outermost"):
     """``ncopies`` independent device copies of the fields, each copy one
-    contiguous allocation with the blocks back to back."""
+    contiguous allocation with the blocks back to back.  ``layout``:
+    ``level_outermost`` stores each component as [level][k][j][i];
+    ``level_innermost`` as [k][j][i][level] (views keep the (C, L, F2, F1,
+    F0) index order, the plan reads the strides)."""
     import torch
     sizes = [a.size for a in w["fields"]]
     dt = torch.float32 if w["dtype"] == "f32" else torch.float64
@@ -193,12 +203,55 @@ def field_copies(w, ncopies, device):
         buf = torch.empty(sum(sizes), dtype=dt, device=device)
         views, pos = [], 0
         for a in w["fields"]:
-            v = buf[pos:pos + a.size].view(a.shape)
+            if layout == "level_innermost":
+                C, L, F2, F1, F0 = a.shape
+                v = buf[pos:pos + a.size].view(C, F2, F1, F0, L).permute(0, 4, 1, 2, 3)
+            else:
+                v = buf[pos:pos + a.size].view(a.shape)
             v.copy_(torch.from_numpy(a))
             views.append(v)
             pos += a.size
         copies.append((buf, views))
     return copies
+
+
+def measure_forward(w, device, stream, steps, warmup, layout="level_outermost",
+                    adjoint=False):
+    """Device time of the batched forward (and optionally the adjoint) of a
+    workload with rotating field copies; returns a dict of numbers."""
+    from paper_2605_14780_gb300 import bc
+    esize = 4 if w["dtype"] == "f32" else 8
+    field_bytes = sum(a.size for a in w["fields"]) * esize
+    ncopies = int(min(8, max(2, np.ceil(3 * 256e6 / field_bytes) + 1)))
+    copies = field_copies(w, ncopies, device, layout)
+    plan = bc.plan_for_workload(w, copies[0][1])
+    tables = [bc.slot_table(v) for _, v in copies]
+    st = plan.stats()
+    hbm, _ = measured_peaks()
+    gs = [capture(lambda t=t: plan.apply(t, stream=stream), stream) for t in tables]
+    per, tot = time_steps([g.replay for g in gs], steps, warmup, stream, 1)
+    ms = tot / steps
+    out = {"ghost_values": int(st["ghost_values"]), "ms": ms,
+           "ghost_values_per_s": st["ghost_values"] / (ms / 1e3),
+           "algorithmic_bytes": int(st["bytes_fwd"]),
+           "useful_gbs": st["bytes_fwd"] / (ms / 1e3) / 1e9,
+           "frac_of_measured_hbm": st["bytes_fwd"] / (ms / 1e3) / 1e9 / hbm,
+           "layout": layout, "field_copies": ncopies}
+    del gs
+    if adjoint:
+        ga = [capture(lambda t=t: plan.adjoint(t, stream=stream), stream) for t in tables]
+        per, tot = time_steps([g.replay for g in ga], steps, warmup, stream, 1)
+        ams = tot / steps
+        out["adjoint"] = {"ms": ams, "ghost_values_per_s": st["ghost_values"] / (ams / 1e3),
+                          "algorithmic_bytes": int(st["bytes_adj"]),
+                          "useful_gbs": st["bytes_adj"] / (ams / 1e3) / 1e9,
+                          "frac_of_measured_hbm": st["bytes_adj"] / (ams / 1e3) / 1e9 / hbm,
+                          "launches_per_step": 2}
+        del ga
+    del copies, tables, plan
+    import torch
+    torch.cuda.empty_cache()
+    return out
 
 
 def capture(fn, stream):
@@ -326,7 +379,8 @@ def run_ours(args, rank, world, local):
     sampler = ClockSampler(local)
     sampler.start()
     per, total = time_steps([g.replay for g in g_batched], args.steps,
-                            args.warmup, stream, world, min_warm_s=1.0)
+                            args.warmup, stream, world,
+                            min_warm_s=args.min_warm_s)
     clocks = sampler.stop()
     t_step = total / args.steps
     t_max = reduce_max(total, world, device)
@@ -337,7 +391,7 @@ def run_ours(args, rank, world, local):
 
     # -- baselines: per-kind and per-sub-matrix launches ---------------------
     forms = {"batched": {"ms": t_step, "launches_per_step": 1}}
-    for name, form, nsteps in (("typewide", bc.BC_FORM_TYPEWIDE, min(args.steps, 200)),
+    for name, form, nsteps in [] if args.only_batched else (("typewide", bc.BC_FORM_TYPEWIDE, min(args.steps, 200)),
                                ("per_bc", bc.BC_FORM_PER_BC, min(args.steps, 20))):
         gs = graphs_for(form)
         p2, tot2 = time_steps([g.replay for g in gs], nsteps, 3, stream, world)
@@ -345,8 +399,9 @@ def run_ours(args, rank, world, local):
         forms[name] = {"ms": tot2 / nsteps, "launches_per_step": int(nl),
                        "ghost_values_per_s": nvals / (tot2 / nsteps / 1e3)}
         del gs
-    forms["speedup_batched_vs_per_bc"] = forms["per_bc"]["ms"] / t_step
-    forms["speedup_batched_vs_typewide"] = forms["typewide"]["ms"] / t_step
+    if not args.only_batched:
+        forms["speedup_batched_vs_per_bc"] = forms["per_bc"]["ms"] / t_step
+        forms["speedup_batched_vs_typewide"] = forms["typewide"]["ms"] / t_step
 
     # -- end to end through the host-buffer C-ABI call -----------------------
     host = torch.empty(copies[0][0].numel(), dtype=copies[0][0].dtype).pin_memory()
@@ -357,14 +412,16 @@ def run_ours(args, rank, world, local):
         pos += a.size
     hptrs = bc.slot_pointers(hviews)
     dptrs = bc.slot_pointers(copies[0][1])
-    e2e_steps = max(3, min(args.steps, 20))
-    pe, tote = time_steps(
-        [lambda: plan.apply_host(hptrs, dptrs, tables[0], stream=stream)],
-        e2e_steps, 2, stream, world)
-    e2e_ms = reduce_max(tote, world, device) / e2e_steps
-    e2e = {"value": nvals * world / (e2e_ms / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": int(field_bytes),
-           "d2h_bytes_per_step": int(field_bytes)}
+    e2e_steps = 0 if args.only_batched else max(3, min(args.steps, 20))
+    e2e = None
+    if e2e_steps:
+        pe, tote = time_steps(
+            [lambda: plan.apply_host(hptrs, dptrs, tables[0], stream=stream)],
+            e2e_steps, 2, stream, world)
+        e2e_ms = reduce_max(tote, world, device) / e2e_steps
+        e2e = {"value": nvals * world / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(field_bytes),
+               "d2h_bytes_per_step": int(field_bytes), "ms_per_step": e2e_ms}
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -392,6 +449,22 @@ def run_ours(args, rank, world, local):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if not args.only_batched and not args.no_variants:
+        # the same workload with every component stored level-innermost
+        result["layout_variants"] = {"level_innermost": measure_forward(
+            w, device, stream, min(args.steps, 500), 5, "level_innermost")}
+        # the other workloads of the scope table, batched forward (+ adjoint)
+        others = {}
+        for name, fn, adj in (
+                ("tiny_cubed_sphere_6x32", lambda: make_workload_named("tiny"), False),
+                ("hpcg_128_P", lambda: make_workload_named("hpcg"), False),
+                ("swe_cubed_sphere_6x384_L32", lambda: make_workload_named("swe"), False),
+                ("adjoint_cubed_sphere_6x768_L32", lambda: make_workload_named("adjoint"), True)):
+            ww = fn()
+            others[name] = measure_forward(ww, device, stream, min(args.steps, 300), 5,
+                                           adjoint=adj)
+            del ww
+        result["other_workloads"] = others
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = oracle_timing(w)
     if rank == 0:
@@ -408,6 +481,12 @@ def main():
                     choices=["batching", "swe", "adjoint", "hpcg"])
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the layout variant and the other workloads")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="time the batched form only (for profiler runs)")
+    ap.add_argument("--min-warm-s", type=float, default=1.0,
+                    help="minimum seconds of warm-up before the timed steps")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

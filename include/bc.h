@@ -171,10 +171,13 @@ typedef struct bc_submatrix {
 
 /* Plan options; a zero-filled struct (or NULL) selects the defaults. */
 typedef struct bc_plan_opts {
-  int32_t cells_per_item;  /* cells of one work item (default 256)          */
-  int32_t levels_per_item; /* levels of one work item (default 16)          */
-  int32_t threads;         /* threads per CTA (default 256)                 */
-  int32_t ctas_per_sm;     /* persistent CTAs per SM; 0 = one CTA per item  */
+  int32_t units_per_lane;  /* work per lane of one warp item: 8-level units
+                              (or 8 single-level values) (default 4)        */
+  int32_t reserved0;
+  int32_t threads;         /* threads per CTA: 32, 64, 128, 256 or 512
+                              (default 256)                                 */
+  int32_t ctas_per_sm;     /* persistent CTAs per SM; 0 = a plain grid with
+                              one warp per work item (default)              */
   int32_t strict_cover;    /* 1: every ghost value must be covered          */
   int32_t no_adjoint;      /* 1: skip the transpose tables                  */
   int32_t reserved[2];
@@ -197,9 +200,8 @@ typedef struct bc_stats {
   int32_t element_size;
   int32_t form_threads;
   int32_t form_ctas_per_sm;
-  int32_t cells_per_item;
-  int32_t levels_per_item;
-  int32_t reserved[3];
+  int32_t units_per_lane;
+  int32_t reserved[4];
 } bc_stats;
 
 /*

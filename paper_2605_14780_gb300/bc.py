@@ -54,7 +54,7 @@ class BcSubmatrix(ctypes.Structure):
 
 
 class BcPlanOpts(ctypes.Structure):
-    _fields_ = [("cells_per_item", c_i32), ("levels_per_item", c_i32),
+    _fields_ = [("units_per_lane", c_i32), ("reserved0", c_i32),
                 ("threads", c_i32), ("ctas_per_sm", c_i32),
                 ("strict_cover", c_i32), ("no_adjoint", c_i32),
                 ("reserved", c_i32 * 2)]
@@ -67,8 +67,8 @@ class BcStats(ctypes.Structure):
                 ("bytes_fwd", c_i64), ("bytes_adj", c_i64),
                 ("table_bytes", c_i64), ("transpose_nnz", c_i64),
                 ("element_size", c_i32), ("form_threads", c_i32),
-                ("form_ctas_per_sm", c_i32), ("cells_per_item", c_i32),
-                ("levels_per_item", c_i32), ("reserved", c_i32 * 3)]
+                ("form_ctas_per_sm", c_i32), ("units_per_lane", c_i32),
+                ("reserved", c_i32 * 4)]
 
 
 #: every function the header declares, with (restype, argtypes)

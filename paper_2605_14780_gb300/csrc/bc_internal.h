@@ -7,10 +7,11 @@
 
 namespace bcg {
 
-// Work-item kinds.  A work item is a rectangular run of ghost cells of one
-// basic sub-matrix (one component, or one rotated component pair) times a
-// range of levels: the independent convex pieces the paper instantiates one
-// by one (Sec. IV-C), here executed by one CTA each.
+// Work-item kinds.  A work item is a run of units of one basic sub-matrix
+// (one component, or one rotated component pair); a unit is one ghost cell
+// times a chunk of up to `ch` consecutive levels.  Items are processed by one
+// warp each: these are the independent convex pieces the paper instantiates
+// one by one (Sec. IV-C), sized for a warp.
 enum ItemKind : int32_t {
   IK_ZERO = 0,
   IK_CONST = 1,
@@ -21,45 +22,48 @@ enum ItemKind : int32_t {
   IK_ADJ = 6
 };
 
-// CELL: each thread owns one cell and loops over the item's levels.
-// FLAT: the item is a flat range of (cell, level) values, cell fastest; each
-//       thread handles up to kFlatUnroll of them (used when levels are few).
-enum ItemMode : int32_t { MODE_CELL = 0, MODE_FLAT = 1 };
-
 constexpr int kPMax = 8;         // largest interpolation stencil
-constexpr int kLevelUnroll = 8;  // levels in flight per thread (CELL mode)
-constexpr int kFlatUnroll = 8;   // values in flight per thread (FLAT mode)
+constexpr int kChunk = 8;        // levels of one unit (blocks with >= 8 levels)
+constexpr int kFlatUnroll = 8;   // single-level units in flight per lane
+constexpr int kUnitsPerWarp = 4; // 8-level units per lane and item
 constexpr int kFlagSnap = 1;     // interpolation row is a unit copy of node 0
 
+// Division of n < 2^31 by an invariant d >= 1: q = (umulhi(n, m) + n) >> s
+// with s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1.
+struct FastDiv {
+  uint32_t d, m;
+  int32_t s;
+};
+
 struct alignas(16) Item {
-  int32_t kind, mode;
-  int32_t ncell, q0;       // CELL: cells [q0, q0+ncell); FLAT: flat values
-  int32_t l0, nlev;        // level range
+  int32_t kind;
+  int32_t ch;              // levels per unit: 1 (flat) or kChunk
+  int32_t u0, nunits;      // units [u0, u0 + nunits) of the unit space
+  FastDiv vol;             // cells (rows) of the sub-matrix box / row group
+  FastDiv w0, w1;          // box extents on axes 0 and 1
+  int32_t L;               // levels of the block
   int32_t dst_slot, dst_slot2;
   int32_t src_slot, p;
-  int32_t W0, W1;          // extents of the sub-matrix box, axes 0 and 1
-  int32_t vol;             // cells of the sub-matrix box
   int32_t table;           // first table row of cell 0 of this component
   int32_t comp, comp2;     // INTERP: source components (pair: u, v)
-  int64_t dst_org;         // dst offset of the box origin, level 0
-  int64_t dst_s0, dst_s1, dst_s2, dst_ls;
-  int64_t src_org;         // MAP: src offset of the image of the origin
-  int64_t src_s0, src_s1, src_s2, src_ls;
+  int32_t dst_org, dst_s0, dst_s1, dst_s2, dst_ls;   // element offsets
+  int32_t src_org, src_s0, src_s1, src_s2, src_ls;   // MAP source
+  int32_t pad[1];
 };
 static_assert(sizeof(Item) % 16 == 0, "Item must be a multiple of 16 bytes");
-constexpr int kItemWords = sizeof(Item) / 4;
 
 // Device-side view of a plan (passed by value to every kernel).
 struct Ctx {
   void* const* slots;       // caller's device array of slot pointers
-  const int64_t* slot_ls;   // level stride of every slot
+  const int32_t* slot_ls;   // level stride of every slot (elements)
   // interpolation: per table row {slot_base of source block, node-0 offset,
   // node step, flags}, weights [row][kPMax], rotation [row][4]
   const int4* itp_idx;
   const void* itp_w;
   const void* itp_m;
-  // CSR rows (global row numbering), entries, per-row constant
-  const int64_t* csr_ptr;
+  // CSR rows (global row numbering): entry count per row, ELL entries
+  // (a row's entries start at item.src_org + q * item.p), per-row constant
+  const int32_t* csr_nnz;
   const int32_t* csr_slot;
   const int32_t* csr_off;
   const void* csr_val;
@@ -77,8 +81,10 @@ struct Ctx {
 };
 
 // Launchers (kernels.cu).  dtype: 0 = float, 1 = double.
+// One warp per item; `threads` per CTA (a multiple of 32).
 cudaError_t launch_items(int dtype, const Ctx& ctx, const Item* items,
                          int nitems, int threads, cudaStream_t s);
+// Persistent: `grid` CTAs whose warps claim items from counter[0].
 cudaError_t launch_persistent(int dtype, const Ctx& ctx, const Item* items,
                               int nitems, int threads, int grid,
                               unsigned* counter, cudaStream_t s);

@@ -57,6 +57,7 @@ struct Sub {
   int perm[3] = {0, 1, 2}, sign[3] = {1, 1, 1}, offset[3] = {0, 0, 0};
   int p = 0, geometry = 0, rot_u = -1, rot_v = -1;
   int table = 0;  // CONST/CSR: first row of comp 0; INTERP: first cell row
+  int ell_base = 0, ell_w = 1;  // CSR: ELL entries of row 0, row width
 };
 
 struct ExplicitRows {
@@ -94,14 +95,15 @@ struct bc_plan {
   int dtype = 0, esize = 4;
   std::vector<bc_block> blocks;
   std::vector<int32_t> slot_base, slot_block;
-  std::vector<int64_t> slot_ls;
+  std::vector<int32_t> slot_ls;
   int nslots = 0;
   std::vector<Sub> subs;
   ExplicitRows rows;  // level 0, in sub-matrix order
   // host tables (FP64 copies)
   std::vector<int4> itp_idx;
   std::vector<double> itp_w, itp_m;
-  std::vector<int64_t> csr_ptr{0};
+  // user CSR rows stored as ELL blocks (one width per sub-matrix)
+  std::vector<int32_t> csr_nnz;
   std::vector<int32_t> csr_slot, csr_off;
   std::vector<double> csr_val, csr_rhs;
   std::vector<double> const_val;
@@ -113,12 +115,14 @@ struct bc_plan {
   bool has_adjoint = false;
   // work lists
   std::vector<Item> items, adj_items, adj_zero;
+  std::vector<Item> items_batched;  // the same items in sub-matrix order
   std::vector<int> sub_begin, sub_end;
   int type_begin[5] = {0, 0, 0, 0, 0}, type_end[5] = {0, 0, 0, 0, 0};
   // device
   DevBuf tables, work;
   Ctx ctx{};
   Item* d_items = nullptr;
+  Item* d_batched = nullptr;
   Item* d_adj = nullptr;
   Item* d_adj_zero = nullptr;
   unsigned* d_counter = nullptr;
@@ -161,14 +165,15 @@ bc_status validate_grid(const bc_grid* g, bc_plan* P) {
     if (B.nlevels > 1 && B.level_stride < 1)
       return fail(BC_ERR_INVALID_ARG, "block %d: level_stride < 1", b);
     const int64_t maxoff = cell_offset(B, B.n[0] + B.h[0] - 1, B.n[1] + B.h[1] - 1,
-                                       B.n[2] + B.h[2] - 1);
-    if (maxoff >= (int64_t(1) << 31))
+                                       B.n[2] + B.h[2] - 1) +
+                           (int64_t)(B.nlevels - 1) * (B.nlevels > 1 ? B.level_stride : 0);
+    if (maxoff >= (int64_t(1) << 31) - 1)
       return fail(BC_ERR_UNSUPPORTED,
-                  "block %d: one level of one component spans >= 2^31 elements", b);
+                  "block %d: one component spans >= 2^31 elements", b);
     P->slot_base.push_back((int32_t)slots);
     for (int c = 0; c < B.ncomp; ++c) {
       P->slot_block.push_back(b);
-      P->slot_ls.push_back(B.nlevels > 1 ? B.level_stride : 0);
+      P->slot_ls.push_back((int32_t)(B.nlevels > 1 ? B.level_stride : 0));
     }
     slots += B.ncomp;
     if (slots > (1 << 24)) return fail(BC_ERR_UNSUPPORTED, "too many slots");
@@ -326,7 +331,17 @@ bc_status add_csr(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
   for (int64_t r = 0; r < nrows; ++r)
     if (m.row_ptr[r + 1] < m.row_ptr[r])
       return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: row_ptr not monotone", idx);
-  s.table = (int)(P->csr_ptr.size() - 1);
+  s.table = (int)P->csr_nnz.size();
+  // ELL width of this sub-matrix: its longest row
+  int64_t w = 1;
+  for (int64_t r = 0; r < nrows; ++r) w = std::max<int64_t>(w, m.row_ptr[r + 1] - m.row_ptr[r]);
+  if (w * nrows > (int64_t(1) << 30))
+    return fail(BC_ERR_UNSUPPORTED, "sub-matrix %d: CSR rows too long", idx);
+  s.ell_w = (int)w;
+  s.ell_base = (int)P->csr_slot.size();
+  P->csr_slot.resize(P->csr_slot.size() + nrows * w, 0);
+  P->csr_off.resize(P->csr_off.size() + nrows * w, 0);
+  P->csr_val.resize(P->csr_val.size() + nrows * w, 0.0);
   for (size_t c = 0; c < s.comps.size(); ++c) {
     const int slot = P->slot_base[s.block] + s.comps[c];
     bc_status st = BC_OK;
@@ -363,13 +378,14 @@ bc_status add_csr(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
         const int cs = P->slot_base[cb] + cc;
         const int64_t co = cell_offset(C, ci, cj, ck);
         P->rows.entry(cs, co, m.val[e]);
-        P->csr_slot.push_back(cs);
-        P->csr_off.push_back((int32_t)co);
-        P->csr_val.push_back(m.val[e]);
+        const int64_t pos = s.ell_base + r * w + (e - m.row_ptr[r]);
+        P->csr_slot[pos] = cs;
+        P->csr_off[pos] = (int32_t)co;
+        P->csr_val[pos] = m.val[e];
       }
       P->rows.end_row();
       P->csr_rhs.push_back(b);
-      P->csr_ptr.push_back((int64_t)P->csr_val.size());
+      P->csr_nnz.push_back((int32_t)(m.row_ptr[r + 1] - m.row_ptr[r]));
     });
     if (st != BC_OK) return st;
   }
@@ -561,57 +577,59 @@ bc_status run_cubed_sphere(bc_plan* P, const std::vector<const bc_submatrix*>& c
 }
 
 // -- work lists ----------------------------------------------------------------
+FastDiv make_div(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.s = 0;
+  while ((uint64_t(1) << f.s) < d) ++f.s;
+  f.m = (uint32_t)((((uint64_t(1) << 32) * ((uint64_t(1) << f.s) - d)) / d) + 1);
+  return f;
+}
+
 void item_common(const bc_plan* P, const Sub& s, int comp, Item& it) {
   const bc_block& B = P->blocks[s.block];
   it.dst_slot = P->slot_base[s.block] + comp;
   it.dst_slot2 = -1;
-  it.W0 = s.W[0];
-  it.W1 = s.W[1];
-  it.vol = s.vol;
-  it.dst_org = cell_offset(B, s.lo[0], s.lo[1], s.lo[2]);
-  it.dst_s0 = B.stride[0];
-  it.dst_s1 = B.stride[1];
-  it.dst_s2 = B.stride[2];
-  it.dst_ls = B.nlevels > 1 ? B.level_stride : 0;
+  it.src_slot = -1;
+  it.vol = make_div((uint32_t)s.vol);
+  it.w0 = make_div((uint32_t)s.W[0]);
+  it.w1 = make_div((uint32_t)s.W[1]);
+  it.L = B.nlevels;
+  it.dst_org = (int32_t)cell_offset(B, s.lo[0], s.lo[1], s.lo[2]);
+  it.dst_s0 = (int32_t)B.stride[0];
+  it.dst_s1 = (int32_t)B.stride[1];
+  it.dst_s2 = (int32_t)B.stride[2];
+  it.dst_ls = (int32_t)(B.nlevels > 1 ? B.level_stride : 0);
 }
 
-void emit_cells(std::vector<Item>& out, const Item& proto, int ncells, int nlev, int cells_per,
-                int lev_per) {
-  for (int l0 = 0; l0 < nlev; l0 += lev_per)
-    for (int q0 = 0; q0 < ncells; q0 += cells_per) {
-      Item it = proto;
-      it.mode = MODE_CELL;
-      it.q0 = q0;
-      it.ncell = std::min(cells_per, ncells - q0);
-      it.l0 = l0;
-      it.nlev = std::min(lev_per, nlev - l0);
-      out.push_back(it);
-    }
-}
-
-void emit_flat(std::vector<Item>& out, const Item& proto, int ncells, int nlev, int per) {
-  const int64_t total = (int64_t)ncells * nlev;
-  for (int64_t f0 = 0; f0 < total; f0 += per) {
+// split the unit space [0, vol * ceil(L / ch)) into warp-sized items
+void emit_units(std::vector<Item>& out, Item proto, int vol, int L, int ch, int per_item) {
+  proto.ch = ch;
+  const int64_t total = (int64_t)vol * ((L + ch - 1) / ch);
+  for (int64_t u0 = 0; u0 < total; u0 += per_item) {
     Item it = proto;
-    it.mode = MODE_FLAT;
-    it.q0 = (int)f0;
-    it.ncell = (int)std::min<int64_t>(per, total - f0);
-    it.l0 = 0;
-    it.nlev = nlev;
+    it.u0 = (int)u0;
+    it.nunits = (int)std::min<int64_t>(per_item, total - u0);
     out.push_back(it);
   }
 }
 
 void build_items(bc_plan* P) {
-  const int threads = P->opts.threads;
-  const int cells_per = std::min(P->opts.cells_per_item, threads);
-  const int lev_per = P->opts.levels_per_item;
+  // units per warp item: single-level values (flat) or 8-level chunks
+  const int upl = std::max(1, std::min(P->opts.units_per_lane, 64));
+  const int per_chunk_item = 32 * upl;
+  const int per_flat_item = 32 * kFlatUnroll * upl;
+  // table-driven kinds (interpolation, CSR, transpose): one unit per lane, so
+  // a warp's dependent table -> data chains run side by side, not in series
+  const int per_table_item = 32;
   std::vector<std::pair<int, std::vector<Item>>> per_sub(P->subs.size());
   for (size_t si = 0; si < P->subs.size(); ++si) {
     const Sub& s = P->subs[si];
     const bc_block& B = P->blocks[s.block];
     std::vector<Item>& out = per_sub[si].second;
     per_sub[si].first = s.kind;
+    const int L = B.nlevels;
+    const int chl = std::min(L, kChunk);
     for (size_t ci = 0; ci < s.comps.size(); ++ci) {
       const int c = s.comps[ci];
       Item it{};
@@ -628,18 +646,18 @@ void build_items(bc_plan* P) {
             int img[3];
             const int lo[3] = {s.lo[0], s.lo[1], s.lo[2]};
             for (int d = 0; d < 3; ++d) img[d] = s.sign[d] * lo[s.perm[d]] + s.offset[d];
-            it.src_org = cell_offset(S, img[0], img[1], img[2]);
+            it.src_org = (int32_t)cell_offset(S, img[0], img[1], img[2]);
             int64_t st[3] = {0, 0, 0};
             for (int d = 0; d < 3; ++d) st[s.perm[d]] = s.sign[d] * S.stride[d];
-            it.src_s0 = st[0];
-            it.src_s1 = st[1];
-            it.src_s2 = st[2];
-            it.src_ls = S.nlevels > 1 ? S.level_stride : 0;
+            it.src_s0 = (int32_t)st[0];
+            it.src_s1 = (int32_t)st[1];
+            it.src_s2 = (int32_t)st[2];
+            it.src_ls = (int32_t)(S.nlevels > 1 ? S.level_stride : 0);
           }
-          if (B.nlevels < kLevelUnroll)
-            emit_flat(out, it, s.vol, B.nlevels, threads * kFlatUnroll);
+          if (L < kChunk)
+            emit_units(out, it, s.vol, L, 1, per_flat_item);
           else
-            emit_cells(out, it, s.vol, B.nlevels, cells_per, lev_per);
+            emit_units(out, it, s.vol, L, kChunk, per_chunk_item);
           break;
         }
         case BC_INTERP: {
@@ -654,13 +672,15 @@ void build_items(bc_plan* P) {
           } else {
             it.kind = IK_INTERP;
           }
-          emit_cells(out, it, s.vol, B.nlevels, cells_per, lev_per);
+          emit_units(out, it, s.vol, L, chl, per_table_item);
           break;
         }
         case BC_CSR: {
           it.kind = IK_CSR;
           it.table = s.table + (int)ci * s.vol;
-          emit_cells(out, it, s.vol, B.nlevels, cells_per, lev_per);
+          it.p = s.ell_w;
+          it.src_org = s.ell_base + (int)ci * s.vol * s.ell_w;
+          emit_units(out, it, s.vol, L, chl, per_table_item);
           break;
         }
       }
@@ -680,16 +700,25 @@ void build_items(bc_plan* P) {
     }
     P->type_end[kind] = (int)P->items.size();
   }
+  // batched launch: sub-matrix order, so the kinds (loads + stores, stores
+  // only, table gathers) are interleaved over the grid
+  P->items_batched.clear();
+  for (size_t si = 0; si < P->subs.size(); ++si)
+    P->items_batched.insert(P->items_batched.end(), per_sub[si].second.begin(),
+                            per_sub[si].second.end());
   // adjoint: the zero pass over every covered ghost value
   P->adj_zero.clear();
-  for (const Item& f : P->items) {
-    Item z = f;
-    z.kind = IK_ZERO;
-    z.dst_slot2 = -1;
-    P->adj_zero.push_back(z);
-    if (f.kind == IK_INTERP_PAIR) {
-      z.dst_slot = f.dst_slot2;
-      P->adj_zero.push_back(z);
+  for (size_t si = 0; si < P->subs.size(); ++si) {
+    const Sub& s = P->subs[si];
+    const int L = P->blocks[s.block].nlevels;
+    for (int c : s.comps) {
+      Item z{};
+      item_common(P, s, c, z);
+      z.kind = IK_ZERO;
+      if (L < kChunk)
+        emit_units(P->adj_zero, z, s.vol, L, 1, per_flat_item);
+      else
+        emit_units(P->adj_zero, z, s.vol, L, kChunk, per_chunk_item);
     }
   }
   // adjoint gather items over the transpose rows, grouped by level count
@@ -699,19 +728,15 @@ void build_items(bc_plan* P) {
   while (r0 < nar) {
     const int L = P->blocks[P->slot_block[P->arow_slot[r0]]].nlevels;
     int r1 = r0;
-    while (r1 < nar && r1 - r0 < cells_per &&
-           P->blocks[P->slot_block[P->arow_slot[r1]]].nlevels == L)
-      ++r1;
-    for (int l0 = 0; l0 < L; l0 += lev_per) {
-      Item it{};
-      it.kind = IK_ADJ;
-      it.mode = MODE_CELL;
-      it.q0 = r0;
-      it.ncell = r1 - r0;
-      it.l0 = l0;
-      it.nlev = std::min(lev_per, L - l0);
-      P->adj_items.push_back(it);
-    }
+    while (r1 < nar && P->blocks[P->slot_block[P->arow_slot[r1]]].nlevels == L) ++r1;
+    Item it{};
+    it.kind = IK_ADJ;
+    it.vol = make_div((uint32_t)(r1 - r0));
+    it.w0 = make_div(1);
+    it.w1 = make_div(1);
+    it.L = L;
+    it.table = r0;
+    emit_units(P->adj_items, it, r1 - r0, L, std::min(L, kChunk), per_table_item);
     r0 = r1;
   }
 }
@@ -780,11 +805,11 @@ void put_raw(std::vector<char>& host, size_t off, const std::vector<V>& v) {
 bc_status upload_tables(bc_plan* P) {
   const size_t S = P->esize;
   Layout L;
-  const size_t o_ls = L.take(P->slot_ls.size() * 8);
+  const size_t o_ls = L.take(P->slot_ls.size() * 4);
   const size_t o_idx = L.take(P->itp_idx.size() * sizeof(int4));
   const size_t o_w = L.take(P->itp_w.size() * S);
   const size_t o_m = L.take(P->itp_m.size() * S);
-  const size_t o_cp = L.take(P->csr_ptr.size() * 8);
+  const size_t o_cp = L.take(P->csr_nnz.size() * 4);
   const size_t o_cs = L.take(P->csr_slot.size() * 4);
   const size_t o_co = L.take(P->csr_off.size() * 4);
   const size_t o_cv = L.take(P->csr_val.size() * S);
@@ -799,7 +824,7 @@ bc_status upload_tables(bc_plan* P) {
   std::vector<char> host(L.off + 256, 0);
   put_raw(host, o_ls, P->slot_ls);
   put_raw(host, o_idx, P->itp_idx);
-  put_raw(host, o_cp, P->csr_ptr);
+  put_raw(host, o_cp, P->csr_nnz);
   put_raw(host, o_cs, P->csr_slot);
   put_raw(host, o_co, P->csr_off);
   put_raw(host, o_as, P->arow_slot);
@@ -832,11 +857,11 @@ bc_status upload_tables(bc_plan* P) {
   if (e != cudaSuccess) return cuda_fail(e, "device tables upload");
   char* b = static_cast<char*>(P->tables.base);
   Ctx& c = P->ctx;
-  c.slot_ls = reinterpret_cast<const int64_t*>(b + o_ls);
+  c.slot_ls = reinterpret_cast<const int32_t*>(b + o_ls);
   c.itp_idx = reinterpret_cast<const int4*>(b + o_idx);
   c.itp_w = b + o_w;
   c.itp_m = b + o_m;
-  c.csr_ptr = reinterpret_cast<const int64_t*>(b + o_cp);
+  c.csr_nnz = reinterpret_cast<const int32_t*>(b + o_cp);
   c.csr_slot = reinterpret_cast<const int32_t*>(b + o_cs);
   c.csr_off = reinterpret_cast<const int32_t*>(b + o_co);
   c.csr_val = b + o_cv;
@@ -858,11 +883,13 @@ bc_status upload_work(bc_plan* P) {
   }
   Layout L;
   const size_t o_i = L.take(P->items.size() * sizeof(Item));
+  const size_t o_b = L.take(P->items_batched.size() * sizeof(Item));
   const size_t o_a = L.take(P->adj_items.size() * sizeof(Item));
   const size_t o_z = L.take(P->adj_zero.size() * sizeof(Item));
   const size_t o_c = L.take(2 * sizeof(unsigned));
   std::vector<char> host(L.off + 256, 0);
   put_raw(host, o_i, P->items);
+  put_raw(host, o_b, P->items_batched);
   put_raw(host, o_a, P->adj_items);
   put_raw(host, o_z, P->adj_zero);
   cudaError_t e = cudaMalloc(&P->work.base, host.size());
@@ -875,6 +902,7 @@ bc_status upload_work(bc_plan* P) {
   if (e != cudaSuccess) return cuda_fail(e, "device work list upload");
   char* b = static_cast<char*>(P->work.base);
   P->d_items = reinterpret_cast<Item*>(b + o_i);
+  P->d_batched = reinterpret_cast<Item*>(b + o_b);
   P->d_adj = reinterpret_cast<Item*>(b + o_a);
   P->d_adj_zero = reinterpret_cast<Item*>(b + o_z);
   P->d_counter = reinterpret_cast<unsigned*>(b + o_c);
@@ -936,19 +964,18 @@ void compute_stats(bc_plan* P) {
   st.element_size = P->esize;
   st.form_threads = P->opts.threads;
   st.form_ctas_per_sm = P->opts.ctas_per_sm;
-  st.cells_per_item = P->opts.cells_per_item;
-  st.levels_per_item = P->opts.levels_per_item;
+  st.units_per_lane = P->opts.units_per_lane;
 }
 
 bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
   std::memset(&o, 0, sizeof(o));
   if (in) o = *in;
-  if (o.threads == 0) o.threads = 256;
-  if (o.threads != 128 && o.threads != 256 && o.threads != 512)
-    return fail(BC_ERR_INVALID_ARG, "threads must be 128, 256 or 512");
-  if (o.cells_per_item == 0) o.cells_per_item = o.threads;
-  if (o.levels_per_item == 0) o.levels_per_item = 16;
-  if (o.cells_per_item < 1 || o.levels_per_item < 1 || o.ctas_per_sm < 0)
+  if (o.threads == 0) o.threads = 128;
+  if (o.threads != 32 && o.threads != 64 && o.threads != 128 && o.threads != 256 &&
+      o.threads != 512)
+    return fail(BC_ERR_INVALID_ARG, "threads must be 32, 64, 128, 256 or 512");
+  if (o.units_per_lane == 0) o.units_per_lane = 4;
+  if (o.units_per_lane < 1 || o.ctas_per_sm < 0)
     return fail(BC_ERR_INVALID_ARG, "bad work-item options");
   return BC_OK;
 }
@@ -1060,10 +1087,10 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
   const int T = P->opts.threads;
   if (form == BC_FORM_BATCHED) {
     if (P->opts.ctas_per_sm > 0)
-      e = launch_persistent(P->dtype, c, P->d_items, (int)P->items.size(), T,
+      e = launch_persistent(P->dtype, c, P->d_batched, (int)P->items_batched.size(), T,
                             P->opts.ctas_per_sm * P->num_sms, P->d_counter, s);
     else
-      e = launch_items(P->dtype, c, P->d_items, (int)P->items.size(), T, s);
+      e = launch_items(P->dtype, c, P->d_batched, (int)P->items_batched.size(), T, s);
   } else if (form == BC_FORM_TYPEWIDE) {
     for (int k = 0; k < 5 && e == cudaSuccess; ++k)
       e = launch_items(P->dtype, c, P->d_items + P->type_begin[k],
@@ -1208,16 +1235,16 @@ bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) 
     return BC_OK;
   };
   const int threads_c[] = {128, 256, 512};
-  const int levels_c[] = {8, 16, 32, 64};
-  const int ctas_c[] = {0, 2, 4, 8};
+  const int units_c[] = {1, 2, 4, 8};
+  const int warps_c[] = {0, 16, 32, 48, 64};  // persistent warps per SM
   bc_status st = BC_OK;
   for (int T : threads_c) {
-    for (int Lp : levels_c) {
-      for (int cps : ctas_c) {
-        if (cps * T > 2048 || st != BC_OK) continue;
+    for (int U : units_c) {
+      for (int wps : warps_c) {
+        const int cps = wps * 32 / T;
+        if (st != BC_OK || (wps > 0 && cps < 1)) continue;
         plan->opts.threads = T;
-        plan->opts.cells_per_item = T;
-        plan->opts.levels_per_item = Lp;
+        plan->opts.units_per_lane = U;
         plan->opts.ctas_per_sm = cps;
         float med = 0;
         st = time_candidate(med);

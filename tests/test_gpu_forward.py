@@ -60,9 +60,10 @@ def test_forms_bit_identical(form):
 
 
 @pytest.mark.parametrize("opts", [
-    {"ctas_per_sm": 2, "threads": 128, "levels_per_item": 8},
-    {"ctas_per_sm": 4, "threads": 256, "levels_per_item": 64},
-    {"ctas_per_sm": 1, "threads": 512, "levels_per_item": 3, "cells_per_item": 37},
+    {"ctas_per_sm": 2, "threads": 128, "units_per_lane": 1},
+    {"ctas_per_sm": 4, "threads": 256, "units_per_lane": 8},
+    {"ctas_per_sm": 1, "threads": 512, "units_per_lane": 3},
+    {"ctas_per_sm": 0, "threads": 128, "units_per_lane": 64},
 ])
 def test_persistent_and_item_shapes(opts):
     """Persistent grid with an atomic work counter, repeated launches (the
