@@ -281,6 +281,51 @@ bc_status bc_plan_export_csr(const bc_plan* plan, int64_t* nrows,
                              int32_t* col_slot, int64_t* col_off,
                              double* val, double* rhs);
 
+/*
+ * Cubed-sphere interpolation stencils without any device allocation.
+ *
+ * The paper has no counterpart: this is a convenience for callers that cannot
+ * call cudaMalloc -- code running while a stream capture in global mode is
+ * active, or inside a framework that owns all device memory through its own
+ * pool and forbids raw allocations.  bc_plan_create allocates device tables
+ * and staging buffers, so such callers cannot build a plan at that moment;
+ * this call still gives them the rows the plan's GPU geometry kernel would
+ * generate for BC_GEOM_CUBED_SPHERE sub-matrices (same FP64 geometry, same
+ * snapping and stencil rules), written to HOST arrays.
+ *
+ * The kernel's scratch (results and an error word) lives in one fixed device
+ * array inside the library, sized for BC_NOALLOC_MAX_CELLS cells (about
+ * 7.3 MB); every GPU that loads the library holds it until the process
+ * exits.  The call allocates nothing else on the device.
+ *
+ * Cells: the edge ghosts of six N x N panels with halo h, in the order
+ * panel 0..5, strip (axis-0 low, axis-0 high, axis-1 low, axis-1 high), depth
+ * 0..h-1 (0 next to the data), along index 0..N-1; ncells = 24 * N * h.
+ * Outputs (host arrays) for cell c:
+ *   nb[c]            neighbour panel 0..5
+ *   node0[2c], node0[2c+1]   (i, j) data cell of stencil node 0 on nb[c]
+ *   axis[c]          axis of nb[c] the nodes step along (+1 per node); the
+ *                    bit BC_NOALLOC_SNAP marks a unit copy of node 0
+ *   w[p*c .. p*c+p-1]  Lagrange weights (FP64)
+ *   rot[4c .. 4c+3]  2x2 change of covariant vector components, row-major
+ *                    (filled only when rot is not NULL)
+ * Errors: BC_ERR_INVALID_ARG (p outside 1..8, h < 1, N < p, h > N, NULL
+ * output), BC_ERR_UNSUPPORTED (24*N*h > BC_NOALLOC_MAX_CELLS),
+ * BC_ERR_GEOMETRY, BC_ERR_CUDA.
+ * Synchronous on the legacy default stream of the current device.  The
+ * first call on a device looks up the scratch array's device address there;
+ * make that first call before any stream capture begins.  All calls share
+ * the one scratch array and it keeps the last call's results: calls that
+ * overlap on the GPU (several host threads, or processes sharing a context)
+ * race with each other.
+ */
+#define BC_NOALLOC_MAX_CELLS 65536
+#define BC_NOALLOC_SNAP 0x100
+bc_status bc_cubed_sphere_stencils_noalloc(int32_t N, int32_t h, int32_t p,
+                                           int32_t* nb, int32_t* node0,
+                                           int32_t* axis, double* w,
+                                           double* rot);
+
 /* Release the plan and its device tables (NULL is a no-op). */
 void bc_plan_destroy(bc_plan* plan);
 

@@ -85,6 +85,8 @@ SIGNATURES = {
     "bc_plan_stats": (c_i32, [c_vp, ctypes.POINTER(BcStats)]),
     "bc_plan_export_csr": (c_i32, [c_vp, P_i64, P_i64, P_i32, P_i64, P_i64,
                                    P_i32, P_i64, P_dbl, P_dbl]),
+    "bc_cubed_sphere_stencils_noalloc": (c_i32, [c_i32, c_i32, c_i32, P_i32, P_i32,
+                                                 P_i32, P_dbl, P_dbl]),
     "bc_plan_destroy": (None, [c_vp]),
     "bc_status_string": (ctypes.c_char_p, [c_i32]),
     "bc_last_error": (ctypes.c_char_p, []),
@@ -354,3 +356,26 @@ class BCFill:
     @classmethod
     def apply(cls, plan, *fields):
         return cls.function().apply(plan, *fields)
+
+
+NOALLOC_MAX_CELLS = 65536
+NOALLOC_SNAP = 0x100
+
+
+def cubed_sphere_stencils_noalloc(N, h, p, rotate=True):
+    """Cubed-sphere edge stencils from the library's allocation-free entry
+    point (for callers that cannot allocate device memory); returns host
+    arrays ``nb, node0 (n, 2), axis, w (n, p), rot (n, 2, 2) | None`` in the
+    order panel, strip (axis-0 low/high, axis-1 low/high), depth, along."""
+    lib = load_library()
+    n = 24 * N * h
+    nb = np.zeros(n, np.int32)
+    node0 = np.zeros((n, 2), np.int32)
+    axis = np.zeros(n, np.int32)
+    w = np.zeros((n, p), np.float64)
+    rot = np.zeros((n, 2, 2), np.float64) if rotate else None
+    _check(lib.bc_cubed_sphere_stencils_noalloc(
+        int(N), int(h), int(p), _ptr(nb, c_i32), _ptr(node0, c_i32),
+        _ptr(axis, c_i32), _ptr(w, c_dbl),
+        _ptr(rot, c_dbl) if rotate else ctypes.POINTER(c_dbl)()))
+    return {"nb": nb, "node0": node0, "axis": axis, "w": w, "rot": rot}

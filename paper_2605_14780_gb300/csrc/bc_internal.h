@@ -101,6 +101,9 @@ cudaError_t launch_cs_geometry(const CsPanels& pan, const int4* cells,
                                int ncells, int4* idx, double* w, double* m,
                                unsigned* err, cudaStream_t s);
 
+// Sets the message bc_last_error() returns on this thread (plan.cpp).
+void set_last_error(const char* msg);
+
 enum CsError : unsigned {
   CS_ERR_NOT_EDGE = 1u,     // a cell is not an edge ghost
   CS_ERR_DEPTH = 2u,        // ghost point is not on a neighbour data row

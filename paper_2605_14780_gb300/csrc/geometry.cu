@@ -16,7 +16,10 @@
 // dtype.
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <mutex>
 
+#include "../../include/bc.h"
 #include "bc_internal.h"
 
 namespace bcg {
@@ -199,4 +202,185 @@ cudaError_t launch_cs_geometry(const CsPanels& pan, const int4* cells,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the geometry kernel (bc_cubed_sphere_stencils_
+// noalloc): the per-cell results and the error word go to one fixed device
+// array instead of buffers the plan allocates.  Layout of the array:
+//   [0, 256)                 error word (cleared by every call)
+//   then, for kNoAllocMax cells: int4 {nb, i0, j0, axis | snap}
+//   then FP64 weights [cell][kPMax], then FP64 rotations [cell][4].
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMax = BC_NOALLOC_MAX_CELLS;
+constexpr size_t kNoAllocIdx = 256;
+constexpr size_t kNoAllocW = kNoAllocIdx + sizeof(int4) * (size_t)kNoAllocMax;
+constexpr size_t kNoAllocM = kNoAllocW + sizeof(double) * kPMax * (size_t)kNoAllocMax;
+constexpr size_t kNoAllocBytes = kNoAllocM + sizeof(double) * 4 * (size_t)kNoAllocMax;
+
+// In host code this name is only a stand-in for the device symbol: host code
+// passes the address cudaGetSymbolAddress returns for the current device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+__global__ void k_cs_stencils_noalloc(int N, int h, int p, int rotate,
+                                      unsigned char* scratch) {
+  const int ncells = 24 * N * h;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ncells) return;
+  unsigned* err = reinterpret_cast<unsigned*>(scratch);
+  int4* idx = reinterpret_cast<int4*>(scratch + kNoAllocIdx);
+  double* wr = reinterpret_cast<double*>(scratch + kNoAllocW) + (int64_t)g * kPMax;
+  double* mr = reinterpret_cast<double*>(scratch + kNoAllocM) + (int64_t)g * 4;
+  // canonical cell order: panel, strip (d, side), depth r, along s
+  const int s = g % N;
+  const int r = (g / N) % h;
+  const int strip = (g / (N * h)) % 4;
+  const int P = g / (4 * N * h);
+  const int d = strip >> 1, side = strip & 1;
+  const int gi = side ? N + r : -1 - r;
+  const int i = d == 0 ? gi : s;
+  const int j = d == 0 ? s : gi;
+  const double pi = 3.14159265358979323846;
+  const double delta = pi / (2.0 * N);
+  for (int n = 0; n < kPMax; ++n) wr[n] = 0.0;
+  mr[0] = 1.0; mr[1] = 0.0; mr[2] = 0.0; mr[3] = 1.0;
+  idx[g] = make_int4(-1, 0, 0, 0);
+  // neighbour's depth axis from the middle of the strip
+  double ref[2] = {0.0, 0.0};
+  ref[d] = (pi / 4 + delta / 2) * (side ? 1.0 : -1.0);
+  const V3 vr = unit_point(P, ref[0], ref[1], nullptr);
+  const int Qr = owner_panel(vr);
+  double ar, br;
+  angles_on(Qr, vr, ar, br);
+  const int dq = fabs(ar) > fabs(br) ? 0 : 1;
+  // the ghost point on the neighbour
+  const double a = -pi / 4 + (i + 0.5) * delta;
+  const double b = -pi / 4 + (j + 0.5) * delta;
+  const V3 v = unit_point(P, a, b, nullptr);
+  const int Q = owner_panel(v);
+  if (Q != Qr || Q == P) {
+    atomicOr(err, (unsigned)CS_ERR_NEIGHBOUR);
+    return;
+  }
+  double aq, bq;
+  angles_on(Q, v, aq, bq);
+  const double fa = (aq + pi / 4) / delta - 0.5;
+  const double fb = (bq + pi / 4) / delta - 0.5;
+  const double fdepth = dq == 0 ? fa : fb;
+  const double t = dq == 0 ? fb : fa;
+  const double rq = rint(fdepth);
+  if (fabs(fdepth - rq) > 1e-9 || rq < 0 || rq > N - 1) {
+    atomicOr(err, (unsigned)CS_ERR_DEPTH);
+    return;
+  }
+  const double tr = rint(t);
+  const bool snap = fabs(t - tr) < 1e-9 && tr >= 0 && tr <= N - 1;
+  int start;
+  if (snap) {
+    start = (int)tr;
+    wr[0] = 1.0;
+  } else {
+    start = (int)floor(t) - (p / 2 - 1);
+    if (start < 0) start = 0;
+    if (start > N - p) start = N - p;
+    const double tau = t - start;
+    for (int k = 0; k < p; ++k) {
+      double acc = 1.0;
+      for (int mm = 0; mm < p; ++mm)
+        if (mm != k) acc *= (tau - mm) / (double)(k - mm);
+      wr[k] = acc;
+    }
+  }
+  const int along = 1 - dq;
+  idx[g] = make_int4(Q, dq == 0 ? (int)rq : start, dq == 0 ? start : (int)rq,
+                     along | (snap ? BC_NOALLOC_SNAP : 0));
+  if (rotate) {
+    V3 ea, eb, qa, qb;
+    basis(P, a, b, ea, eb);
+    basis(Q, aq, bq, qa, qb);
+    const double g11 = dot(qa, qa), g12 = dot(qa, qb), g22 = dot(qb, qb);
+    const double det = g11 * g22 - g12 * g12;
+    const V3 da = scl(1.0 / det, sub(scl(g22, qa), scl(g12, qb)));
+    const V3 db = scl(1.0 / det, sub(scl(g11, qb), scl(g12, qa)));
+    mr[0] = dot(ea, da);
+    mr[1] = dot(ea, db);
+    mr[2] = dot(eb, da);
+    mr[3] = dot(eb, db);
+  }
+}
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {nullptr};  // device address of the array, per device
+
+bc_status noalloc_fail(bc_status st, const char* msg) {
+  set_last_error(msg);
+  return st;
+}
+
+bc_status noalloc_cuda(cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  return noalloc_fail(BC_ERR_CUDA, buf);
+}
+
+}  // namespace
 }  // namespace bcg
+
+extern "C" bc_status bc_cubed_sphere_stencils_noalloc(int32_t N, int32_t h, int32_t p,
+                                                      int32_t* nb, int32_t* node0,
+                                                      int32_t* axis, double* w,
+                                                      double* rot) {
+  using namespace bcg;
+  set_last_error("");
+  if (p < 1 || p > kPMax) return noalloc_fail(BC_ERR_INVALID_ARG, "p must be in 1..8");
+  if (h < 1 || N < p || h > N) return noalloc_fail(BC_ERR_INVALID_ARG, "need 1 <= h <= N and N >= p");
+  if (!nb || !node0 || !axis || !w) return noalloc_fail(BC_ERR_INVALID_ARG, "NULL output array");
+  if ((int64_t)24 * N * h > BC_NOALLOC_MAX_CELLS) {
+    char buf[200];
+    snprintf(buf, sizeof(buf), "24*N*h = %lld edge ghosts exceed the fixed scratch of %d cells",
+             (long long)24 * N * h, BC_NOALLOC_MAX_CELLS);
+    return noalloc_fail(BC_ERR_UNSUPPORTED, buf);
+  }
+  const int ncells = 24 * N * h;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return noalloc_cuda(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 256) return noalloc_fail(BC_ERR_UNSUPPORTED, "device index out of range");
+  unsigned char* scratch = nullptr;
+  {
+    // set-up once per device, with that device current
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess || !ptr) return noalloc_cuda(e, "cudaGetSymbolAddress of the scratch array");
+      g_noalloc_ptr[dev] = ptr;
+    }
+    scratch = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  }
+  // the error word must start at zero; results are fully rewritten
+  if ((e = cudaMemset(scratch, 0, sizeof(unsigned))) != cudaSuccess)
+    return noalloc_cuda(e, "clearing the error word");
+  const int threads = 128;
+  k_cs_stencils_noalloc<<<(ncells + threads - 1) / threads, threads>>>(N, h, p, rot ? 1 : 0, scratch);
+  if ((e = cudaGetLastError()) != cudaSuccess) return noalloc_cuda(e, "stencil kernel launch");
+  unsigned herr = 0;
+  if ((e = cudaMemcpy(&herr, scratch, sizeof(unsigned), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return noalloc_cuda(e, "stencil kernel");
+  if (herr) return noalloc_fail(BC_ERR_GEOMETRY, "cubed sphere: neighbour or depth-row check failed");
+  // scatter the int4 rows into the caller's arrays with strided copies
+  const unsigned char* ix = scratch + kNoAllocIdx;
+  if ((e = cudaMemcpy2D(nb, sizeof(int32_t), ix, sizeof(int4), sizeof(int32_t), ncells,
+                        cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy2D(node0, 2 * sizeof(int32_t), ix + sizeof(int32_t), sizeof(int4),
+                        2 * sizeof(int32_t), ncells, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy2D(axis, sizeof(int32_t), ix + 3 * sizeof(int32_t), sizeof(int4),
+                        sizeof(int32_t), ncells, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy2D(w, p * sizeof(double), scratch + kNoAllocW, kPMax * sizeof(double),
+                        p * sizeof(double), ncells, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return noalloc_cuda(e, "copying the stencils to the host");
+  if (rot && (e = cudaMemcpy(rot, scratch + kNoAllocM, (size_t)ncells * 4 * sizeof(double),
+                             cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return noalloc_cuda(e, "copying the rotations to the host");
+  return BC_OK;
+}

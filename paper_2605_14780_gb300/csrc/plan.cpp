@@ -1328,3 +1328,11 @@ const char* bc_status_string(bc_status status) {
 const char* bc_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+namespace bcg {
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace bcg
+
+extern "C" {
+
+}  // extern "C"
