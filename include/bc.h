@@ -173,7 +173,9 @@ typedef struct bc_submatrix {
 typedef struct bc_plan_opts {
   int32_t units_per_lane;  /* work per lane of one warp item: 8-level units
                               (or 8 single-level values) (default 4)        */
-  int32_t reserved0;
+  int32_t unit_order;      /* 0: auto (levels fastest when they are adjacent
+                              in memory), 1: cells fastest, 2: levels
+                              fastest                                       */
   int32_t threads;         /* threads per CTA: 32, 64, 128, 256 or 512
                               (default 256)                                 */
   int32_t ctas_per_sm;     /* persistent CTAs per SM; 0 = a plain grid with

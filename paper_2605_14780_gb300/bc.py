@@ -54,7 +54,7 @@ class BcSubmatrix(ctypes.Structure):
 
 
 class BcPlanOpts(ctypes.Structure):
-    _fields_ = [("units_per_lane", c_i32), ("reserved0", c_i32),
+    _fields_ = [("units_per_lane", c_i32), ("unit_order", c_i32),
                 ("threads", c_i32), ("ctas_per_sm", c_i32),
                 ("strict_cover", c_i32), ("no_adjoint", c_i32),
                 ("reserved", c_i32 * 2)]

@@ -35,20 +35,27 @@ struct FastDiv {
   int32_t s;
 };
 
+// Unit orders of a work item (Item::mode):
+//   MODE_FLAT_CELL  one value (cell, level) per unit, cell fastest
+//   MODE_FLAT_LEVEL one value per unit, level fastest (levels contiguous in
+//                   memory: lanes of a warp then write one contiguous run)
+//   mode >= 2       a unit is a cell times a chunk of `mode` levels; lanes
+//                   take consecutive cells (levels far apart in memory)
+enum ItemMode : int32_t { MODE_FLAT_CELL = 0, MODE_FLAT_LEVEL = 1 };
+
 struct alignas(16) Item {
   int32_t kind;
-  int32_t ch;              // levels per unit: 1 (flat) or kChunk
+  int32_t mode;            // ItemMode, or the chunk length (>= 2)
   int32_t u0, nunits;      // units [u0, u0 + nunits) of the unit space
   FastDiv vol;             // cells (rows) of the sub-matrix box / row group
   FastDiv w0, w1;          // box extents on axes 0 and 1
-  int32_t L;               // levels of the block
+  FastDiv lev;             // levels of the block (lev.d)
   int32_t dst_slot, dst_slot2;
   int32_t src_slot, p;
   int32_t table;           // first table row of cell 0 of this component
-  int32_t comp, comp2;     // INTERP: source components (pair: u, v)
+  int32_t comp;            // INTERP source components: u | v << 16
   int32_t dst_org, dst_s0, dst_s1, dst_s2, dst_ls;   // element offsets
-  int32_t src_org, src_s0, src_s1, src_s2, src_ls;   // MAP source
-  int32_t pad[1];
+  int32_t src_org, src_s0, src_s1, src_s2, src_ls;   // MAP source; CSR: ELL base
 };
 static_assert(sizeof(Item) % 16 == 0, "Item must be a multiple of 16 bytes");
 
@@ -80,14 +87,18 @@ struct Ctx {
   const void* aent_w;
 };
 
-// Launchers (kernels.cu).  dtype: 0 = float, 1 = double.
-// One warp per item; `threads` per CTA (a multiple of 32).
-cudaError_t launch_items(int dtype, const Ctx& ctx, const Item* items,
-                         int nitems, int threads, cudaStream_t s);
-// Persistent: `grid` CTAs whose warps claim items from counter[0].
-cudaError_t launch_persistent(int dtype, const Ctx& ctx, const Item* items,
-                              int nitems, int threads, int grid,
-                              unsigned* counter, cudaStream_t s);
+// Kernel families: item kinds that share one kernel (and one register
+// budget).  Zero, constant and map items are FAM_STRUCT; interpolation and
+// rotated pairs FAM_INTERP; CSR rows FAM_CSR; the transpose gather FAM_ADJ.
+enum Family : int32_t { FAM_STRUCT = 0, FAM_INTERP = 1, FAM_CSR = 2, FAM_ADJ = 3 };
+constexpr int kFamilies = 4;
+
+// Launcher (kernels.cu).  dtype: 0 = float, 1 = double.  One warp per item,
+// `threads` per CTA (32..512).  grid <= 0: one warp per item; otherwise a
+// persistent grid of `grid` CTAs whose warps claim items from counter[0..1].
+cudaError_t launch_family(int dtype, int family, const Ctx& ctx,
+                          const Item* items, int nitems, int threads, int grid,
+                          unsigned* counter, cudaStream_t s);
 
 // Cubed-sphere geometry (geometry.cu).
 struct CsPanels {

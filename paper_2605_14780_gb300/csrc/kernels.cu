@@ -7,10 +7,13 @@
 // atomic counter.  No warp ever waits on another; there is no CTA barrier.
 //
 // The path is a sparse gather/scatter bounded by HBM bandwidth, so it runs on
-// the CUDA cores: lanes take consecutive ghost cells (coalesced along axis 0),
-// each lane keeps 8 independent levels (or 8 single-level values) in flight,
-// copies move integer bit patterns so they are exact, and table rows
-// (stencils, CSR entries) are loaded once per cell and reused for its levels.
+// the CUDA cores.  The lanes of a warp are laid over the item's (cell, level)
+// values in the order that is contiguous in memory -- consecutive cells when
+// levels are far apart, consecutive levels when they are adjacent -- so a
+// warp instruction touches as few 32-byte sectors as the layout allows; each
+// lane keeps several independent values in flight; copies move integer bit
+// patterns so they are exact; table rows (stencils, CSR entries) are loaded
+// once per cell and level chunk.
 #include <cstdint>
 
 #include "bc_internal.h"
@@ -22,6 +25,11 @@ template <typename T> struct BitsOf;
 template <> struct BitsOf<float> { using type = uint32_t; };
 template <> struct BitsOf<double> { using type = uint64_t; };
 
+__device__ __forceinline__ uint32_t to_bits(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ uint64_t to_bits(double v) {
+  return (uint64_t)__double_as_longlong(v);
+}
+
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
@@ -29,7 +37,18 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
   return (__umulhi(n, f.m) + n) >> f.s;
 }
 
-// unit u -> cell q of the box and level chunk c (u = q + vol * c)
+// flat unit f -> (cell q, level l)
+__device__ __forceinline__ void flat_of(int f, const Item& it, int& q, int& l) {
+  if (it.mode == MODE_FLAT_LEVEL) {
+    q = (int)fdiv((uint32_t)f, it.lev);
+    l = f - q * (int)it.lev.d;
+  } else {
+    l = (int)fdiv((uint32_t)f, it.vol);
+    q = f - l * (int)it.vol.d;
+  }
+}
+
+// chunk unit u -> cell q of the box and level chunk c (u = q + vol * c)
 __device__ __forceinline__ void unit_of(int u, const Item& it, int& q, int& c) {
   c = (int)fdiv((uint32_t)u, it.vol);
   q = u - c * (int)it.vol.d;
@@ -48,19 +67,20 @@ __device__ __forceinline__ int dst_offset(const Item& it, int i, int j, int k) {
   return it.dst_org + i * it.dst_s0 + j * it.dst_s1 + k * it.dst_s2;
 }
 
+__device__ __forceinline__ int dst_cell(const Item& it, int q) {
+  int i, j, k;
+  cell_of(q, it, i, j, k);
+  return dst_offset(it, i, j, k);
+}
+
 // ---------------------------------------------------------------------------
 // zero / constant / map (matrix-free rows, Sec. III-B)
 // ---------------------------------------------------------------------------
-// Per-lane work batches: every load of a batch is issued before its first
-// store, so a lane keeps up to kFlatUnroll * 2 (single-level values) or
-// UnitsInFlight<T> * kChunk (8-level units) independent loads in flight.
-template <typename T> struct UnitsInFlight { static constexpr int v = 4; };
-template <> struct UnitsInFlight<double> { static constexpr int v = 2; };
-
+// Flat: every lane keeps U single values in flight.
 template <typename T>
 __device__ void structured_flat(const Item& it, const Ctx& c, int lane) {
   using B = typename BitsOf<T>::type;
-  constexpr int U = 2 * kFlatUnroll;
+  constexpr int U = kFlatUnroll;
   const int end = it.u0 + it.nunits;
   B* dbase = static_cast<B*>(c.slots[it.dst_slot]);
   const bool is_map = it.kind == IK_MAP;
@@ -76,7 +96,7 @@ __device__ void structured_flat(const Item& it, const Ctx& c, int lane) {
       v[u] = B(0);
       if (f < end) {
         int q, l, i, j, k;
-        unit_of(f, it, q, l);
+        flat_of(f, it, q, l);
         cell_of(q, it, i, j, k);
         doff[u] = dst_offset(it, i, j, k) + l * it.dst_ls;
         if (is_map)
@@ -92,78 +112,29 @@ __device__ void structured_flat(const Item& it, const Ctx& c, int lane) {
   }
 }
 
-template <typename T>
-__device__ void structured_chunk(const Item& it, const Ctx& c, int lane) {
-  using B = typename BitsOf<T>::type;
-  constexpr int R = UnitsInFlight<T>::v;
-  const int end = it.u0 + it.nunits;
-  B* dbase = static_cast<B*>(c.slots[it.dst_slot]);
-  const bool is_map = it.kind == IK_MAP;
-  const B* sbase = is_map ? static_cast<const B*>(c.slots[it.src_slot]) : nullptr;
-  const int ls = it.dst_ls, sls = it.src_ls;
-  for (int ub = it.u0 + lane; ub < end; ub += 32 * R) {
-    B v[R][kChunk];
-    int doff[R], nl[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int u = ub + 32 * r;
-      nl[r] = 0;
-      doff[r] = 0;
-      if (u < end) {
-        int q, ch, i, j, k;
-        unit_of(u, it, q, ch);
-        cell_of(q, it, i, j, k);
-        const int l0 = ch * kChunk;
-        nl[r] = min(kChunk, it.L - l0);
-        doff[r] = dst_offset(it, i, j, k) + l0 * ls;
-        if (is_map) {
-          const B* s = sbase + (it.src_org + i * it.src_s0 + j * it.src_s1 +
-                                k * it.src_s2 + l0 * sls);
-#pragma unroll
-          for (int l = 0; l < kChunk; ++l)
-            if (l < nl[r]) v[r][l] = ldg(s + l * sls);
-        } else {
-          const B b = it.kind == IK_CONST
-                          ? ldg(static_cast<const B*>(c.const_val) + it.table + q)
-                          : B(0);
-#pragma unroll
-          for (int l = 0; l < kChunk; ++l) v[r][l] = b;
-        }
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      B* d = dbase + doff[r];
-#pragma unroll
-      for (int l = 0; l < kChunk; ++l)
-        if (l < nl[r]) d[l * ls] = v[r][l];
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // interpolation rows (user Itp, Sec. III-B) with optional 2x2 rotation of a
 // covariant component pair (Sec. V-A): y = M (sum_k w_k x_u, sum_k w_k x_v)
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void interp_scalar(const Item& it, const Ctx& c, int lane) {
+__device__ void interp_scalar_chunk(const Item& it, const Ctx& c, int lane) {
   using B = typename BitsOf<T>::type;
   const int end = it.u0 + it.nunits;
   const int ls = it.dst_ls;
   const int p = it.p;
-  const int chn = it.ch;
+  const int chn = it.mode;
+  const int comp = it.comp & 0xffff;
   for (int u = it.u0 + lane; u < end; u += 32) {
-    int q, ch, i, j, k;
+    int q, ch;
     unit_of(u, it, q, ch);
-    cell_of(q, it, i, j, k);
     const int l0 = ch * chn;
-    const int nl = min(chn, it.L - l0);
+    const int nl = min(chn, (int)it.lev.d - l0);
     const int row = it.table + q;
     const int4 ix = __ldg(c.itp_idx + row);
-    const int su = ix.x + it.comp;
+    const int su = ix.x + comp;
     const int sls = __ldg(c.slot_ls + su);
     const T* x = static_cast<const T*>(c.slots[su]) + (ix.y + l0 * sls);
-    T* d = static_cast<T*>(c.slots[it.dst_slot]) + (dst_offset(it, i, j, k) + l0 * ls);
+    T* d = static_cast<T*>(c.slots[it.dst_slot]) + (dst_cell(it, q) + l0 * ls);
     if (ix.w & kFlagSnap) {  // unit row: exact copy of node 0
       const B* s = reinterpret_cast<const B*>(x);
       B* db = reinterpret_cast<B*>(d);
@@ -197,30 +168,30 @@ __device__ void interp_scalar(const Item& it, const Ctx& c, int lane) {
 }
 
 template <typename T>
-__device__ void interp_pair(const Item& it, const Ctx& c, int lane) {
+__device__ void interp_pair_chunk(const Item& it, const Ctx& c, int lane) {
   constexpr int LU = kChunk / 2;
   const int end = it.u0 + it.nunits;
   const int ls = it.dst_ls;
   const int p = it.p;
-  const int chn = it.ch;
+  const int chn = it.mode;
   for (int u = it.u0 + lane; u < end; u += 32) {
-    int q, ch, i, j, k;
+    int q, ch;
     unit_of(u, it, q, ch);
-    cell_of(q, it, i, j, k);
     const int l0 = ch * chn;
-    const int nl = min(chn, it.L - l0);
+    const int nl = min(chn, (int)it.lev.d - l0);
     const int row = it.table + q;
     const int4 ix = __ldg(c.itp_idx + row);
-    const int su = ix.x + it.comp, sv = ix.x + it.comp2;
+    const int su = ix.x + (it.comp & 0xffff), sv = ix.x + (it.comp >> 16);
     const int slu = __ldg(c.slot_ls + su), slv = __ldg(c.slot_ls + sv);
     const T* xu = static_cast<const T*>(c.slots[su]) + (ix.y + l0 * slu);
     const T* xv = static_cast<const T*>(c.slots[sv]) + (ix.y + l0 * slv);
-    const int doff = dst_offset(it, i, j, k) + l0 * ls;
+    const int doff = dst_cell(it, q) + l0 * ls;
     T* du = static_cast<T*>(c.slots[it.dst_slot]) + doff;
     T* dv = static_cast<T*>(c.slots[it.dst_slot2]) + doff;
     const T* mr = static_cast<const T*>(c.itp_m) + row * 4;
     const T* wr = static_cast<const T*>(c.itp_w) + row * kPMax;
-    const int pe = (ix.w & kFlagSnap) ? 1 : p;
+    const bool snap = ix.w & kFlagSnap;
+    const int pe = snap ? 1 : p;
     for (int lb = 0; lb < nl; lb += LU) {
       T au[LU], av[LU];
 #pragma unroll
@@ -228,7 +199,7 @@ __device__ void interp_pair(const Item& it, const Ctx& c, int lane) {
 #pragma unroll
       for (int n = 0; n < kPMax; ++n) {
         if (n < pe) {
-          const T w = (ix.w & kFlagSnap) ? T(1) : ldg(wr + n);
+          const T w = snap ? T(1) : ldg(wr + n);
           const T* xun = xu + n * ix.z + lb * slu;
           const T* xvn = xv + n * ix.z + lb * slv;
 #pragma unroll
@@ -250,28 +221,93 @@ __device__ void interp_pair(const Item& it, const Ctx& c, int lane) {
   }
 }
 
+// Flat interpolation: each lane keeps U values (cell, level) in flight; with
+// level-fastest order the lanes of a warp share a cell, so its table row is
+// one broadcast load and the node loads of the warp are contiguous.
+template <typename T, bool PAIR>
+__device__ void interp_flat(const Item& it, const Ctx& c, int lane) {
+  using B = typename BitsOf<T>::type;
+  constexpr int U = 4;
+  const int end = it.u0 + it.nunits;
+  const int p = it.p;
+  const int cu = it.comp & 0xffff, cv = it.comp >> 16;
+  B* du = static_cast<B*>(c.slots[it.dst_slot]);
+  B* dv = PAIR ? static_cast<B*>(c.slots[it.dst_slot2]) : nullptr;
+  for (int f0 = it.u0 + lane; f0 < end; f0 += 32 * U) {
+    int doff[U];
+    B ou[U], ov[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int f = f0 + 32 * u;
+      doff[u] = -1;
+      ou[u] = ov[u] = B(0);
+      if (f < end) {
+        int q, l;
+        flat_of(f, it, q, l);
+        doff[u] = dst_cell(it, q) + l * it.dst_ls;
+        const int row = it.table + q;
+        const int4 ix = __ldg(c.itp_idx + row);
+        const int su = ix.x + cu;
+        const T* xu = static_cast<const T*>(c.slots[su]) + (ix.y + l * __ldg(c.slot_ls + su));
+        const bool snap = ix.w & kFlagSnap;
+        if (!PAIR && snap) {  // unit row: exact copy of node 0
+          ou[u] = ldg(reinterpret_cast<const B*>(xu));
+          continue;
+        }
+        const T* wr = static_cast<const T*>(c.itp_w) + row * kPMax;
+        const int pe = snap ? 1 : p;
+        T au = T(0), av = T(0);
+        const T* xv = nullptr;
+        if (PAIR) {
+          const int sv = ix.x + cv;
+          xv = static_cast<const T*>(c.slots[sv]) + (ix.y + l * __ldg(c.slot_ls + sv));
+        }
+#pragma unroll
+        for (int n = 0; n < kPMax; ++n)
+          if (n < pe) {
+            const T w = snap ? T(1) : ldg(wr + n);
+            au = fma(w, ldg(xu + n * ix.z), au);
+            if (PAIR) av = fma(w, ldg(xv + n * ix.z), av);
+          }
+        if (PAIR) {
+          const T* mr = static_cast<const T*>(c.itp_m) + row * 4;
+          ou[u] = to_bits(fma(ldg(mr), au, ldg(mr + 1) * av));
+          ov[u] = to_bits(fma(ldg(mr + 2), au, ldg(mr + 3) * av));
+        } else {
+          ou[u] = to_bits(au);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (doff[u] >= 0) {
+        du[doff[u]] = ou[u];
+        if (PAIR) dv[doff[u]] = ov[u];
+      }
+  }
+}
+
 // ---------------------------------------------------------------------------
-// user CSR rows (Table III: F_NNZ / F_COL / F_DATA): the row's entries are
-// loaded once per unit and reused for its levels
+// user CSR rows (Table III: F_NNZ / F_COL / F_DATA), ELL-packed: row q of the
+// item's component has its entries at src_org + q * p
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void csr_rows(const Item& it, const Ctx& c, int lane) {
+__device__ void csr_chunk(const Item& it, const Ctx& c, int lane) {
   constexpr int E = 8;  // rows up to E entries: all entry loads issued at once
   const int end = it.u0 + it.nunits;
   const int ls = it.dst_ls;
-  const int chn = it.ch;
+  const int chn = it.mode;
   const int W = it.p;
   const T* val = static_cast<const T*>(c.csr_val);
   for (int u = it.u0 + lane; u < end; u += 32) {
-    int q, ch, i, j, k;
+    int q, ch;
     unit_of(u, it, q, ch);
-    cell_of(q, it, i, j, k);
     const int l0 = ch * chn;
-    const int nl = min(chn, it.L - l0);
+    const int nl = min(chn, (int)it.lev.d - l0);
     const int row = it.table + q;
     const int nnz = __ldg(c.csr_nnz + row);
     const int e0 = it.src_org + q * W;
-    T* d = static_cast<T*>(c.slots[it.dst_slot]) + (dst_offset(it, i, j, k) + l0 * ls);
+    T* d = static_cast<T*>(c.slots[it.dst_slot]) + (dst_cell(it, q) + l0 * ls);
     T acc[kChunk];
 #pragma unroll
     for (int l = 0; l < kChunk; ++l) acc[l] = T(0);
@@ -312,20 +348,58 @@ __device__ void csr_rows(const Item& it, const Ctx& c, int lane) {
   }
 }
 
+template <typename T>
+__device__ void csr_flat(const Item& it, const Ctx& c, int lane) {
+  constexpr int U = 4;
+  const int end = it.u0 + it.nunits;
+  const int W = it.p;
+  const T* val = static_cast<const T*>(c.csr_val);
+  T* dbase = static_cast<T*>(c.slots[it.dst_slot]);
+  for (int f0 = it.u0 + lane; f0 < end; f0 += 32 * U) {
+    int doff[U];
+    T out[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int f = f0 + 32 * u;
+      doff[u] = -1;
+      out[u] = T(0);
+      if (f < end) {
+        int q, l;
+        flat_of(f, it, q, l);
+        doff[u] = dst_cell(it, q) + l * it.dst_ls;
+        const int row = it.table + q;
+        const int nnz = __ldg(c.csr_nnz + row);
+        const int e0 = it.src_org + q * W;
+        T acc = T(0);
+        for (int e = 0; e < nnz; ++e) {
+          const int s = __ldg(c.csr_slot + e0 + e);
+          const T* x = static_cast<const T*>(c.slots[s]) +
+                       (__ldg(c.csr_off + e0 + e) + l * __ldg(c.slot_ls + s));
+          acc = fma(ldg(val + e0 + e), ldg(x), acc);
+        }
+        out[u] = acc + ldg(static_cast<const T*>(c.csr_rhs) + row);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (doff[u] >= 0) dbase[doff[u]] = out[u];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // adjoint gather: x_bar_j += sum_i A_ij y_bar_i over the stored transpose,
 // entries in ascending ghost order (deterministic, no atomics)
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void adj_rows(const Item& it, const Ctx& c, int lane) {
+__device__ void adj_chunk(const Item& it, const Ctx& c, int lane) {
   const int end = it.u0 + it.nunits;
-  const int chn = it.ch;
+  const int chn = it.mode;
   const T* wv = static_cast<const T*>(c.aent_w);
   for (int u = it.u0 + lane; u < end; u += 32) {
     int q, ch;
     unit_of(u, it, q, ch);
     const int l0 = ch * chn;
-    const int nl = min(chn, it.L - l0);
+    const int nl = min(chn, (int)it.lev.d - l0);
     const int r = it.table + q;
     const int slot = __ldg(c.arow_slot + r);
     const int ls = __ldg(c.slot_ls + slot);
@@ -350,21 +424,72 @@ __device__ void adj_rows(const Item& it, const Ctx& c, int lane) {
 }
 
 template <typename T>
+__device__ void adj_flat(const Item& it, const Ctx& c, int lane) {
+  constexpr int U = 4;
+  const int end = it.u0 + it.nunits;
+  const T* wv = static_cast<const T*>(c.aent_w);
+  for (int f0 = it.u0 + lane; f0 < end; f0 += 32 * U) {
+    T* dst[U];
+    T out[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int f = f0 + 32 * u;
+      dst[u] = nullptr;
+      out[u] = T(0);
+      if (f < end) {
+        int q, l;
+        flat_of(f, it, q, l);
+        const int r = it.table + q;
+        const int slot = __ldg(c.arow_slot + r);
+        T* xb = static_cast<T*>(c.slots[slot]) +
+                (__ldg(c.arow_off + r) + l * __ldg(c.slot_ls + slot));
+        const int64_t e0 = __ldg(c.adj_ptr + r), e1 = __ldg(c.adj_ptr + r + 1);
+        T acc = *xb;
+        for (int64_t e = e0; e < e1; ++e) {
+          const int gs = __ldg(c.aent_slot + e);
+          const T* y = static_cast<const T*>(c.slots[gs]) +
+                       (__ldg(c.aent_off + e) + l * __ldg(c.slot_ls + gs));
+          acc = fma(ldg(wv + e), *y, acc);
+        }
+        dst[u] = xb;
+        out[u] = acc;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (dst[u]) *dst[u] = out[u];
+  }
+}
+
+// Kernel families: one kernel per family keeps each family's register
+// budget (and so its occupancy) independent of the others.
+template <typename T, int FAM>
 __device__ __forceinline__ void run_item(const Item& it, const Ctx& c, int lane) {
-  switch (it.kind) {
-    case IK_ZERO:
-    case IK_CONST:
-    case IK_MAP:
-      if (it.ch == 1)
-        structured_flat<T>(it, c, lane);
+  const bool flat = it.mode < 2;
+  if constexpr (FAM == FAM_STRUCT) {
+    structured_flat<T>(it, c, lane);
+  } else if constexpr (FAM == FAM_INTERP) {
+    if (it.kind == IK_INTERP_PAIR) {
+      if (flat)
+        interp_flat<T, true>(it, c, lane);
       else
-        structured_chunk<T>(it, c, lane);
-      break;
-    case IK_INTERP: interp_scalar<T>(it, c, lane); break;
-    case IK_INTERP_PAIR: interp_pair<T>(it, c, lane); break;
-    case IK_CSR: csr_rows<T>(it, c, lane); break;
-    case IK_ADJ: adj_rows<T>(it, c, lane); break;
-    default: break;
+        interp_pair_chunk<T>(it, c, lane);
+    } else {
+      if (flat)
+        interp_flat<T, false>(it, c, lane);
+      else
+        interp_scalar_chunk<T>(it, c, lane);
+    }
+  } else if constexpr (FAM == FAM_CSR) {
+    if (flat)
+      csr_flat<T>(it, c, lane);
+    else
+      csr_chunk<T>(it, c, lane);
+  } else {
+    if (flat)
+      adj_flat<T>(it, c, lane);
+    else
+      adj_chunk<T>(it, c, lane);
   }
 }
 
@@ -375,25 +500,28 @@ __device__ __forceinline__ void load_item(Item* dst, const Item* src, int lane) 
   __syncwarp();
 }
 
-template <int THREADS> struct Occ {
-  static constexpr int kMinBlocks = THREADS >= 512 ? 1 : 512 / THREADS;
+// Resident CTAs the register budget is set for: the structured family is
+// lean (about 40 registers, 48 warps per SM); the table families get 64.
+template <int FAM, int THREADS> struct Occ {
+  static constexpr int kWarps = FAM == FAM_STRUCT ? 48 : 32;
+  static constexpr int kMinBlocks = (kWarps * 32) / THREADS > 0 ? (kWarps * 32) / THREADS : 1;
 };
 
-template <typename T, int THREADS>
-__global__ void __launch_bounds__(THREADS, Occ<THREADS>::kMinBlocks)
+template <typename T, int THREADS, int FAM>
+__global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     k_items(Ctx c, const Item* __restrict__ items, int nitems) {
   __shared__ Item sit[THREADS / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int idx = blockIdx.x * (THREADS / 32) + warp;
   if (idx >= nitems) return;
   load_item(&sit[warp], items + idx, lane);
-  run_item<T>(sit[warp], c, lane);
+  run_item<T, FAM>(sit[warp], c, lane);
 }
 
 // Persistent form: warps claim items from counter[0]; the last warp to
 // finish resets both counters for the next launch.  No warp waits on another.
-template <typename T, int THREADS>
-__global__ void __launch_bounds__(THREADS, Occ<THREADS>::kMinBlocks)
+template <typename T, int THREADS, int FAM>
+__global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     k_persistent(Ctx c, const Item* __restrict__ items, int nitems,
                  unsigned* counter) {
   __shared__ Item sit[THREADS / 32];
@@ -404,7 +532,7 @@ __global__ void __launch_bounds__(THREADS, Occ<THREADS>::kMinBlocks)
     idx = __shfl_sync(0xffffffffu, idx, 0);
     if (idx >= nitems) break;
     load_item(&sit[warp], items + idx, lane);
-    run_item<T>(sit[warp], c, lane);
+    run_item<T, FAM>(sit[warp], c, lane);
     __syncwarp();
   }
   if (lane == 0) {
@@ -418,55 +546,51 @@ __global__ void __launch_bounds__(THREADS, Occ<THREADS>::kMinBlocks)
   }
 }
 
-template <typename T>
-cudaError_t launch_items_t(const Ctx& c, const Item* items, int nitems,
-                           int threads, cudaStream_t s) {
-  if (nitems <= 0) return cudaSuccess;
-  const int wpb = threads / 32;
-  const int grid = (nitems + wpb - 1) / wpb;
-  switch (threads) {
-    case 32: k_items<T, 32><<<grid, 32, 0, s>>>(c, items, nitems); break;
-    case 64: k_items<T, 64><<<grid, 64, 0, s>>>(c, items, nitems); break;
-    case 128: k_items<T, 128><<<grid, 128, 0, s>>>(c, items, nitems); break;
-    case 512: k_items<T, 512><<<grid, 512, 0, s>>>(c, items, nitems); break;
-    default: k_items<T, 256><<<grid, 256, 0, s>>>(c, items, nitems); break;
+template <typename T, int THREADS, int FAM>
+cudaError_t launch_t(const Ctx& c, const Item* items, int nitems, int grid,
+                     unsigned* counter, cudaStream_t s) {
+  const int wpb = THREADS / 32;
+  const int need = (nitems + wpb - 1) / wpb;
+  if (grid <= 0 || counter == nullptr) {
+    k_items<T, THREADS, FAM><<<need, THREADS, 0, s>>>(c, items, nitems);
+  } else {
+    k_persistent<T, THREADS, FAM><<<grid < need ? grid : need, THREADS, 0, s>>>(
+        c, items, nitems, counter);
   }
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_persistent_t(const Ctx& c, const Item* items, int nitems,
-                                int threads, int grid, unsigned* counter,
-                                cudaStream_t s) {
-  if (nitems <= 0) return cudaSuccess;
-  const int wpb = threads / 32;
-  const int need = (nitems + wpb - 1) / wpb;
-  if (grid > need) grid = need;
+template <typename T, int FAM>
+cudaError_t launch_fam(const Ctx& c, const Item* items, int nitems, int threads,
+                       int grid, unsigned* counter, cudaStream_t s) {
   switch (threads) {
-    case 32: k_persistent<T, 32><<<grid, 32, 0, s>>>(c, items, nitems, counter); break;
-    case 64: k_persistent<T, 64><<<grid, 64, 0, s>>>(c, items, nitems, counter); break;
-    case 128: k_persistent<T, 128><<<grid, 128, 0, s>>>(c, items, nitems, counter); break;
-    case 512: k_persistent<T, 512><<<grid, 512, 0, s>>>(c, items, nitems, counter); break;
-    default: k_persistent<T, 256><<<grid, 256, 0, s>>>(c, items, nitems, counter); break;
+    case 32: return launch_t<T, 32, FAM>(c, items, nitems, grid, counter, s);
+    case 64: return launch_t<T, 64, FAM>(c, items, nitems, grid, counter, s);
+    case 128: return launch_t<T, 128, FAM>(c, items, nitems, grid, counter, s);
+    case 512: return launch_t<T, 512, FAM>(c, items, nitems, grid, counter, s);
+    default: return launch_t<T, 256, FAM>(c, items, nitems, grid, counter, s);
   }
-  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_any(int fam, const Ctx& c, const Item* items, int nitems,
+                       int threads, int grid, unsigned* counter, cudaStream_t s) {
+  switch (fam) {
+    case FAM_STRUCT: return launch_fam<T, FAM_STRUCT>(c, items, nitems, threads, grid, counter, s);
+    case FAM_INTERP: return launch_fam<T, FAM_INTERP>(c, items, nitems, threads, grid, counter, s);
+    case FAM_CSR: return launch_fam<T, FAM_CSR>(c, items, nitems, threads, grid, counter, s);
+    default: return launch_fam<T, FAM_ADJ>(c, items, nitems, threads, grid, counter, s);
+  }
 }
 
 }  // namespace
 
-cudaError_t launch_items(int dtype, const Ctx& ctx, const Item* items,
-                         int nitems, int threads, cudaStream_t s) {
-  return dtype == 1 ? launch_items_t<double>(ctx, items, nitems, threads, s)
-                    : launch_items_t<float>(ctx, items, nitems, threads, s);
-}
-
-cudaError_t launch_persistent(int dtype, const Ctx& ctx, const Item* items,
-                              int nitems, int threads, int grid,
-                              unsigned* counter, cudaStream_t s) {
-  return dtype == 1 ? launch_persistent_t<double>(ctx, items, nitems, threads,
-                                                  grid, counter, s)
-                    : launch_persistent_t<float>(ctx, items, nitems, threads,
-                                                 grid, counter, s);
+cudaError_t launch_family(int dtype, int family, const Ctx& ctx,
+                          const Item* items, int nitems, int threads, int grid,
+                          unsigned* counter, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  return dtype == 1 ? launch_any<double>(family, ctx, items, nitems, threads, grid, counter, s)
+                    : launch_any<float>(family, ctx, items, nitems, threads, grid, counter, s);
 }
 
 }  // namespace bcg

@@ -115,14 +115,25 @@ struct bc_plan {
   bool has_adjoint = false;
   // work lists
   std::vector<Item> items, adj_items, adj_zero;
-  std::vector<Item> items_batched;  // the same items in sub-matrix order
+  std::vector<Item> fam_items[kFamilies];  // batched form: per family, sub-matrix order
   std::vector<int> sub_begin, sub_end;
   int type_begin[5] = {0, 0, 0, 0, 0}, type_end[5] = {0, 0, 0, 0, 0};
   // device
   DevBuf tables, work;
   Ctx ctx{};
   Item* d_items = nullptr;
-  Item* d_batched = nullptr;
+  Item* d_fam[kFamilies] = {nullptr, nullptr, nullptr, nullptr};
+  // the batched form runs the families side by side: fork to these streams
+  cudaStream_t aux[kFamilies - 1] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kFamilies - 1] = {nullptr, nullptr, nullptr};
+  ~bc_plan() {
+    for (auto& a : aux)
+      if (a) cudaStreamDestroy(a);
+    for (auto& e : ev_join)
+      if (e) cudaEventDestroy(e);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+  }
   Item* d_adj = nullptr;
   Item* d_adj_zero = nullptr;
   unsigned* d_counter = nullptr;
@@ -577,6 +588,10 @@ bc_status run_cubed_sphere(bc_plan* P, const std::vector<const bc_submatrix*>& c
 }
 
 // -- work lists ----------------------------------------------------------------
+int family_of_kind(int kind) {
+  return kind == BC_INTERP ? FAM_INTERP : (kind == BC_CSR ? FAM_CSR : FAM_STRUCT);
+}
+
 FastDiv make_div(uint32_t d) {
   FastDiv f;
   f.d = d;
@@ -594,7 +609,7 @@ void item_common(const bc_plan* P, const Sub& s, int comp, Item& it) {
   it.vol = make_div((uint32_t)s.vol);
   it.w0 = make_div((uint32_t)s.W[0]);
   it.w1 = make_div((uint32_t)s.W[1]);
-  it.L = B.nlevels;
+  it.lev = make_div((uint32_t)B.nlevels);
   it.dst_org = (int32_t)cell_offset(B, s.lo[0], s.lo[1], s.lo[2]);
   it.dst_s0 = (int32_t)B.stride[0];
   it.dst_s1 = (int32_t)B.stride[1];
@@ -602,10 +617,30 @@ void item_common(const bc_plan* P, const Sub& s, int comp, Item& it) {
   it.dst_ls = (int32_t)(B.nlevels > 1 ? B.level_stride : 0);
 }
 
-// split the unit space [0, vol * ceil(L / ch)) into warp-sized items
-void emit_units(std::vector<Item>& out, Item proto, int vol, int L, int ch, int per_item) {
-  proto.ch = ch;
-  const int64_t total = (int64_t)vol * ((L + ch - 1) / ch);
+// Unit order of a block's items: level-fastest flat values when the levels
+// are contiguous; otherwise cell-major chunks of up to 8 levels, or flat
+// cell-fastest values when there are too few levels for a chunk.
+// `order`: 0 auto, 1 cells fastest, 2 levels fastest (bc_plan_opts).
+bool levels_fastest(const bc_block& B, int order) {
+  if (B.nlevels <= 1 || order == 1) return false;
+  return order == 2 || B.level_stride == 1;
+}
+
+int structured_mode(const bc_block& B, int order) {
+  return levels_fastest(B, order) ? MODE_FLAT_LEVEL : MODE_FLAT_CELL;
+}
+
+int table_mode(const bc_block& B, int order) {
+  if (levels_fastest(B, order)) return MODE_FLAT_LEVEL;
+  if (B.nlevels == 1) return MODE_FLAT_CELL;
+  return std::min(B.nlevels, kChunk);
+}
+
+// split the unit space into warp-sized items: vol * L single values (flat
+// modes) or vol * ceil(L / mode) chunks
+void emit_units(std::vector<Item>& out, Item proto, int vol, int L, int mode, int per_item) {
+  proto.mode = mode;
+  const int64_t total = mode < 2 ? (int64_t)vol * L : (int64_t)vol * ((L + mode - 1) / mode);
   for (int64_t u0 = 0; u0 < total; u0 += per_item) {
     Item it = proto;
     it.u0 = (int)u0;
@@ -622,14 +657,21 @@ void build_items(bc_plan* P) {
   // table-driven kinds (interpolation, CSR, transpose): one unit per lane, so
   // a warp's dependent table -> data chains run side by side, not in series
   const int per_table_item = 32;
+  const int per_table_flat_item = 32 * 8;
+  auto structured_emit = [&](std::vector<Item>& out, const Item& it, const bc_block& B, int vol) {
+    const int mode = structured_mode(B, P->opts.unit_order);
+    emit_units(out, it, vol, B.nlevels, mode, mode < 2 ? per_flat_item : per_chunk_item);
+  };
+  auto table_emit = [&](std::vector<Item>& out, const Item& it, const bc_block& B, int vol) {
+    const int mode = table_mode(B, P->opts.unit_order);
+    emit_units(out, it, vol, B.nlevels, mode, mode < 2 ? per_table_flat_item : per_table_item);
+  };
   std::vector<std::pair<int, std::vector<Item>>> per_sub(P->subs.size());
   for (size_t si = 0; si < P->subs.size(); ++si) {
     const Sub& s = P->subs[si];
     const bc_block& B = P->blocks[s.block];
     std::vector<Item>& out = per_sub[si].second;
     per_sub[si].first = s.kind;
-    const int L = B.nlevels;
-    const int chl = std::min(L, kChunk);
     for (size_t ci = 0; ci < s.comps.size(); ++ci) {
       const int c = s.comps[ci];
       Item it{};
@@ -654,10 +696,7 @@ void build_items(bc_plan* P) {
             it.src_s2 = (int32_t)st[2];
             it.src_ls = (int32_t)(S.nlevels > 1 ? S.level_stride : 0);
           }
-          if (L < kChunk)
-            emit_units(out, it, s.vol, L, 1, per_flat_item);
-          else
-            emit_units(out, it, s.vol, L, kChunk, per_chunk_item);
+          structured_emit(out, it, B, s.vol);
           break;
         }
         case BC_INTERP: {
@@ -667,12 +706,12 @@ void build_items(bc_plan* P) {
           it.comp = c;
           if (c == s.rot_u) {
             it.kind = IK_INTERP_PAIR;
-            it.comp2 = s.rot_v;
+            it.comp = c | (s.rot_v << 16);
             it.dst_slot2 = P->slot_base[s.block] + s.rot_v;
           } else {
             it.kind = IK_INTERP;
           }
-          emit_units(out, it, s.vol, L, chl, per_table_item);
+          table_emit(out, it, B, s.vol);
           break;
         }
         case BC_CSR: {
@@ -680,7 +719,7 @@ void build_items(bc_plan* P) {
           it.table = s.table + (int)ci * s.vol;
           it.p = s.ell_w;
           it.src_org = s.ell_base + (int)ci * s.vol * s.ell_w;
-          emit_units(out, it, s.vol, L, chl, per_table_item);
+          table_emit(out, it, B, s.vol);
           break;
         }
       }
@@ -702,41 +741,46 @@ void build_items(bc_plan* P) {
   }
   // batched launch: sub-matrix order, so the kinds (loads + stores, stores
   // only, table gathers) are interleaved over the grid
-  P->items_batched.clear();
-  for (size_t si = 0; si < P->subs.size(); ++si)
-    P->items_batched.insert(P->items_batched.end(), per_sub[si].second.begin(),
-                            per_sub[si].second.end());
+  for (auto& v : P->fam_items) v.clear();
+  for (size_t si = 0; si < P->subs.size(); ++si) {
+    const int f = family_of_kind(P->subs[si].kind);
+    P->fam_items[f].insert(P->fam_items[f].end(), per_sub[si].second.begin(),
+                           per_sub[si].second.end());
+  }
   // adjoint: the zero pass over every covered ghost value
   P->adj_zero.clear();
   for (size_t si = 0; si < P->subs.size(); ++si) {
     const Sub& s = P->subs[si];
-    const int L = P->blocks[s.block].nlevels;
     for (int c : s.comps) {
       Item z{};
       item_common(P, s, c, z);
       z.kind = IK_ZERO;
-      if (L < kChunk)
-        emit_units(P->adj_zero, z, s.vol, L, 1, per_flat_item);
-      else
-        emit_units(P->adj_zero, z, s.vol, L, kChunk, per_chunk_item);
+      structured_emit(P->adj_zero, z, P->blocks[s.block], s.vol);
     }
   }
-  // adjoint gather items over the transpose rows, grouped by level count
+  // adjoint gather items over the transpose rows, grouped by the level
+  // count and level layout of the data block
   P->adj_items.clear();
   const int nar = (int)P->arow_slot.size();
+  auto block_of_row = [&](int r) -> const bc_block& {
+    return P->blocks[P->slot_block[P->arow_slot[r]]];
+  };
   int r0 = 0;
   while (r0 < nar) {
-    const int L = P->blocks[P->slot_block[P->arow_slot[r0]]].nlevels;
+    const bc_block& B0 = block_of_row(r0);
+    const int mode0 = table_mode(B0, P->opts.unit_order);
     int r1 = r0;
-    while (r1 < nar && P->blocks[P->slot_block[P->arow_slot[r1]]].nlevels == L) ++r1;
+    while (r1 < nar && block_of_row(r1).nlevels == B0.nlevels &&
+           table_mode(block_of_row(r1), P->opts.unit_order) == mode0)
+      ++r1;
     Item it{};
     it.kind = IK_ADJ;
     it.vol = make_div((uint32_t)(r1 - r0));
     it.w0 = make_div(1);
     it.w1 = make_div(1);
-    it.L = L;
+    it.lev = make_div((uint32_t)B0.nlevels);
     it.table = r0;
-    emit_units(P->adj_items, it, r1 - r0, L, std::min(L, kChunk), per_table_item);
+    table_emit(P->adj_items, it, B0, r1 - r0);
     r0 = r1;
   }
 }
@@ -883,13 +927,14 @@ bc_status upload_work(bc_plan* P) {
   }
   Layout L;
   const size_t o_i = L.take(P->items.size() * sizeof(Item));
-  const size_t o_b = L.take(P->items_batched.size() * sizeof(Item));
+  size_t o_f[kFamilies];
+  for (int f = 0; f < kFamilies; ++f) o_f[f] = L.take(P->fam_items[f].size() * sizeof(Item));
   const size_t o_a = L.take(P->adj_items.size() * sizeof(Item));
   const size_t o_z = L.take(P->adj_zero.size() * sizeof(Item));
-  const size_t o_c = L.take(2 * sizeof(unsigned));
+  const size_t o_c = L.take(2 * kFamilies * sizeof(unsigned));
   std::vector<char> host(L.off + 256, 0);
   put_raw(host, o_i, P->items);
-  put_raw(host, o_b, P->items_batched);
+  for (int f = 0; f < kFamilies; ++f) put_raw(host, o_f[f], P->fam_items[f]);
   put_raw(host, o_a, P->adj_items);
   put_raw(host, o_z, P->adj_zero);
   cudaError_t e = cudaMalloc(&P->work.base, host.size());
@@ -902,7 +947,7 @@ bc_status upload_work(bc_plan* P) {
   if (e != cudaSuccess) return cuda_fail(e, "device work list upload");
   char* b = static_cast<char*>(P->work.base);
   P->d_items = reinterpret_cast<Item*>(b + o_i);
-  P->d_batched = reinterpret_cast<Item*>(b + o_b);
+  for (int f = 0; f < kFamilies; ++f) P->d_fam[f] = reinterpret_cast<Item*>(b + o_f[f]);
   P->d_adj = reinterpret_cast<Item*>(b + o_a);
   P->d_adj_zero = reinterpret_cast<Item*>(b + o_z);
   P->d_counter = reinterpret_cast<unsigned*>(b + o_c);
@@ -975,7 +1020,7 @@ bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
       o.threads != 512)
     return fail(BC_ERR_INVALID_ARG, "threads must be 32, 64, 128, 256 or 512");
   if (o.units_per_lane == 0) o.units_per_lane = 4;
-  if (o.units_per_lane < 1 || o.ctas_per_sm < 0)
+  if (o.units_per_lane < 1 || o.ctas_per_sm < 0 || o.unit_order < 0 || o.unit_order > 2)
     return fail(BC_ERR_INVALID_ARG, "bad work-item options");
   return BC_OK;
 }
@@ -1041,6 +1086,14 @@ bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_fail(e, "device attributes");
+  for (auto& a : P->aux)
+    if ((e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "plan streams");
+  if ((e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "plan events");
+  for (auto& ev : P->ev_join)
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "plan events");
   if ((st = run_cubed_sphere(P, cs_subs, cs_idx)) != BC_OK) return st;
   // explicit rows of interpolation sub-matrices, in sub-matrix order
   {
@@ -1080,25 +1133,42 @@ bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_
   return BC_OK;
 }
 
+int persistent_grid(const bc_plan* P) {
+  return P->opts.ctas_per_sm > 0 ? P->opts.ctas_per_sm * P->num_sms : 0;
+}
+
 bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t s) {
   Ctx c = P->ctx;
   c.slots = slots;
   cudaError_t e = cudaSuccess;
   const int T = P->opts.threads;
   if (form == BC_FORM_BATCHED) {
-    if (P->opts.ctas_per_sm > 0)
-      e = launch_persistent(P->dtype, c, P->d_batched, (int)P->items_batched.size(), T,
-                            P->opts.ctas_per_sm * P->num_sms, P->d_counter, s);
-    else
-      e = launch_items(P->dtype, c, P->d_batched, (int)P->items_batched.size(), T, s);
+    // one launch per kernel family, the families side by side
+    int fams[kFamilies], nf = 0;
+    for (int f = 0; f < kFamilies; ++f)
+      if (!P->fam_items[f].empty()) fams[nf++] = f;
+    const int grid = persistent_grid(P);
+    if (nf > 1 && (e = cudaEventRecord(P->ev_fork, s)) != cudaSuccess)
+      return cuda_fail(e, "fork event");
+    for (int t = 0; t < nf && e == cudaSuccess; ++t) {
+      cudaStream_t st = t == 0 ? s : P->aux[t - 1];
+      if (t > 0 && (e = cudaStreamWaitEvent(st, P->ev_fork, 0)) != cudaSuccess) break;
+      e = launch_family(P->dtype, fams[t], c, P->d_fam[fams[t]],
+                        (int)P->fam_items[fams[t]].size(), T, grid,
+                        P->d_counter + 2 * fams[t], st);
+      if (e == cudaSuccess && t > 0) e = cudaEventRecord(P->ev_join[t - 1], st);
+    }
+    for (int t = 1; t < nf && e == cudaSuccess; ++t)
+      e = cudaStreamWaitEvent(s, P->ev_join[t - 1], 0);
   } else if (form == BC_FORM_TYPEWIDE) {
     for (int k = 0; k < 5 && e == cudaSuccess; ++k)
-      e = launch_items(P->dtype, c, P->d_items + P->type_begin[k],
-                       P->type_end[k] - P->type_begin[k], T, s);
+      e = launch_family(P->dtype, family_of_kind(k), c, P->d_items + P->type_begin[k],
+                        P->type_end[k] - P->type_begin[k], T, 0, nullptr, s);
   } else if (form == BC_FORM_PER_BC) {
     for (size_t si = 0; si < P->subs.size() && e == cudaSuccess; ++si)
-      e = launch_items(P->dtype, c, P->d_items + P->sub_begin[si],
-                       P->sub_end[si] - P->sub_begin[si], T, s);
+      e = launch_family(P->dtype, family_of_kind(P->subs[si].kind), c,
+                        P->d_items + P->sub_begin[si], P->sub_end[si] - P->sub_begin[si], T,
+                        0, nullptr, s);
   } else {
     return fail(BC_ERR_INVALID_ARG, "unknown form %d", form);
   }
@@ -1154,9 +1224,11 @@ bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs, void* stream) 
   c.slots = slot_ptrs;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int T = plan->opts.threads;
-  cudaError_t e = launch_items(plan->dtype, c, plan->d_adj, (int)plan->adj_items.size(), T, s);
+  cudaError_t e = launch_family(plan->dtype, FAM_ADJ, c, plan->d_adj,
+                                (int)plan->adj_items.size(), T, 0, nullptr, s);
   if (e == cudaSuccess)
-    e = launch_items(plan->dtype, c, plan->d_adj_zero, (int)plan->adj_zero.size(), T, s);
+    e = launch_family(plan->dtype, FAM_STRUCT, c, plan->d_adj_zero,
+                      (int)plan->adj_zero.size(), T, 0, nullptr, s);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   return BC_OK;
 }
@@ -1234,9 +1306,9 @@ bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) 
     med = ts[ts.size() / 2];
     return BC_OK;
   };
-  const int threads_c[] = {128, 256, 512};
+  const int threads_c[] = {64, 128, 256};
   const int units_c[] = {1, 2, 4, 8};
-  const int warps_c[] = {0, 16, 32, 48, 64};  // persistent warps per SM
+  const int warps_c[] = {0, 16, 32, 48};  // persistent warps per SM (0: grid)
   bc_status st = BC_OK;
   for (int T : threads_c) {
     for (int U : units_c) {

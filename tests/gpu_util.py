@@ -14,6 +14,17 @@ def to_device(fields):
     return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in fields]
 
 
+def to_device_innermost(fields):
+    """Device copies with every component stored [k][j][i][level]; the views
+    keep the (C, L, F2, F1, F0) index order."""
+    import torch
+    out = []
+    for a in fields:
+        base = torch.from_numpy(np.ascontiguousarray(a.transpose(0, 2, 3, 4, 1))).cuda()
+        out.append(base.permute(0, 4, 1, 2, 3))
+    return out
+
+
 def run(w, form=bc.BC_FORM_BATCHED, opts=None, tensors=None, repeat=1):
     import torch
     ts = tensors if tensors is not None else to_device(w["fields"])

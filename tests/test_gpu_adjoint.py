@@ -75,6 +75,24 @@ def test_adjoint_vs_oracle(make):
     _check_adjoint(w, cot, out)
 
 
+@pytest.mark.parametrize("make", [
+    lambda: synth.batching(nblocks=30, side_lo=3, side_hi=30, lev_lo=1,
+                           lev_hi=20, h=2, seed=3, dtype="f32"),
+    lambda: synth.cubed_sphere(10, 3, 6, 9, ("h", "u", "v"), "f64", seed=4),
+])
+def test_adjoint_level_innermost(make):
+    import torch
+    from gpu_util import to_device_innermost
+    w = make()
+    cot = synth.cotangent_like(w, 78)
+    ts = to_device_innermost(w["fields"])
+    plan = bc.plan_for_workload(w, ts)
+    cs = to_device_innermost(cot)
+    plan.adjoint(bc.slot_table(cs))
+    torch.cuda.synchronize()
+    _check_adjoint(w, cot, [c.cpu().numpy() for c in cs])
+
+
 def test_adjoint_full_768_sampled():
     """The 6 x 768^2, (h, u, v) x 32-level FP32 adjoint, levels 2 and 29
     compared with the oracle's explicit transpose."""

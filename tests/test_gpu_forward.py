@@ -6,7 +6,7 @@ Copies, zero and constant rows bit-exact; interpolation and CSR rows within
 import numpy as np
 import pytest
 
-from gpu_util import bits, compare, flat, run, to_device
+from gpu_util import bits, compare, flat, run, to_device, to_device_innermost
 from oracle.operator import build_operator
 from paper_2605_14780_gb300 import bc, synth
 
@@ -174,6 +174,25 @@ def test_non_contiguous_layout():
     plan, _ = run(w, tensors=views)
     out = [v.cpu().numpy() for v in views]
     compare(w, out)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("form", FORMS)
+def test_level_innermost_batching(dtype, form):
+    """Levels contiguous in memory: every kind runs level-fastest."""
+    w = synth.batching(nblocks=40, side_lo=3, side_hi=40, lev_lo=1, lev_hi=40,
+                       h=2, seed=17, dtype=dtype)
+    ts = to_device_innermost(w["fields"])
+    _, _ = run(w, form=form, tensors=ts)
+    compare(w, [t.cpu().numpy() for t in ts])
+
+
+@pytest.mark.parametrize("N,L", [(9, 1), (16, 7), (12, 33)])
+def test_level_innermost_cubed_sphere(N, L):
+    w = synth.cubed_sphere(N, 3, 6, L, ("h", "u", "v"), "f32", seed=N)
+    ts = to_device_innermost(w["fields"])
+    run(w, tensors=ts)
+    compare(w, [t.cpu().numpy() for t in ts])
 
 
 def test_empty_plan():
