@@ -201,22 +201,29 @@ def field_copies(w, ncopies, device, layout="level_outermost"):
     copies = []
     for _ in range(ncopies):
         buf = torch.empty(sum(sizes), dtype=dt, device=device)
-        views, pos = [], 0
-        for a in w["fields"]:
-            if layout == "level_innermost":
-                C, L, F2, F1, F0 = a.shape
-                v = buf[pos:pos + a.size].view(C, F2, F1, F0, L).permute(0, 4, 1, 2, 3)
-            else:
-                v = buf[pos:pos + a.size].view(a.shape)
+        views = layout_views(buf, w, layout)
+        for v, a in zip(views, w["fields"]):
             v.copy_(torch.from_numpy(a))
-            views.append(v)
-            pos += a.size
         copies.append((buf, views))
     return copies
 
 
+def layout_views(buf, w, layout):
+    """Per-block (C, L, F2, F1, F0) views of one flat buffer in ``layout``."""
+    views, pos = [], 0
+    for a in w["fields"]:
+        if layout == "level_innermost":
+            C, L, F2, F1, F0 = a.shape
+            v = buf[pos:pos + a.size].view(C, F2, F1, F0, L).permute(0, 4, 1, 2, 3)
+        else:
+            v = buf[pos:pos + a.size].view(a.shape)
+        views.append(v)
+        pos += a.size
+    return views
+
+
 def measure_forward(w, device, stream, steps, warmup, layout="level_outermost",
-                    adjoint=False):
+                    adjoint=False, floor=False):
     """Device time of the batched forward (and optionally the adjoint) of a
     workload with rotating field copies; returns a dict of numbers."""
     from paper_2605_14780_gb300 import bc
@@ -237,6 +244,8 @@ def measure_forward(w, device, stream, steps, warmup, layout="level_outermost",
            "useful_gbs": st["bytes_fwd"] / (ms / 1e3) / 1e9,
            "frac_of_measured_hbm": st["bytes_fwd"] / (ms / 1e3) / 1e9 / hbm,
            "layout": layout, "field_copies": ncopies}
+    if floor:
+        out["dram_floor"] = dram_floor(plan, w, copies[0][1], copies[0][0])
     del gs
     if adjoint:
         ga = [capture(lambda t=t: plan.adjoint(t, stream=stream), stream) for t in tables]
@@ -350,6 +359,60 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+def dram_floor(plan, w, views, buf):
+    """Smallest DRAM traffic one forward apply can cause: every 32- or 64-byte
+    granule it reads, every granule it writes, and one extra read for each
+    granule it writes only partly (HBM3e with ECC has no write mask).  Built
+    from the plan's own rows (bc_plan_export_csr) and the fields' addresses."""
+    ex = plan.export_csr()
+    esize = buf.element_size()
+    base = buf.data_ptr()
+    slot_addr, slot_ls, slot_L = [], [], []
+    for v, blk in zip(views, w["blocks"]):
+        for c in range(blk["ncomp"]):
+            slot_addr.append((v[c].data_ptr() - base) // esize)
+            slot_ls.append(v.stride(1))
+            slot_L.append(blk["nlevels"])
+    slot_addr = np.array(slot_addr, np.int64)
+    slot_ls = np.array(slot_ls, np.int64)
+    slot_L = np.array(slot_L, np.int64)
+
+    def expand(slots, offs):
+        L = slot_L[slots]
+        rep = np.repeat(np.arange(len(slots)), L)
+        lev = np.arange(L.sum()) - np.repeat(np.cumsum(L) - L, L)
+        return slot_addr[slots][rep] + offs[rep] + lev * slot_ls[slots][rep]
+
+    wr = expand(ex["row_slot"], ex["row_off"])
+    rd = expand(ex["col_slot"], ex["col_off"])
+    out = {}
+    for g in (32, 64):
+        per = g // esize
+        wsec, wcnt = np.unique(wr // per, return_counts=True)
+        partial = wsec[wcnt < per]
+        rsec = np.union1d(np.unique(rd // per), partial)
+        out[f"granule_{g}B_bytes"] = int((len(wsec) + len(rsec)) * g)
+    return out
+
+
+FAMILY_KINDS = {"structured (zero/const/map)": (0, 1, 2), "interpolation": (3,),
+                "csr": (4,)}
+
+
+def family_plans(w, tensors):
+    """One plan per kernel family over the same fields, to time each family's
+    kernel on its own."""
+    from paper_2605_14780_gb300 import bc, specs
+    subs = specs.submatrices(w)
+    blocks = bc.block_descriptors(tensors, w["blocks"])
+    out = {}
+    for name, kinds in FAMILY_KINDS.items():
+        part = [s for s in subs if s["kind"] in kinds]
+        if part:
+            out[name] = bc.Plan(blocks, part, w["dtype"], {"no_adjoint": 1})
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2605_14780_gb300 import bc
@@ -361,7 +424,7 @@ def run_ours(args, rank, world, local):
     field_bytes = sum(a.size for a in w["fields"]) * esize
     ncopies = max(2, int(np.ceil(3 * 256e6 / field_bytes)) + 1)
     ncopies = min(ncopies, 8)
-    copies = field_copies(w, ncopies, device)
+    copies = field_copies(w, ncopies, device, args.layout)
     plan = bc.plan_for_workload(w, copies[0][1])
     tables = [bc.slot_table(v) for _, v in copies]
     if args.autotune:
@@ -369,31 +432,53 @@ def run_ours(args, rank, world, local):
     st = plan.stats()
     nvals = st["ghost_values"]
     stream = torch.cuda.Stream(device)
+    hbm, peak_kind = measured_peaks()
 
-    def graphs_for(form):
-        return [capture(lambda t=t: plan.apply(t, form, stream=stream), stream)
+    def graphs_for(pl, form=bc.BC_FORM_BATCHED):
+        return [capture(lambda t=t: pl.apply(t, form, stream=stream), stream)
                 for t in tables]
 
-    # -- headline: batched form -------------------------------------------
-    g_batched = graphs_for(bc.BC_FORM_BATCHED)
+    # -- headline: batched form (one fork/join group of family kernels) -----
+    g_batched = graphs_for(plan)
     sampler = ClockSampler(local)
     sampler.start()
     per, total = time_steps([g.replay for g in g_batched], args.steps,
                             args.warmup, stream, world,
                             min_warm_s=args.min_warm_s)
     clocks = sampler.stop()
+    del g_batched
     t_step = total / args.steps
     t_max = reduce_max(total, world, device)
     value = nvals * args.steps * world / (t_max / 1e3)
-    kernel_ms = statistics.mean(per)
-    hbm, peak_kind = measured_peaks()
-    achieved = st["bytes_fwd"] / (kernel_ms / 1e3) / 1e9
+    step_gbs = st["bytes_fwd"] / (statistics.mean(per) / 1e3) / 1e9
+
+    # -- each family kernel on its own: the roofline of the dominant one ----
+    kernels = {}
+    if not args.only_batched:
+        for name, fp in family_plans(w, copies[0][1]).items():
+            fst = fp.stats()
+            gs = graphs_for(fp)
+            pk, tk = time_steps([g.replay for g in gs], min(args.steps, 500), 5,
+                                stream, world)
+            ms = statistics.mean(pk)
+            kernels[name] = {"ms": ms, "algorithmic_bytes": int(fst["bytes_fwd"]),
+                             "ghost_values": int(fst["ghost_values"]),
+                             "achieved_gbs": fst["bytes_fwd"] / (ms / 1e3) / 1e9}
+            kernels[name]["frac"] = kernels[name]["achieved_gbs"] / hbm
+            del gs, fp
+    if kernels:
+        dom_name = max(kernels, key=lambda k: kernels[k]["ms"])
+        dom = kernels[dom_name]
+    else:
+        dom_name, dom = "batched step", {"ms": statistics.mean(per),
+                                         "algorithmic_bytes": st["bytes_fwd"],
+                                         "achieved_gbs": step_gbs}
 
     # -- baselines: per-kind and per-sub-matrix launches ---------------------
-    forms = {"batched": {"ms": t_step, "launches_per_step": 1}}
+    forms = {"batched": {"ms": t_step, "launches_per_step": "1 graph: one kernel per family, concurrent"}}
     for name, form, nsteps in [] if args.only_batched else (("typewide", bc.BC_FORM_TYPEWIDE, min(args.steps, 200)),
                                ("per_bc", bc.BC_FORM_PER_BC, min(args.steps, 20))):
-        gs = graphs_for(form)
+        gs = graphs_for(plan, form)
         p2, tot2 = time_steps([g.replay for g in gs], nsteps, 3, stream, world)
         nl = 5 if form == bc.BC_FORM_TYPEWIDE else st["nsubmatrices"]
         forms[name] = {"ms": tot2 / nsteps, "launches_per_step": int(nl),
@@ -404,17 +489,13 @@ def run_ours(args, rank, world, local):
         forms["speedup_batched_vs_typewide"] = forms["typewide"]["ms"] / t_step
 
     # -- end to end through the host-buffer C-ABI call -----------------------
-    host = torch.empty(copies[0][0].numel(), dtype=copies[0][0].dtype).pin_memory()
-    host.copy_(copies[0][0].cpu())
-    hviews, pos = [], 0
-    for a in w["fields"]:
-        hviews.append(host[pos:pos + a.size].view(a.shape))
-        pos += a.size
-    hptrs = bc.slot_pointers(hviews)
-    dptrs = bc.slot_pointers(copies[0][1])
-    e2e_steps = 0 if args.only_batched else max(3, min(args.steps, 20))
     e2e = None
-    if e2e_steps:
+    if not args.only_batched:
+        host = torch.empty(copies[0][0].numel(), dtype=copies[0][0].dtype).pin_memory()
+        host.copy_(copies[0][0].cpu())
+        hptrs = bc.slot_pointers(layout_views(host, w, args.layout))
+        dptrs = bc.slot_pointers(copies[0][1])
+        e2e_steps = max(3, min(args.steps, 20))
         pe, tote = time_steps(
             [lambda: plan.apply_host(hptrs, dptrs, tables[0], stream=stream)],
             e2e_steps, 2, stream, world)
@@ -429,30 +510,37 @@ def run_ours(args, rank, world, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": w["dtype"], "data": "synthetic",
         "config": {"workload": desc, "ghost_values": int(nvals),
-                   "form": "batched, one graph-captured launch per step",
+                   "layout": LAYOUT_DESC[args.layout],
+                   "form": "batched: one graph launch, one kernel per family, concurrent",
                    "threads": st["form_threads"],
-                   "ctas_per_sm": st["form_ctas_per_sm"],
+                   "units_per_lane": st["units_per_lane"],
                    "l2": (f"{ncopies} rotating copies of the fields "
                           f"({ncopies * field_bytes / 1e9:.2f} GB), a copy is "
                           f"reused every {ncopies} steps"),
                    "parallelism": f"replicas x{world}"},
-        "hbm_gbs_useful": achieved,
-        "pct_of_8tbs": 100.0 * achieved / NOMINAL_HBM_GBS,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm,
+        "hbm_gbs_useful": step_gbs,
+        "pct_of_8tbs": 100.0 * step_gbs / NOMINAL_HBM_GBS,
+        "roofline": {"bound": "hbm", "kernel": dom_name,
+                     "achieved": dom["achieved_gbs"], "peak": hbm,
+                     "unit": "GB/s", "frac": dom["achieved_gbs"] / hbm,
                      "peak_source": peak_kind,
-                     "traffic": profiled_traffic(args.workload),
-                     "algorithmic_bytes_per_launch": int(st["bytes_fwd"]),
-                     "kernel_ms": kernel_ms},
+                     "traffic": profiled_traffic(f"{args.workload}:{args.layout}:{dom_name}"),
+                     "algorithmic_bytes_per_launch": int(dom["algorithmic_bytes"]),
+                     "kernel_ms": dom["ms"],
+                     "step": {"algorithmic_bytes": int(st["bytes_fwd"]),
+                              "achieved": step_gbs, "frac": step_gbs / hbm}},
+        "kernels": kernels,
         "forms": forms,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * n_family_kernels(st),
         "clocks": clocks,
     }
+    if not args.only_batched:
+        result["dram_floor"] = dram_floor(plan, w, copies[0][1], copies[0][0])
     if not args.only_batched and not args.no_variants:
-        # the same workload with every component stored level-innermost
-        result["layout_variants"] = {"level_innermost": measure_forward(
-            w, device, stream, min(args.steps, 500), 5, "level_innermost")}
+        other = "level_outermost" if args.layout == "level_innermost" else "level_innermost"
+        result["layout_variants"] = {other: measure_forward(
+            w, device, stream, min(args.steps, 500), 5, other, floor=True)}
         # the other workloads of the scope table, batched forward (+ adjoint)
         others = {}
         for name, fn, adj in (
@@ -471,6 +559,18 @@ def run_ours(args, rank, world, local):
         print(json.dumps(result))
 
 
+def n_family_kernels(st):
+    """Kernels of one batched apply: one per non-empty kernel family."""
+    k = st["ghost_values_kind"]
+    return sum(1 for v in (k[0] + k[1] + k[2], k[3], k[4]) if v)
+
+
+LAYOUT_DESC = {
+    "level_innermost": "levels innermost: each component stored [k][j][i][level]",
+    "level_outermost": "levels outermost: each component stored [level][k][j][i]",
+}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -480,6 +580,8 @@ def main():
     ap.add_argument("--workload", default="batching",
                     choices=["batching", "swe", "adjoint", "hpcg"])
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--layout", default="level_innermost",
+                    choices=["level_innermost", "level_outermost"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the layout variant and the other workloads")

@@ -48,14 +48,16 @@ struct alignas(16) Item {
   int32_t mode;            // ItemMode, or the chunk length (>= 2)
   int32_t u0, nunits;      // units [u0, u0 + nunits) of the unit space
   FastDiv vol;             // cells (rows) of the sub-matrix box / row group
-  FastDiv w0, w1;          // box extents on axes 0 and 1
   FastDiv lev;             // levels of the block (lev.d)
+  int32_t ctab;            // first row of the sub-matrix in the cell tables
   int32_t dst_slot, dst_slot2;
-  int32_t src_slot, p;
-  int32_t table;           // first table row of cell 0 of this component
+  int32_t src_slot;        // MAP source; CSR: the one slot all rows read, or -1
+  int32_t p;               // INTERP: stencil points; CSR: ELL row width
+  int32_t table;           // CONST / INTERP / CSR: first table row of cell 0
   int32_t comp;            // INTERP source components: u | v << 16
-  int32_t dst_org, dst_s0, dst_s1, dst_s2, dst_ls;   // element offsets
-  int32_t src_org, src_s0, src_s1, src_s2, src_ls;   // MAP source; CSR: ELL base
+  int32_t dst_ls, src_ls;  // level strides (elements)
+  int32_t src_org;         // CSR: ELL entry of row 0 of this component
+  int32_t pad[12];
 };
 static_assert(sizeof(Item) % 16 == 0, "Item must be a multiple of 16 bytes");
 
@@ -63,6 +65,10 @@ static_assert(sizeof(Item) % 16 == 0, "Item must be a multiple of 16 bytes");
 struct Ctx {
   void* const* slots;       // caller's device array of slot pointers
   const int32_t* slot_ls;   // level stride of every slot (elements)
+  // cell tables, one row per cell of every sub-matrix box: the element
+  // offset of the ghost cell (level 0) and, for maps, of its source cell
+  const int32_t* ctab_d;
+  const int32_t* ctab_s;
   // interpolation: per table row {slot_base of source block, node-0 offset,
   // node step, flags}, weights [row][kPMax], rotation [row][4]
   const int4* itp_idx;
@@ -94,11 +100,14 @@ enum Family : int32_t { FAM_STRUCT = 0, FAM_INTERP = 1, FAM_CSR = 2, FAM_ADJ = 3
 constexpr int kFamilies = 4;
 
 // Launcher (kernels.cu).  dtype: 0 = float, 1 = double.  One warp per item,
-// `threads` per CTA (32..512).  grid <= 0: one warp per item; otherwise a
-// persistent grid of `grid` CTAs whose warps claim items from counter[0..1].
+// `threads` per CTA (32..512).  grid <= 0: a plain grid with one warp per
+// item; otherwise `grid` resident CTAs whose warps walk the items with a
+// fixed stride, prefetching the next items' descriptors and slot pointers.
 cudaError_t launch_family(int dtype, int family, const Ctx& ctx,
                           const Item* items, int nitems, int threads, int grid,
-                          unsigned* counter, cudaStream_t s);
+                          cudaStream_t s);
+// CTAs of one family kernel that fit on an SM at once.
+int resident_ctas(int dtype, int family, int threads);
 
 // Cubed-sphere geometry (geometry.cu).
 struct CsPanels {

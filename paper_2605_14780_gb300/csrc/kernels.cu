@@ -14,6 +14,7 @@
 // lane keeps several independent values in flight; copies move integer bit
 // patterns so they are exact; table rows (stencils, CSR entries) are loaded
 // once per cell and level chunk.
+#include <cstddef>
 #include <cstdint>
 
 #include "bc_internal.h"
@@ -54,38 +55,39 @@ __device__ __forceinline__ void unit_of(int u, const Item& it, int& q, int& c) {
   q = u - c * (int)it.vol.d;
 }
 
-// cell q of the box -> (i, j, k) relative to the box origin
-__device__ __forceinline__ void cell_of(int q, const Item& it, int& i, int& j,
-                                        int& k) {
-  const int r = (int)fdiv((uint32_t)q, it.w0);
-  i = q - r * (int)it.w0.d;
-  k = (int)fdiv((uint32_t)r, it.w1);
-  j = r - k * (int)it.w1.d;
+// element offset (level 0) of cell q of the item's box, from the cell table
+__device__ __forceinline__ int dst_cell(const Item& it, const Ctx& c, int q) {
+  return __ldg(c.ctab_d + it.ctab + q);
 }
 
-__device__ __forceinline__ int dst_offset(const Item& it, int i, int j, int k) {
-  return it.dst_org + i * it.dst_s0 + j * it.dst_s1 + k * it.dst_s2;
-}
-
-__device__ __forceinline__ int dst_cell(const Item& it, int q) {
-  int i, j, k;
-  cell_of(q, it, i, j, k);
-  return dst_offset(it, i, j, k);
-}
+// Base pointers of an item's destination slot(s) and of its source slot (MAP,
+// or the common source slot of CSR rows), resolved once per item.
+struct Ptrs {
+  void* d;
+  void* d2;
+  const void* s;
+};
 
 // ---------------------------------------------------------------------------
 // zero / constant / map (matrix-free rows, Sec. III-B)
 // ---------------------------------------------------------------------------
-// Flat: every lane keeps U single values in flight.
-template <typename T>
-__device__ void structured_flat(const Item& it, const Ctx& c, int lane) {
+// Flat: every lane keeps U single values in flight.  The item fields the
+// loop needs are copied to registers first (the item itself sits in shared
+// memory), and the loop is specialised on the unit order.
+template <typename T, bool LEVEL>
+__device__ void structured_flat_t(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
   using B = typename BitsOf<T>::type;
   constexpr int U = kFlatUnroll;
   const int end = it.u0 + it.nunits;
-  B* dbase = static_cast<B*>(c.slots[it.dst_slot]);
-  const bool is_map = it.kind == IK_MAP;
-  const B* sbase = is_map ? static_cast<const B*>(c.slots[it.src_slot]) : nullptr;
-  const B* cval = static_cast<const B*>(c.const_val);
+  const FastDiv dv = LEVEL ? it.lev : it.vol;
+  const int div = (int)dv.d;
+  const int* __restrict__ cd = c.ctab_d + it.ctab;
+  const int* __restrict__ cs = c.ctab_s + it.ctab;
+  const int dls = it.dst_ls, sls = it.src_ls;
+  const int kind = it.kind;
+  B* dbase = static_cast<B*>(P.d);
+  const B* sbase = static_cast<const B*>(P.s);
+  const B* cval = static_cast<const B*>(c.const_val) + it.table;
   for (int f0 = it.u0 + lane; f0 < end; f0 += 32 * U) {
     int doff[U];
     B v[U];
@@ -95,15 +97,14 @@ __device__ void structured_flat(const Item& it, const Ctx& c, int lane) {
       doff[u] = -1;
       v[u] = B(0);
       if (f < end) {
-        int q, l, i, j, k;
-        flat_of(f, it, q, l);
-        cell_of(q, it, i, j, k);
-        doff[u] = dst_offset(it, i, j, k) + l * it.dst_ls;
-        if (is_map)
-          v[u] = ldg(sbase + (it.src_org + i * it.src_s0 + j * it.src_s1 +
-                              k * it.src_s2 + l * it.src_ls));
-        else if (it.kind == IK_CONST)
-          v[u] = ldg(cval + it.table + q);
+        const int a = (int)fdiv((uint32_t)f, dv);
+        const int q = LEVEL ? a : f - a * div;
+        const int l = LEVEL ? f - a * div : a;
+        doff[u] = __ldg(cd + q) + l * dls;
+        if (kind == IK_MAP)
+          v[u] = ldg(sbase + (__ldg(cs + q) + l * sls));
+        else if (kind == IK_CONST)
+          v[u] = ldg(cval + q);
       }
     }
 #pragma unroll
@@ -112,12 +113,21 @@ __device__ void structured_flat(const Item& it, const Ctx& c, int lane) {
   }
 }
 
+template <typename T>
+__device__ __forceinline__ void structured_flat(const Item& it, const Ptrs& P, const Ctx& c,
+                                                int lane) {
+  if (it.mode == MODE_FLAT_LEVEL)
+    structured_flat_t<T, true>(it, P, c, lane);
+  else
+    structured_flat_t<T, false>(it, P, c, lane);
+}
+
 // ---------------------------------------------------------------------------
 // interpolation rows (user Itp, Sec. III-B) with optional 2x2 rotation of a
 // covariant component pair (Sec. V-A): y = M (sum_k w_k x_u, sum_k w_k x_v)
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void interp_scalar_chunk(const Item& it, const Ctx& c, int lane) {
+__device__ void interp_scalar_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
   using B = typename BitsOf<T>::type;
   const int end = it.u0 + it.nunits;
   const int ls = it.dst_ls;
@@ -134,7 +144,7 @@ __device__ void interp_scalar_chunk(const Item& it, const Ctx& c, int lane) {
     const int su = ix.x + comp;
     const int sls = __ldg(c.slot_ls + su);
     const T* x = static_cast<const T*>(c.slots[su]) + (ix.y + l0 * sls);
-    T* d = static_cast<T*>(c.slots[it.dst_slot]) + (dst_cell(it, q) + l0 * ls);
+    T* d = static_cast<T*>(P.d) + (dst_cell(it, c, q) + l0 * ls);
     if (ix.w & kFlagSnap) {  // unit row: exact copy of node 0
       const B* s = reinterpret_cast<const B*>(x);
       B* db = reinterpret_cast<B*>(d);
@@ -168,7 +178,7 @@ __device__ void interp_scalar_chunk(const Item& it, const Ctx& c, int lane) {
 }
 
 template <typename T>
-__device__ void interp_pair_chunk(const Item& it, const Ctx& c, int lane) {
+__device__ void interp_pair_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
   constexpr int LU = kChunk / 2;
   const int end = it.u0 + it.nunits;
   const int ls = it.dst_ls;
@@ -185,9 +195,9 @@ __device__ void interp_pair_chunk(const Item& it, const Ctx& c, int lane) {
     const int slu = __ldg(c.slot_ls + su), slv = __ldg(c.slot_ls + sv);
     const T* xu = static_cast<const T*>(c.slots[su]) + (ix.y + l0 * slu);
     const T* xv = static_cast<const T*>(c.slots[sv]) + (ix.y + l0 * slv);
-    const int doff = dst_cell(it, q) + l0 * ls;
-    T* du = static_cast<T*>(c.slots[it.dst_slot]) + doff;
-    T* dv = static_cast<T*>(c.slots[it.dst_slot2]) + doff;
+    const int doff = dst_cell(it, c, q) + l0 * ls;
+    T* du = static_cast<T*>(P.d) + doff;
+    T* dv = static_cast<T*>(P.d2) + doff;
     const T* mr = static_cast<const T*>(c.itp_m) + row * 4;
     const T* wr = static_cast<const T*>(c.itp_w) + row * kPMax;
     const bool snap = ix.w & kFlagSnap;
@@ -225,14 +235,14 @@ __device__ void interp_pair_chunk(const Item& it, const Ctx& c, int lane) {
 // level-fastest order the lanes of a warp share a cell, so its table row is
 // one broadcast load and the node loads of the warp are contiguous.
 template <typename T, bool PAIR>
-__device__ void interp_flat(const Item& it, const Ctx& c, int lane) {
+__device__ void interp_flat(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
   using B = typename BitsOf<T>::type;
   constexpr int U = 4;
   const int end = it.u0 + it.nunits;
   const int p = it.p;
   const int cu = it.comp & 0xffff, cv = it.comp >> 16;
-  B* du = static_cast<B*>(c.slots[it.dst_slot]);
-  B* dv = PAIR ? static_cast<B*>(c.slots[it.dst_slot2]) : nullptr;
+  B* du = static_cast<B*>(P.d);
+  B* dv = PAIR ? static_cast<B*>(P.d2) : nullptr;
   for (int f0 = it.u0 + lane; f0 < end; f0 += 32 * U) {
     int doff[U];
     B ou[U], ov[U];
@@ -244,7 +254,7 @@ __device__ void interp_flat(const Item& it, const Ctx& c, int lane) {
       if (f < end) {
         int q, l;
         flat_of(f, it, q, l);
-        doff[u] = dst_cell(it, q) + l * it.dst_ls;
+        doff[u] = dst_cell(it, c, q) + l * it.dst_ls;
         const int row = it.table + q;
         const int4 ix = __ldg(c.itp_idx + row);
         const int su = ix.x + cu;
@@ -291,9 +301,28 @@ __device__ void interp_flat(const Item& it, const Ctx& c, int lane) {
 // user CSR rows (Table III: F_NNZ / F_COL / F_DATA), ELL-packed: row q of the
 // item's component has its entries at src_org + q * p
 // ---------------------------------------------------------------------------
+// When every entry of the item's rows reads one slot (P.s, level stride
+// src_ls), the per-entry slot lookups are skipped.
 template <typename T>
-__device__ void csr_chunk(const Item& it, const Ctx& c, int lane) {
-  constexpr int E = 8;  // rows up to E entries: all entry loads issued at once
+__device__ __forceinline__ const T* csr_src(const Item& it, const Ptrs& P, const Ctx& c,
+                                             int e, int l, int& sls) {
+  if (P.s) {
+    sls = it.src_ls;
+    return static_cast<const T*>(P.s) + (__ldg(c.csr_off + e) + l * sls);
+  }
+  const int s = __ldg(c.csr_slot + e);
+  sls = __ldg(c.slot_ls + s);
+  return static_cast<const T*>(c.slots[s]) + (__ldg(c.csr_off + e) + l * sls);
+}
+
+// Rows are processed E entries at a time: the E offsets and values load
+// together, then the E x E-level source loads, so one row costs two memory
+// latencies per E entries instead of two per entry.
+constexpr int kCsrBatch = 8;
+
+template <typename T>
+__device__ void csr_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
+  constexpr int E = kCsrBatch;
   const int end = it.u0 + it.nunits;
   const int ls = it.dst_ls;
   const int chn = it.mode;
@@ -307,39 +336,27 @@ __device__ void csr_chunk(const Item& it, const Ctx& c, int lane) {
     const int row = it.table + q;
     const int nnz = __ldg(c.csr_nnz + row);
     const int e0 = it.src_org + q * W;
-    T* d = static_cast<T*>(c.slots[it.dst_slot]) + (dst_cell(it, q) + l0 * ls);
+    T* d = static_cast<T*>(P.d) + (dst_cell(it, c, q) + l0 * ls);
     T acc[kChunk];
 #pragma unroll
     for (int l = 0; l < kChunk; ++l) acc[l] = T(0);
-    if (W <= E) {
-      int es[E], eo[E];
-      T ea[E];
+    for (int eb = 0; eb < nnz; eb += E) {
+      const T* xs[E];
+      int sl[E];
+      T a[E];
 #pragma unroll
       for (int e = 0; e < E; ++e)
-        if (e < nnz) {
-          es[e] = __ldg(c.csr_slot + e0 + e);
-          eo[e] = __ldg(c.csr_off + e0 + e);
-          ea[e] = ldg(val + e0 + e);
+        if (eb + e < nnz) {
+          xs[e] = csr_src<T>(it, P, c, e0 + eb + e, l0, sl[e]);
+          a[e] = ldg(val + e0 + eb + e);
         }
 #pragma unroll
       for (int e = 0; e < E; ++e)
-        if (e < nnz) {
-          const int sls = __ldg(c.slot_ls + es[e]);
-          const T* x = static_cast<const T*>(c.slots[es[e]]) + (eo[e] + l0 * sls);
+        if (eb + e < nnz) {
 #pragma unroll
           for (int l = 0; l < kChunk; ++l)
-            if (l < nl) acc[l] = fma(ea[e], ldg(x + l * sls), acc[l]);
+            if (l < nl) acc[l] = fma(a[e], ldg(xs[e] + l * sl[e]), acc[l]);
         }
-    } else {
-      for (int e = 0; e < nnz; ++e) {
-        const int s = __ldg(c.csr_slot + e0 + e);
-        const T a = ldg(val + e0 + e);
-        const int sls = __ldg(c.slot_ls + s);
-        const T* x = static_cast<const T*>(c.slots[s]) + (__ldg(c.csr_off + e0 + e) + l0 * sls);
-#pragma unroll
-        for (int l = 0; l < kChunk; ++l)
-          if (l < nl) acc[l] = fma(a, ldg(x + l * sls), acc[l]);
-      }
     }
     const T rhs = ldg(static_cast<const T*>(c.csr_rhs) + row);
 #pragma unroll
@@ -349,40 +366,33 @@ __device__ void csr_chunk(const Item& it, const Ctx& c, int lane) {
 }
 
 template <typename T>
-__device__ void csr_flat(const Item& it, const Ctx& c, int lane) {
-  constexpr int U = 4;
+__device__ void csr_flat(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
+  constexpr int E = kCsrBatch;
   const int end = it.u0 + it.nunits;
   const int W = it.p;
   const T* val = static_cast<const T*>(c.csr_val);
-  T* dbase = static_cast<T*>(c.slots[it.dst_slot]);
-  for (int f0 = it.u0 + lane; f0 < end; f0 += 32 * U) {
-    int doff[U];
-    T out[U];
+  T* dbase = static_cast<T*>(P.d);
+  for (int f = it.u0 + lane; f < end; f += 32) {
+    int q, l;
+    flat_of(f, it, q, l);
+    const int row = it.table + q;
+    const int nnz = __ldg(c.csr_nnz + row);
+    const int e0 = it.src_org + q * W;
+    T acc = ldg(static_cast<const T*>(c.csr_rhs) + row);
+    for (int eb = 0; eb < nnz; eb += E) {
+      T x[E], a[E];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int f = f0 + 32 * u;
-      doff[u] = -1;
-      out[u] = T(0);
-      if (f < end) {
-        int q, l;
-        flat_of(f, it, q, l);
-        doff[u] = dst_cell(it, q) + l * it.dst_ls;
-        const int row = it.table + q;
-        const int nnz = __ldg(c.csr_nnz + row);
-        const int e0 = it.src_org + q * W;
-        T acc = T(0);
-        for (int e = 0; e < nnz; ++e) {
-          const int s = __ldg(c.csr_slot + e0 + e);
-          const T* x = static_cast<const T*>(c.slots[s]) +
-                       (__ldg(c.csr_off + e0 + e) + l * __ldg(c.slot_ls + s));
-          acc = fma(ldg(val + e0 + e), ldg(x), acc);
+      for (int e = 0; e < E; ++e)
+        if (eb + e < nnz) {
+          int sls;
+          x[e] = ldg(csr_src<T>(it, P, c, e0 + eb + e, l, sls));
+          a[e] = ldg(val + e0 + eb + e);
         }
-        out[u] = acc + ldg(static_cast<const T*>(c.csr_rhs) + row);
-      }
-    }
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (doff[u] >= 0) dbase[doff[u]] = out[u];
+      for (int e = 0; e < E; ++e)
+        if (eb + e < nnz) acc = fma(a[e], x[e], acc);
+    }
+    dbase[dst_cell(it, c, q) + l * it.dst_ls] = acc;
   }
 }
 
@@ -390,8 +400,11 @@ __device__ void csr_flat(const Item& it, const Ctx& c, int lane) {
 // adjoint gather: x_bar_j += sum_i A_ij y_bar_i over the stored transpose,
 // entries in ascending ghost order (deterministic, no atomics)
 // ---------------------------------------------------------------------------
+constexpr int kAdjBatch = 4;
+
 template <typename T>
-__device__ void adj_chunk(const Item& it, const Ctx& c, int lane) {
+__device__ void adj_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
+  constexpr int E = kAdjBatch;
   const int end = it.u0 + it.nunits;
   const int chn = it.mode;
   const T* wv = static_cast<const T*>(c.aent_w);
@@ -404,18 +417,29 @@ __device__ void adj_chunk(const Item& it, const Ctx& c, int lane) {
     const int slot = __ldg(c.arow_slot + r);
     const int ls = __ldg(c.slot_ls + slot);
     T* xb = static_cast<T*>(c.slots[slot]) + (__ldg(c.arow_off + r) + l0 * ls);
-    const int64_t e0 = __ldg(c.adj_ptr + r), e1 = __ldg(c.adj_ptr + r + 1);
+    const int e0 = (int)__ldg(c.adj_ptr + r), e1 = (int)__ldg(c.adj_ptr + r + 1);
     T acc[kChunk];
 #pragma unroll
     for (int l = 0; l < kChunk; ++l) acc[l] = (l < nl) ? xb[l * ls] : T(0);
-    for (int64_t e = e0; e < e1; ++e) {
-      const int gs = __ldg(c.aent_slot + e);
-      const T a = ldg(wv + e);
-      const int gls = __ldg(c.slot_ls + gs);
-      const T* y = static_cast<const T*>(c.slots[gs]) + (__ldg(c.aent_off + e) + l0 * gls);
+    for (int eb = e0; eb < e1; eb += E) {
+      const T* ys[E];
+      int gl[E];
+      T a[E];
 #pragma unroll
-      for (int l = 0; l < kChunk; ++l)
-        if (l < nl) acc[l] = fma(a, y[l * gls], acc[l]);
+      for (int e = 0; e < E; ++e)
+        if (eb + e < e1) {
+          const int gs = __ldg(c.aent_slot + eb + e);
+          gl[e] = __ldg(c.slot_ls + gs);
+          ys[e] = static_cast<const T*>(c.slots[gs]) + (__ldg(c.aent_off + eb + e) + l0 * gl[e]);
+          a[e] = ldg(wv + eb + e);
+        }
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (eb + e < e1) {
+#pragma unroll
+          for (int l = 0; l < kChunk; ++l)
+            if (l < nl) acc[l] = fma(a[e], ys[e][l * gl[e]], acc[l]);
+        }
     }
 #pragma unroll
     for (int l = 0; l < kChunk; ++l)
@@ -424,72 +448,67 @@ __device__ void adj_chunk(const Item& it, const Ctx& c, int lane) {
 }
 
 template <typename T>
-__device__ void adj_flat(const Item& it, const Ctx& c, int lane) {
-  constexpr int U = 4;
+__device__ void adj_flat(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
+  constexpr int E = kAdjBatch;
   const int end = it.u0 + it.nunits;
   const T* wv = static_cast<const T*>(c.aent_w);
-  for (int f0 = it.u0 + lane; f0 < end; f0 += 32 * U) {
-    T* dst[U];
-    T out[U];
+  for (int f = it.u0 + lane; f < end; f += 32) {
+    int q, l;
+    flat_of(f, it, q, l);
+    const int r = it.table + q;
+    const int slot = __ldg(c.arow_slot + r);
+    T* xb = static_cast<T*>(c.slots[slot]) +
+            (__ldg(c.arow_off + r) + l * __ldg(c.slot_ls + slot));
+    const int e0 = (int)__ldg(c.adj_ptr + r), e1 = (int)__ldg(c.adj_ptr + r + 1);
+    T acc = *xb;
+    for (int eb = e0; eb < e1; eb += E) {
+      T y[E], a[E];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int f = f0 + 32 * u;
-      dst[u] = nullptr;
-      out[u] = T(0);
-      if (f < end) {
-        int q, l;
-        flat_of(f, it, q, l);
-        const int r = it.table + q;
-        const int slot = __ldg(c.arow_slot + r);
-        T* xb = static_cast<T*>(c.slots[slot]) +
-                (__ldg(c.arow_off + r) + l * __ldg(c.slot_ls + slot));
-        const int64_t e0 = __ldg(c.adj_ptr + r), e1 = __ldg(c.adj_ptr + r + 1);
-        T acc = *xb;
-        for (int64_t e = e0; e < e1; ++e) {
-          const int gs = __ldg(c.aent_slot + e);
-          const T* y = static_cast<const T*>(c.slots[gs]) +
-                       (__ldg(c.aent_off + e) + l * __ldg(c.slot_ls + gs));
-          acc = fma(ldg(wv + e), *y, acc);
+      for (int e = 0; e < E; ++e)
+        if (eb + e < e1) {
+          const int gs = __ldg(c.aent_slot + eb + e);
+          const T* yp = static_cast<const T*>(c.slots[gs]) +
+                        (__ldg(c.aent_off + eb + e) + l * __ldg(c.slot_ls + gs));
+          y[e] = *yp;
+          a[e] = ldg(wv + eb + e);
         }
-        dst[u] = xb;
-        out[u] = acc;
-      }
-    }
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (dst[u]) *dst[u] = out[u];
+      for (int e = 0; e < E; ++e)
+        if (eb + e < e1) acc = fma(a[e], y[e], acc);
+    }
+    *xb = acc;
   }
 }
 
 // Kernel families: one kernel per family keeps each family's register
 // budget (and so its occupancy) independent of the others.
 template <typename T, int FAM>
-__device__ __forceinline__ void run_item(const Item& it, const Ctx& c, int lane) {
+__device__ __forceinline__ void run_item(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
   const bool flat = it.mode < 2;
   if constexpr (FAM == FAM_STRUCT) {
-    structured_flat<T>(it, c, lane);
+    structured_flat<T>(it, P, c, lane);
   } else if constexpr (FAM == FAM_INTERP) {
     if (it.kind == IK_INTERP_PAIR) {
       if (flat)
-        interp_flat<T, true>(it, c, lane);
+        interp_flat<T, true>(it, P, c, lane);
       else
-        interp_pair_chunk<T>(it, c, lane);
+        interp_pair_chunk<T>(it, P, c, lane);
     } else {
       if (flat)
-        interp_flat<T, false>(it, c, lane);
+        interp_flat<T, false>(it, P, c, lane);
       else
-        interp_scalar_chunk<T>(it, c, lane);
+        interp_scalar_chunk<T>(it, P, c, lane);
     }
   } else if constexpr (FAM == FAM_CSR) {
     if (flat)
-      csr_flat<T>(it, c, lane);
+      csr_flat<T>(it, P, c, lane);
     else
-      csr_chunk<T>(it, c, lane);
+      csr_chunk<T>(it, P, c, lane);
   } else {
     if (flat)
-      adj_flat<T>(it, c, lane);
+      adj_flat<T>(it, P, c, lane);
     else
-      adj_chunk<T>(it, c, lane);
+      adj_chunk<T>(it, P, c, lane);
   }
 }
 
@@ -501,12 +520,33 @@ __device__ __forceinline__ void load_item(Item* dst, const Item* src, int lane) 
 }
 
 // Resident CTAs the register budget is set for: the structured family is
-// lean (about 40 registers, 48 warps per SM); the table families get 64.
+// lean (48 registers, 40 warps per SM); the table families get 64.
 template <int FAM, int THREADS> struct Occ {
-  static constexpr int kWarps = FAM == FAM_STRUCT ? 48 : 32;
+  static constexpr int kWarps = FAM == FAM_STRUCT ? 40 : 32;
   static constexpr int kMinBlocks = (kWarps * 32) / THREADS > 0 ? (kWarps * 32) / THREADS : 1;
 };
 
+constexpr int kWordDst = offsetof(Item, dst_slot) / 4;
+constexpr int kWordDst2 = offsetof(Item, dst_slot2) / 4;
+constexpr int kWordSrc = offsetof(Item, src_slot) / 4;
+
+// The lanes holding an item's slot words look up the slot pointers.
+__device__ __forceinline__ void* lookup_slot(const Ctx& c, int word, int lane) {
+  return ((lane == kWordDst || lane == kWordDst2 || lane == kWordSrc) && word >= 0)
+             ? c.slots[word]
+             : nullptr;
+}
+
+__device__ __forceinline__ Ptrs gather_ptrs(void* mine) {
+  const unsigned long long v = reinterpret_cast<unsigned long long>(mine);
+  Ptrs P;
+  P.d = reinterpret_cast<void*>(__shfl_sync(0xffffffffu, v, kWordDst));
+  P.d2 = reinterpret_cast<void*>(__shfl_sync(0xffffffffu, v, kWordDst2));
+  P.s = reinterpret_cast<const void*>(__shfl_sync(0xffffffffu, v, kWordSrc));
+  return P;
+}
+
+// Plain grid: warp w of CTA b processes item b * warps + w.
 template <typename T, int THREADS, int FAM>
 __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     k_items(Ctx c, const Item* __restrict__ items, int nitems) {
@@ -514,72 +554,109 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int idx = blockIdx.x * (THREADS / 32) + warp;
   if (idx >= nitems) return;
-  load_item(&sit[warp], items + idx, lane);
-  run_item<T, FAM>(sit[warp], c, lane);
+  const int w = __ldg(reinterpret_cast<const int*>(items + idx) + lane);
+  reinterpret_cast<int*>(&sit[warp])[lane] = w;
+  const Ptrs P = gather_ptrs(lookup_slot(c, w, lane));
+  __syncwarp();
+  run_item<T, FAM>(sit[warp], P, c, lane);
 }
 
-// Persistent form: warps claim items from counter[0]; the last warp to
-// finish resets both counters for the next launch.  No warp waits on another.
+// Streaming form: a grid of resident warps walks the items with a fixed
+// stride; while a warp works on one item, the descriptor of the item after
+// next and the slot pointers of the next one are already in flight.  No warp
+// waits on another.
 template <typename T, int THREADS, int FAM>
 __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
-    k_persistent(Ctx c, const Item* __restrict__ items, int nitems,
-                 unsigned* counter) {
+    k_stream(Ctx c, const Item* __restrict__ items, int nitems) {
   __shared__ Item sit[THREADS / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int stride = gridDim.x * (THREADS / 32);
+  const int* iw = reinterpret_cast<const int*>(items);
+  int cur = blockIdx.x * (THREADS / 32) + warp;
+  if (cur >= nitems) return;
+  int w_cur = __ldg(iw + (int64_t)cur * 32 + lane);
+  void* p_cur = lookup_slot(c, w_cur, lane);
+  int nxt = cur + stride;
+  int w_nxt = nxt < nitems ? __ldg(iw + (int64_t)nxt * 32 + lane) : 0;
   for (;;) {
-    int idx = 0;
-    if (lane == 0) idx = (int)atomicAdd(counter, 1u);
-    idx = __shfl_sync(0xffffffffu, idx, 0);
-    if (idx >= nitems) break;
-    load_item(&sit[warp], items + idx, lane);
-    run_item<T, FAM>(sit[warp], c, lane);
+    reinterpret_cast<int*>(&sit[warp])[lane] = w_cur;
+    void* p_nxt = nxt < nitems ? lookup_slot(c, w_nxt, lane) : nullptr;
+    const int nxt2 = nxt + stride;
+    const int w_nxt2 = nxt2 < nitems ? __ldg(iw + (int64_t)nxt2 * 32 + lane) : 0;
+    const Ptrs P = gather_ptrs(p_cur);
     __syncwarp();
-  }
-  if (lane == 0) {
-    __threadfence();
-    const unsigned nwarps = gridDim.x * (THREADS / 32);
-    if (atomicAdd(counter + 1, 1u) == nwarps - 1) {
-      atomicExch(counter, 0u);
-      atomicExch(counter + 1, 0u);
-      __threadfence();
-    }
+    run_item<T, FAM>(sit[warp], P, c, lane);
+    __syncwarp();
+    if (nxt >= nitems) break;
+    w_cur = w_nxt;
+    p_cur = p_nxt;
+    nxt = nxt2;
+    w_nxt = w_nxt2;
   }
 }
 
 template <typename T, int THREADS, int FAM>
 cudaError_t launch_t(const Ctx& c, const Item* items, int nitems, int grid,
-                     unsigned* counter, cudaStream_t s) {
+                     cudaStream_t s) {
   const int wpb = THREADS / 32;
   const int need = (nitems + wpb - 1) / wpb;
-  if (grid <= 0 || counter == nullptr) {
+  if (grid <= 0)
     k_items<T, THREADS, FAM><<<need, THREADS, 0, s>>>(c, items, nitems);
-  } else {
-    k_persistent<T, THREADS, FAM><<<grid < need ? grid : need, THREADS, 0, s>>>(
-        c, items, nitems, counter);
-  }
+  else
+    k_stream<T, THREADS, FAM><<<grid < need ? grid : need, THREADS, 0, s>>>(c, items, nitems);
   return cudaGetLastError();
+}
+
+template <typename T, int THREADS, int FAM>
+int resident_t() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream<T, THREADS, FAM>, THREADS, 0) !=
+      cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
 }
 
 template <typename T, int FAM>
 cudaError_t launch_fam(const Ctx& c, const Item* items, int nitems, int threads,
-                       int grid, unsigned* counter, cudaStream_t s) {
+                       int grid, cudaStream_t s) {
   switch (threads) {
-    case 32: return launch_t<T, 32, FAM>(c, items, nitems, grid, counter, s);
-    case 64: return launch_t<T, 64, FAM>(c, items, nitems, grid, counter, s);
-    case 128: return launch_t<T, 128, FAM>(c, items, nitems, grid, counter, s);
-    case 512: return launch_t<T, 512, FAM>(c, items, nitems, grid, counter, s);
-    default: return launch_t<T, 256, FAM>(c, items, nitems, grid, counter, s);
+    case 32: return launch_t<T, 32, FAM>(c, items, nitems, grid, s);
+    case 64: return launch_t<T, 64, FAM>(c, items, nitems, grid, s);
+    case 128: return launch_t<T, 128, FAM>(c, items, nitems, grid, s);
+    case 512: return launch_t<T, 512, FAM>(c, items, nitems, grid, s);
+    default: return launch_t<T, 256, FAM>(c, items, nitems, grid, s);
+  }
+}
+
+template <typename T, int FAM>
+int resident_fam(int threads) {
+  switch (threads) {
+    case 32: return resident_t<T, 32, FAM>();
+    case 64: return resident_t<T, 64, FAM>();
+    case 128: return resident_t<T, 128, FAM>();
+    case 512: return resident_t<T, 512, FAM>();
+    default: return resident_t<T, 256, FAM>();
   }
 }
 
 template <typename T>
 cudaError_t launch_any(int fam, const Ctx& c, const Item* items, int nitems,
-                       int threads, int grid, unsigned* counter, cudaStream_t s) {
+                       int threads, int grid, cudaStream_t s) {
   switch (fam) {
-    case FAM_STRUCT: return launch_fam<T, FAM_STRUCT>(c, items, nitems, threads, grid, counter, s);
-    case FAM_INTERP: return launch_fam<T, FAM_INTERP>(c, items, nitems, threads, grid, counter, s);
-    case FAM_CSR: return launch_fam<T, FAM_CSR>(c, items, nitems, threads, grid, counter, s);
-    default: return launch_fam<T, FAM_ADJ>(c, items, nitems, threads, grid, counter, s);
+    case FAM_STRUCT: return launch_fam<T, FAM_STRUCT>(c, items, nitems, threads, grid, s);
+    case FAM_INTERP: return launch_fam<T, FAM_INTERP>(c, items, nitems, threads, grid, s);
+    case FAM_CSR: return launch_fam<T, FAM_CSR>(c, items, nitems, threads, grid, s);
+    default: return launch_fam<T, FAM_ADJ>(c, items, nitems, threads, grid, s);
+  }
+}
+
+template <typename T>
+int resident_any(int fam, int threads) {
+  switch (fam) {
+    case FAM_STRUCT: return resident_fam<T, FAM_STRUCT>(threads);
+    case FAM_INTERP: return resident_fam<T, FAM_INTERP>(threads);
+    case FAM_CSR: return resident_fam<T, FAM_CSR>(threads);
+    default: return resident_fam<T, FAM_ADJ>(threads);
   }
 }
 
@@ -587,10 +664,15 @@ cudaError_t launch_any(int fam, const Ctx& c, const Item* items, int nitems,
 
 cudaError_t launch_family(int dtype, int family, const Ctx& ctx,
                           const Item* items, int nitems, int threads, int grid,
-                          unsigned* counter, cudaStream_t s) {
+                          cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
-  return dtype == 1 ? launch_any<double>(family, ctx, items, nitems, threads, grid, counter, s)
-                    : launch_any<float>(family, ctx, items, nitems, threads, grid, counter, s);
+  return dtype == 1 ? launch_any<double>(family, ctx, items, nitems, threads, grid, s)
+                    : launch_any<float>(family, ctx, items, nitems, threads, grid, s);
+}
+
+int resident_ctas(int dtype, int family, int threads) {
+  return dtype == 1 ? resident_any<double>(family, threads)
+                    : resident_any<float>(family, threads);
 }
 
 }  // namespace bcg

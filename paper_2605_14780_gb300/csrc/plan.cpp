@@ -58,6 +58,8 @@ struct Sub {
   int p = 0, geometry = 0, rot_u = -1, rot_v = -1;
   int table = 0;  // CONST/CSR: first row of comp 0; INTERP: first cell row
   int ell_base = 0, ell_w = 1;  // CSR: ELL entries of row 0, row width
+  std::vector<int> csr_common;  // CSR: the one slot a component's rows read, or -1
+  int ctab = 0;                 // first row in the cell tables
 };
 
 struct ExplicitRows {
@@ -107,6 +109,8 @@ struct bc_plan {
   std::vector<int32_t> csr_slot, csr_off;
   std::vector<double> csr_val, csr_rhs;
   std::vector<double> const_val;
+  // cell tables: ghost-cell offset and (maps) source-cell offset, level 0
+  std::vector<int32_t> ctab_d, ctab_s;
   // transpose
   std::vector<int32_t> arow_slot, arow_off;
   std::vector<int64_t> adj_ptr{0};
@@ -136,7 +140,6 @@ struct bc_plan {
   }
   Item* d_adj = nullptr;
   Item* d_adj_zero = nullptr;
-  unsigned* d_counter = nullptr;
   int num_sms = 1;
   bc_plan_opts opts{};
   bc_stats stats{};
@@ -399,6 +402,15 @@ bc_status add_csr(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
       P->csr_nnz.push_back((int32_t)(m.row_ptr[r + 1] - m.row_ptr[r]));
     });
     if (st != BC_OK) return st;
+    // the one slot all rows of this component read, if there is one
+    int common = -2;
+    for (int64_t r = (int64_t)c * s.vol; r < (int64_t)(c + 1) * s.vol && common != -1; ++r)
+      for (int64_t e = m.row_ptr[r]; e < m.row_ptr[r + 1]; ++e) {
+        const int cs = P->slot_base[m.col_block[e]] + m.col_comp[e];
+        if (common == -2) common = cs;
+        else if (common != cs) { common = -1; break; }
+      }
+    s.csr_common.push_back(common < 0 ? -1 : common);
   }
   return BC_OK;
 }
@@ -607,13 +619,8 @@ void item_common(const bc_plan* P, const Sub& s, int comp, Item& it) {
   it.dst_slot2 = -1;
   it.src_slot = -1;
   it.vol = make_div((uint32_t)s.vol);
-  it.w0 = make_div((uint32_t)s.W[0]);
-  it.w1 = make_div((uint32_t)s.W[1]);
   it.lev = make_div((uint32_t)B.nlevels);
-  it.dst_org = (int32_t)cell_offset(B, s.lo[0], s.lo[1], s.lo[2]);
-  it.dst_s0 = (int32_t)B.stride[0];
-  it.dst_s1 = (int32_t)B.stride[1];
-  it.dst_s2 = (int32_t)B.stride[2];
+  it.ctab = s.ctab;
   it.dst_ls = (int32_t)(B.nlevels > 1 ? B.level_stride : 0);
 }
 
@@ -685,15 +692,6 @@ void build_items(bc_plan* P) {
           if (s.kind == BC_MAP) {
             const bc_block& S = P->blocks[s.src_block];
             it.src_slot = P->slot_base[s.src_block] + c;
-            int img[3];
-            const int lo[3] = {s.lo[0], s.lo[1], s.lo[2]};
-            for (int d = 0; d < 3; ++d) img[d] = s.sign[d] * lo[s.perm[d]] + s.offset[d];
-            it.src_org = (int32_t)cell_offset(S, img[0], img[1], img[2]);
-            int64_t st[3] = {0, 0, 0};
-            for (int d = 0; d < 3; ++d) st[s.perm[d]] = s.sign[d] * S.stride[d];
-            it.src_s0 = (int32_t)st[0];
-            it.src_s1 = (int32_t)st[1];
-            it.src_s2 = (int32_t)st[2];
             it.src_ls = (int32_t)(S.nlevels > 1 ? S.level_stride : 0);
           }
           structured_emit(out, it, B, s.vol);
@@ -719,6 +717,11 @@ void build_items(bc_plan* P) {
           it.table = s.table + (int)ci * s.vol;
           it.p = s.ell_w;
           it.src_org = s.ell_base + (int)ci * s.vol * s.ell_w;
+          it.src_slot = s.csr_common[ci];
+          if (it.src_slot >= 0) {
+            const bc_block& S = P->blocks[P->slot_block[it.src_slot]];
+            it.src_ls = (int32_t)(S.nlevels > 1 ? S.level_stride : 0);
+          }
           table_emit(out, it, B, s.vol);
           break;
         }
@@ -776,8 +779,6 @@ void build_items(bc_plan* P) {
     Item it{};
     it.kind = IK_ADJ;
     it.vol = make_div((uint32_t)(r1 - r0));
-    it.w0 = make_div(1);
-    it.w1 = make_div(1);
     it.lev = make_div((uint32_t)B0.nlevels);
     it.table = r0;
     table_emit(P->adj_items, it, B0, r1 - r0);
@@ -850,6 +851,8 @@ bc_status upload_tables(bc_plan* P) {
   const size_t S = P->esize;
   Layout L;
   const size_t o_ls = L.take(P->slot_ls.size() * 4);
+  const size_t o_cd = L.take(P->ctab_d.size() * 4);
+  const size_t o_cs2 = L.take(P->ctab_s.size() * 4);
   const size_t o_idx = L.take(P->itp_idx.size() * sizeof(int4));
   const size_t o_w = L.take(P->itp_w.size() * S);
   const size_t o_m = L.take(P->itp_m.size() * S);
@@ -867,6 +870,8 @@ bc_status upload_tables(bc_plan* P) {
   const size_t o_ew = L.take(P->aent_w.size() * S);
   std::vector<char> host(L.off + 256, 0);
   put_raw(host, o_ls, P->slot_ls);
+  put_raw(host, o_cd, P->ctab_d);
+  put_raw(host, o_cs2, P->ctab_s);
   put_raw(host, o_idx, P->itp_idx);
   put_raw(host, o_cp, P->csr_nnz);
   put_raw(host, o_cs, P->csr_slot);
@@ -902,6 +907,8 @@ bc_status upload_tables(bc_plan* P) {
   char* b = static_cast<char*>(P->tables.base);
   Ctx& c = P->ctx;
   c.slot_ls = reinterpret_cast<const int32_t*>(b + o_ls);
+  c.ctab_d = reinterpret_cast<const int32_t*>(b + o_cd);
+  c.ctab_s = reinterpret_cast<const int32_t*>(b + o_cs2);
   c.itp_idx = reinterpret_cast<const int4*>(b + o_idx);
   c.itp_w = b + o_w;
   c.itp_m = b + o_m;
@@ -931,7 +938,6 @@ bc_status upload_work(bc_plan* P) {
   for (int f = 0; f < kFamilies; ++f) o_f[f] = L.take(P->fam_items[f].size() * sizeof(Item));
   const size_t o_a = L.take(P->adj_items.size() * sizeof(Item));
   const size_t o_z = L.take(P->adj_zero.size() * sizeof(Item));
-  const size_t o_c = L.take(2 * kFamilies * sizeof(unsigned));
   std::vector<char> host(L.off + 256, 0);
   put_raw(host, o_i, P->items);
   for (int f = 0; f < kFamilies; ++f) put_raw(host, o_f[f], P->fam_items[f]);
@@ -950,7 +956,6 @@ bc_status upload_work(bc_plan* P) {
   for (int f = 0; f < kFamilies; ++f) P->d_fam[f] = reinterpret_cast<Item*>(b + o_f[f]);
   P->d_adj = reinterpret_cast<Item*>(b + o_a);
   P->d_adj_zero = reinterpret_cast<Item*>(b + o_z);
-  P->d_counter = reinterpret_cast<unsigned*>(b + o_c);
   return BC_OK;
 }
 
@@ -1069,6 +1074,22 @@ bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_
     }
     if (st != BC_OK) return st;
   }
+  // cell tables: every box cell's offset, and the source cell of maps
+  for (Sub& s2 : P->subs) {
+    const bc_block& B = P->blocks[s2.block];
+    s2.ctab = (int)P->ctab_d.size();
+    for_box(s2, [&](int, int i, int j, int k) {
+      P->ctab_d.push_back((int32_t)cell_offset(B, i, j, k));
+      if (s2.kind == BC_MAP) {
+        const int g[3] = {i, j, k};
+        int src[3];
+        for (int d = 0; d < 3; ++d) src[d] = s2.sign[d] * g[s2.perm[d]] + s2.offset[d];
+        P->ctab_s.push_back((int32_t)cell_offset(P->blocks[s2.src_block], src[0], src[1], src[2]));
+      } else {
+        P->ctab_s.push_back(0);
+      }
+    });
+  }
   if (P->opts.strict_cover) {
     for (int slot = 0; slot < P->nslots; ++slot) {
       const bc_block& B = P->blocks[P->slot_block[slot]];
@@ -1133,8 +1154,12 @@ bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_
   return BC_OK;
 }
 
-int persistent_grid(const bc_plan* P) {
-  return P->opts.ctas_per_sm > 0 ? P->opts.ctas_per_sm * P->num_sms : 0;
+// streaming grid of a family: ctas_per_sm resident CTAs per SM (capped by
+// what fits), or 0 for a plain grid with one warp per item
+int stream_grid(const bc_plan* P, int fam) {
+  if (P->opts.ctas_per_sm <= 0) return 0;
+  const int fit = resident_ctas(P->dtype, fam, P->opts.threads);
+  return std::min(P->opts.ctas_per_sm, fit) * P->num_sms;
 }
 
 bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t s) {
@@ -1147,15 +1172,13 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
     int fams[kFamilies], nf = 0;
     for (int f = 0; f < kFamilies; ++f)
       if (!P->fam_items[f].empty()) fams[nf++] = f;
-    const int grid = persistent_grid(P);
     if (nf > 1 && (e = cudaEventRecord(P->ev_fork, s)) != cudaSuccess)
       return cuda_fail(e, "fork event");
     for (int t = 0; t < nf && e == cudaSuccess; ++t) {
       cudaStream_t st = t == 0 ? s : P->aux[t - 1];
       if (t > 0 && (e = cudaStreamWaitEvent(st, P->ev_fork, 0)) != cudaSuccess) break;
       e = launch_family(P->dtype, fams[t], c, P->d_fam[fams[t]],
-                        (int)P->fam_items[fams[t]].size(), T, grid,
-                        P->d_counter + 2 * fams[t], st);
+                        (int)P->fam_items[fams[t]].size(), T, stream_grid(P, fams[t]), st);
       if (e == cudaSuccess && t > 0) e = cudaEventRecord(P->ev_join[t - 1], st);
     }
     for (int t = 1; t < nf && e == cudaSuccess; ++t)
@@ -1163,12 +1186,12 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
   } else if (form == BC_FORM_TYPEWIDE) {
     for (int k = 0; k < 5 && e == cudaSuccess; ++k)
       e = launch_family(P->dtype, family_of_kind(k), c, P->d_items + P->type_begin[k],
-                        P->type_end[k] - P->type_begin[k], T, 0, nullptr, s);
+                        P->type_end[k] - P->type_begin[k], T, 0, s);
   } else if (form == BC_FORM_PER_BC) {
     for (size_t si = 0; si < P->subs.size() && e == cudaSuccess; ++si)
       e = launch_family(P->dtype, family_of_kind(P->subs[si].kind), c,
                         P->d_items + P->sub_begin[si], P->sub_end[si] - P->sub_begin[si], T,
-                        0, nullptr, s);
+                        0, s);
   } else {
     return fail(BC_ERR_INVALID_ARG, "unknown form %d", form);
   }
@@ -1225,10 +1248,10 @@ bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs, void* stream) 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int T = plan->opts.threads;
   cudaError_t e = launch_family(plan->dtype, FAM_ADJ, c, plan->d_adj,
-                                (int)plan->adj_items.size(), T, 0, nullptr, s);
+                                (int)plan->adj_items.size(), T, stream_grid(plan, FAM_ADJ), s);
   if (e == cudaSuccess)
     e = launch_family(plan->dtype, FAM_STRUCT, c, plan->d_adj_zero,
-                      (int)plan->adj_zero.size(), T, 0, nullptr, s);
+                      (int)plan->adj_zero.size(), T, stream_grid(plan, FAM_STRUCT), s);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   return BC_OK;
 }
