@@ -177,12 +177,16 @@ typedef struct bc_plan_opts {
                               in memory), 1: cells fastest, 2: levels
                               fastest                                       */
   int32_t threads;         /* threads per CTA: 32, 64, 128, 256 or 512
-                              (default 256)                                 */
+                              (default 128)                                 */
   int32_t ctas_per_sm;     /* persistent CTAs per SM; 0 = a plain grid with
                               one warp per work item (default)              */
   int32_t strict_cover;    /* 1: every ghost value must be covered          */
   int32_t no_adjoint;      /* 1: skip the transpose tables                  */
-  int32_t reserved[2];
+  int32_t no_runs;         /* 1: zero and map sub-matrices always use
+                              per-value units; 0 (default): they copy
+                              contiguous runs when the average run holds 16
+                              values or more                                */
+  int32_t reserved[1];
 } bc_plan_opts;
 
 typedef struct bc_plan bc_plan;

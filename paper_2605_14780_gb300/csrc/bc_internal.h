@@ -25,6 +25,10 @@ enum ItemKind : int32_t {
 constexpr int kPMax = 8;         // largest interpolation stencil
 constexpr int kChunk = 8;        // levels of one unit (blocks with >= 8 levels)
 constexpr int kFlatUnroll = 8;   // single-level units in flight per lane
+#ifndef BC_RUN_UNROLL
+#define BC_RUN_UNROLL 8
+#endif
+constexpr int kRunUnroll = BC_RUN_UNROLL;  // run values in flight per lane
 constexpr int kUnitsPerWarp = 4; // 8-level units per lane and item
 constexpr int kFlagSnap = 1;     // interpolation row is a unit copy of node 0
 
@@ -41,7 +45,11 @@ struct FastDiv {
 //                   memory: lanes of a warp then write one contiguous run)
 //   mode >= 2       a unit is a cell times a chunk of `mode` levels; lanes
 //                   take consecutive cells (levels far apart in memory)
-enum ItemMode : int32_t { MODE_FLAT_CELL = 0, MODE_FLAT_LEVEL = 1 };
+//   MODE_RUNS       zero / map items only: a unit is a run of values that are
+//                   contiguous in the destination and (maps) in the source;
+//                   units [u0, u0 + nunits) index the run table (at most 32
+//                   runs) and Item::p lanes (a power of two) share one run
+enum ItemMode : int32_t { MODE_RUNS = -1, MODE_FLAT_CELL = 0, MODE_FLAT_LEVEL = 1 };
 
 struct alignas(16) Item {
   int32_t kind;
@@ -52,7 +60,8 @@ struct alignas(16) Item {
   int32_t ctab;            // first row of the sub-matrix in the cell tables
   int32_t dst_slot, dst_slot2;
   int32_t src_slot;        // MAP source; CSR: the one slot all rows read, or -1
-  int32_t p;               // INTERP: stencil points; CSR: ELL row width
+  int32_t p;               // INTERP: stencil points; CSR: ELL row width;
+                           // MODE_RUNS: lanes per run
   int32_t table;           // CONST / INTERP / CSR: first table row of cell 0
   int32_t comp;            // INTERP source components: u | v << 16
   int32_t dst_ls, src_ls;  // level strides (elements)
@@ -69,6 +78,8 @@ struct Ctx {
   // offset of the ghost cell (level 0) and, for maps, of its source cell
   const int32_t* ctab_d;
   const int32_t* ctab_s;
+  // runs of zero / map items: {destination offset, source offset, length}
+  const int4* runs;
   // interpolation: per table row {slot_base of source block, node-0 offset,
   // node step, flags}, weights [row][kPMax], rotation [row][4]
   const int4* itp_idx;

@@ -113,10 +113,69 @@ __device__ void structured_flat_t(const Item& it, const Ptrs& P, const Ctx& c, i
   }
 }
 
+// Runs: an item holds up to 32 runs, one descriptor per lane, loaded at
+// once.  Groups of g = Item::p lanes (a power of two) each take one run, so
+// 32 / g runs are copied side by side and short runs still fill the warp;
+// within its run a lane keeps U values in flight.  A run is contiguous in the
+// destination and, for maps, in the source: a value costs a load and a store.
+template <typename T>
+__device__ void structured_runs(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
+  using B = typename BitsOf<T>::type;
+  constexpr int U = kRunUnroll;
+  const bool is_map = it.kind == IK_MAP;
+  const int nr = it.nunits;
+  const int lg = __ffs(it.p) - 1;  // log2 of the lanes per run
+  const int g = 1 << lg;
+  const int side = 32 >> lg;       // runs side by side
+  int4 mine = make_int4(0, 0, 0, 0);
+  if (lane < nr) mine = __ldg(c.runs + it.u0 + lane);
+  B* dbase = static_cast<B*>(P.d);
+  const B* sbase = static_cast<const B*>(P.s);
+  const int sub = lane >> lg, off = lane & (g - 1);
+  for (int k = 0; k < nr; k += side) {
+    const int r = k + sub;
+    const int dof = __shfl_sync(0xffffffffu, mine.x, r & 31);
+    const int sof = __shfl_sync(0xffffffffu, mine.y, r & 31);
+    int len = __shfl_sync(0xffffffffu, mine.z, r & 31);
+    if (r >= nr) len = 0;
+    B* d = dbase + dof;
+    if (is_map) {
+      const B* s = sbase + sof;
+      int t = off;
+      for (; t + g * (U - 1) < len; t += g * U) {
+        B v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = ldg(s + t + g * u);
+#pragma unroll
+        for (int u = 0; u < U; ++u) d[t + g * u] = v[u];
+      }
+      if (t < len) {
+        B v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = t + g * u < len ? ldg(s + t + g * u) : B(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (t + g * u < len) d[t + g * u] = v[u];
+      }
+    } else {
+      int t = off;
+      for (; t + g * (U - 1) < len; t += g * U) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) d[t + g * u] = B(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (t + g * u < len) d[t + g * u] = B(0);
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void structured_flat(const Item& it, const Ptrs& P, const Ctx& c,
                                                 int lane) {
-  if (it.mode == MODE_FLAT_LEVEL)
+  if (it.mode == MODE_RUNS)
+    structured_runs<T>(it, P, c, lane);
+  else if (it.mode == MODE_FLAT_LEVEL)
     structured_flat_t<T, true>(it, P, c, lane);
   else
     structured_flat_t<T, false>(it, P, c, lane);
@@ -522,7 +581,10 @@ __device__ __forceinline__ void load_item(Item* dst, const Item* src, int lane) 
 // Resident CTAs the register budget is set for: the structured family is
 // lean (48 registers, 40 warps per SM); the table families get 64.
 template <int FAM, int THREADS> struct Occ {
-  static constexpr int kWarps = FAM == FAM_STRUCT ? 40 : 32;
+#ifndef BC_STRUCT_WARPS
+#define BC_STRUCT_WARPS 40
+#endif
+  static constexpr int kWarps = FAM == FAM_STRUCT ? BC_STRUCT_WARPS : 32;
   static constexpr int kMinBlocks = (kWarps * 32) / THREADS > 0 ? (kWarps * 32) / THREADS : 1;
 };
 

@@ -12,7 +12,9 @@
 //   * the transpose of A (rows = data values read by some ghost, entries in
 //     ascending ghost order) and its own work list, for the adjoint.
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -111,6 +113,8 @@ struct bc_plan {
   std::vector<double> const_val;
   // cell tables: ghost-cell offset and (maps) source-cell offset, level 0
   std::vector<int32_t> ctab_d, ctab_s;
+  // runs of zero / map items (rebuilt with the work lists)
+  std::vector<int4> runs;
   // transpose
   std::vector<int32_t> arow_slot, arow_off;
   std::vector<int64_t> adj_ptr{0};
@@ -656,7 +660,103 @@ void emit_units(std::vector<Item>& out, Item proto, int vol, int L, int mode, in
   }
 }
 
+#ifndef BC_RUN_ITEM
+#define BC_RUN_ITEM 256  // values of a run item per unit of units_per_lane
+#endif
+#ifndef BC_RUN_MIN_AVG
+#define BC_RUN_MIN_AVG 16  // shortest average run (values) worth a run table
+#endif
+
+// Runs of a zero / map sub-matrix: maximal stretches of its ghost values
+// that are contiguous in the destination and (maps) in the source, in the
+// order the unit order visits them, cut into pieces of at most `cap` values.
+// Returns false (use per-value units) when the runs would be short.
+bool build_runs(bc_plan* P, const Sub& s, bool lev_fast, int cap, int& r0, int& nr) {
+  const bc_block& B = P->blocks[s.block];
+  const bool map = s.kind == BC_MAP;
+  if (s.kind != BC_ZERO && !map) return false;
+  const int L = B.nlevels;
+  const int64_t dls = L > 1 ? B.level_stride : 0;
+  const int64_t sls = map ? (P->blocks[s.src_block].nlevels > 1 ? P->blocks[s.src_block].level_stride : 0) : 0;
+  if (lev_fast && (dls != 1 || (map && sls != 1))) return false;
+  struct Run {
+    int64_t d, s, n;
+  };
+  std::vector<Run> merged;
+  const int len = lev_fast ? L : 1;
+  for (int l = 0; l < (lev_fast ? 1 : L); ++l) {
+    for (int q = s.ctab; q < s.ctab + s.vol; ++q) {
+      const int64_t d = P->ctab_d[q] + (int64_t)l * dls;
+      const int64_t sr = map ? P->ctab_s[q] + (int64_t)l * sls : 0;
+      if (d + len > INT32_MAX || sr + len > INT32_MAX) return false;
+      if (!merged.empty()) {
+        Run& cur = merged.back();
+        if (d == cur.d + cur.n && (!map || sr == cur.s + cur.n)) {
+          cur.n += len;
+          continue;
+        }
+      }
+      merged.push_back({d, sr, len});
+    }
+  }
+  const int64_t total = (int64_t)s.vol * L;
+  if (merged.empty() || total < BC_RUN_MIN_AVG * (int64_t)merged.size()) return false;  // short runs
+  r0 = (int)P->runs.size();
+  for (const Run& m : merged)
+    for (int64_t o = 0; o < m.n; o += cap)
+      P->runs.push_back(make_int4((int)(m.d + o), (int)(m.s + (map ? o : 0)),
+                                  (int)std::min<int64_t>(cap, m.n - o), 0));
+  nr = (int)P->runs.size() - r0;
+  return true;
+}
+
+// Lanes per run for the runs [a, b) of one item: the power of two g that
+// needs the fewest U-value steps when 32 / g runs go side by side (ties to
+// the larger g, for wider coalesced segments), and at least min(8, longest
+// run) so a lane group covers a 32-byte sector where the runs allow it.
+int run_lanes(const std::vector<int4>& runs, int a, int b) {
+  int longest = 0;
+  for (int r = a; r < b; ++r) longest = std::max(longest, runs[r].z);
+  int gmin = 1;
+  while (gmin < std::min(longest, 8)) gmin <<= 1;
+  int best_g = 32;
+  int64_t best = INT64_MAX;
+  for (int g = 32; g >= gmin; g >>= 1) {
+    const int side = 32 / g;
+    int64_t steps = 0;
+    for (int k = a; k < b; k += side) {
+      int m = 0;
+      for (int r = k; r < std::min(b, k + side); ++r) m = std::max(m, runs[r].z);
+      steps += (m + g * kRunUnroll - 1) / (g * kRunUnroll);
+    }
+    if (steps < best) {
+      best = steps;
+      best_g = g;
+    }
+  }
+  return best_g;
+}
+
+// split runs [r0, r0 + nr) into warp items of at most 32 runs and about
+// `per_item` values
+void emit_runs(std::vector<Item>& out, Item proto, const std::vector<int4>& runs, int r0, int nr,
+               int per_item) {
+  proto.mode = MODE_RUNS;
+  int a = r0;
+  while (a < r0 + nr) {
+    int b = a, sum = 0;
+    while (b < r0 + nr && b - a < 32 && (b == a || sum + runs[b].z <= per_item)) sum += runs[b++].z;
+    Item it = proto;
+    it.u0 = a;
+    it.nunits = b - a;
+    it.p = run_lanes(runs, a, b);
+    out.push_back(it);
+    a = b;
+  }
+}
+
 void build_items(bc_plan* P) {
+  P->runs.clear();
   // units per warp item: single-level values (flat) or 8-level chunks
   const int upl = std::max(1, std::min(P->opts.units_per_lane, 64));
   const int per_chunk_item = 32 * upl;
@@ -669,6 +769,20 @@ void build_items(bc_plan* P) {
     const int mode = structured_mode(B, P->opts.unit_order);
     emit_units(out, it, vol, B.nlevels, mode, mode < 2 ? per_flat_item : per_chunk_item);
   };
+  // zero / map sub-matrices: runs when they are long, cached per sub-matrix
+  const int per_run_item = BC_RUN_ITEM * upl;
+  std::vector<int> run_r0(P->subs.size(), -1), run_n(P->subs.size(), 0);
+  for (size_t si = 0; si < P->subs.size(); ++si) {
+    const Sub& s = P->subs[si];
+    const bc_block& B = P->blocks[s.block];
+    int r0 = 0, nr = 0;
+    if (!P->opts.no_runs &&
+        build_runs(P, s, structured_mode(B, P->opts.unit_order) == MODE_FLAT_LEVEL,
+                   per_run_item, r0, nr)) {
+      run_r0[si] = r0;
+      run_n[si] = nr;
+    }
+  }
   auto table_emit = [&](std::vector<Item>& out, const Item& it, const bc_block& B, int vol) {
     const int mode = table_mode(B, P->opts.unit_order);
     emit_units(out, it, vol, B.nlevels, mode, mode < 2 ? per_table_flat_item : per_table_item);
@@ -694,7 +808,10 @@ void build_items(bc_plan* P) {
             it.src_slot = P->slot_base[s.src_block] + c;
             it.src_ls = (int32_t)(S.nlevels > 1 ? S.level_stride : 0);
           }
-          structured_emit(out, it, B, s.vol);
+          if (run_r0[si] >= 0)
+            emit_runs(out, it, P->runs, run_r0[si], run_n[si], per_run_item);
+          else
+            structured_emit(out, it, B, s.vol);
           break;
         }
         case BC_INTERP: {
@@ -754,11 +871,22 @@ void build_items(bc_plan* P) {
   P->adj_zero.clear();
   for (size_t si = 0; si < P->subs.size(); ++si) {
     const Sub& s = P->subs[si];
+    // zero runs over the box: the same destination runs as a zero item
+    int r0 = 0, nr = 0;
+    Sub zs = s;
+    zs.kind = BC_ZERO;
+    const bool use_runs =
+        !P->opts.no_runs &&
+        build_runs(P, zs, structured_mode(P->blocks[s.block], P->opts.unit_order) == MODE_FLAT_LEVEL,
+                   per_run_item, r0, nr);
     for (int c : s.comps) {
       Item z{};
       item_common(P, s, c, z);
       z.kind = IK_ZERO;
-      structured_emit(P->adj_zero, z, P->blocks[s.block], s.vol);
+      if (use_runs)
+        emit_runs(P->adj_zero, z, P->runs, r0, nr, per_run_item);
+      else
+        structured_emit(P->adj_zero, z, P->blocks[s.block], s.vol);
     }
   }
   // adjoint gather items over the transpose rows, grouped by the level
@@ -936,11 +1064,13 @@ bc_status upload_work(bc_plan* P) {
   const size_t o_i = L.take(P->items.size() * sizeof(Item));
   size_t o_f[kFamilies];
   for (int f = 0; f < kFamilies; ++f) o_f[f] = L.take(P->fam_items[f].size() * sizeof(Item));
+  const size_t o_r = L.take(P->runs.size() * sizeof(int4));
   const size_t o_a = L.take(P->adj_items.size() * sizeof(Item));
   const size_t o_z = L.take(P->adj_zero.size() * sizeof(Item));
   std::vector<char> host(L.off + 256, 0);
   put_raw(host, o_i, P->items);
   for (int f = 0; f < kFamilies; ++f) put_raw(host, o_f[f], P->fam_items[f]);
+  put_raw(host, o_r, P->runs);
   put_raw(host, o_a, P->adj_items);
   put_raw(host, o_z, P->adj_zero);
   cudaError_t e = cudaMalloc(&P->work.base, host.size());
@@ -954,6 +1084,7 @@ bc_status upload_work(bc_plan* P) {
   char* b = static_cast<char*>(P->work.base);
   P->d_items = reinterpret_cast<Item*>(b + o_i);
   for (int f = 0; f < kFamilies; ++f) P->d_fam[f] = reinterpret_cast<Item*>(b + o_f[f]);
+  P->ctx.runs = reinterpret_cast<const int4*>(b + o_r);
   P->d_adj = reinterpret_cast<Item*>(b + o_a);
   P->d_adj_zero = reinterpret_cast<Item*>(b + o_z);
   return BC_OK;

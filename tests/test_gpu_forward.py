@@ -263,3 +263,36 @@ def test_autotune_keeps_results():
     plan.apply(table)
     torch.cuda.synchronize()
     compare(w, [t.cpu().numpy() for t in ts])
+
+
+@pytest.mark.parametrize("layout", ["outermost", "innermost"])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_runs_and_per_value_units_agree(layout, dtype):
+    """Zero and map sub-matrices copy contiguous runs by default; with
+    ``no_runs`` they use per-value units.  Both give the oracle's values bit
+    for bit, forward and adjoint."""
+    import torch
+    w = synth.batching(nblocks=48, side_lo=3, side_hi=48, lev_lo=1, lev_hi=33,
+                       h=2, seed=23, dtype=dtype)
+    dev = to_device_innermost if layout == "innermost" else to_device
+    outs, adjs = [], []
+    cot = synth.cotangent_like(w, 24)
+    for opts in ({}, {"no_runs": 1}):
+        ts = dev(w["fields"])
+        plan, _ = run(w, opts=opts, tensors=ts, repeat=2)
+        outs.append(flat([t.cpu().numpy() for t in ts]))
+        cs = dev(cot)
+        plan.adjoint(bc.slot_table(cs))
+        torch.cuda.synchronize()
+        adjs.append(flat([c.cpu().numpy() for c in cs]))
+    assert np.array_equal(bits(outs[0]), bits(outs[1]))
+    assert np.array_equal(bits(adjs[0]), bits(adjs[1]))
+    compare(w, [o for o in _unflat(outs[0], w["fields"])])
+
+
+def _unflat(v, like):
+    out, k = [], 0
+    for a in like:
+        out.append(v[k:k + a.size].reshape(a.shape))
+        k += a.size
+    return out
