@@ -19,7 +19,8 @@ enum ItemKind : int32_t {
   IK_INTERP = 3,
   IK_CSR = 4,
   IK_INTERP_PAIR = 5,
-  IK_ADJ = 6
+  IK_ADJ = 6,
+  IK_ADD = 7  // adjoint of unit copies: x_bar[dst + t] += y_bar[src + t] over runs
 };
 
 constexpr int kPMax = 8;         // largest interpolation stencil

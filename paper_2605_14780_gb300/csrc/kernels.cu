@@ -113,6 +113,53 @@ __device__ void structured_flat_t(const Item& it, const Ptrs& P, const Ctx& c, i
   }
 }
 
+// Adjoint of unit copies over runs: x_bar[dst + t] += y_bar[src + t], the
+// data values of P.d and the ghost values of P.s, with the lane layout of
+// the copy runs below.  Runs in the transpose-gather kernel (its register
+// budget), as items of the same launch.
+template <typename T>
+__device__ void add_runs(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
+  constexpr int U = kRunUnroll;
+  const int nr = it.nunits;
+  const int lg = __ffs(it.p) - 1;
+  const int g = 1 << lg, side = 32 >> lg;
+  const int sub = lane >> lg, off = lane & (g - 1);
+  int4 mine = make_int4(0, 0, 0, 0);
+  if (lane < nr) mine = __ldg(c.runs + it.u0 + lane);
+  for (int k = 0; k < nr; k += side) {
+    const int r = k + sub;
+    const int dof = __shfl_sync(0xffffffffu, mine.x, r & 31);
+    const int sof = __shfl_sync(0xffffffffu, mine.y, r & 31);
+    int len = __shfl_sync(0xffffffffu, mine.z, r & 31);
+    if (r >= nr) len = 0;
+    T* d = static_cast<T*>(P.d) + dof;
+    const T* s = static_cast<const T*>(P.s) + sof;
+    int t = off;
+    for (; t + g * (U - 1) < len; t += g * U) {
+      T y[U], x[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        y[u] = ldg(s + t + g * u);
+        x[u] = d[t + g * u];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) d[t + g * u] = x[u] + y[u];
+    }
+    if (t < len) {
+      T y[U], x[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool on = t + g * u < len;
+        y[u] = on ? ldg(s + t + g * u) : T(0);
+        x[u] = on ? d[t + g * u] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (t + g * u < len) d[t + g * u] = x[u] + y[u];
+    }
+  }
+}
+
 // Runs: an item holds up to 32 runs, one descriptor per lane, loaded at
 // once.  Groups of g = Item::p lanes (a power of two) each take one run, so
 // 32 / g runs are copied side by side and short runs still fill the warp;
@@ -473,9 +520,8 @@ __device__ void adj_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane)
     const int l0 = ch * chn;
     const int nl = min(chn, (int)it.lev.d - l0);
     const int r = it.table + q;
-    const int slot = __ldg(c.arow_slot + r);
-    const int ls = __ldg(c.slot_ls + slot);
-    T* xb = static_cast<T*>(c.slots[slot]) + (__ldg(c.arow_off + r) + l0 * ls);
+    const int ls = it.dst_ls;
+    T* xb = static_cast<T*>(P.d) + (__ldg(c.arow_off + r) + l0 * ls);
     const int e0 = (int)__ldg(c.adj_ptr + r), e1 = (int)__ldg(c.adj_ptr + r + 1);
     T acc[kChunk];
 #pragma unroll
@@ -487,9 +533,16 @@ __device__ void adj_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane)
 #pragma unroll
       for (int e = 0; e < E; ++e)
         if (eb + e < e1) {
-          const int gs = __ldg(c.aent_slot + eb + e);
-          gl[e] = __ldg(c.slot_ls + gs);
-          ys[e] = static_cast<const T*>(c.slots[gs]) + (__ldg(c.aent_off + eb + e) + l0 * gl[e]);
+          const T* ybase;
+          if (P.s) {
+            ybase = static_cast<const T*>(P.s);
+            gl[e] = it.src_ls;
+          } else {
+            const int gs = __ldg(c.aent_slot + eb + e);
+            gl[e] = __ldg(c.slot_ls + gs);
+            ybase = static_cast<const T*>(c.slots[gs]);
+          }
+          ys[e] = ybase + (__ldg(c.aent_off + eb + e) + l0 * gl[e]);
           a[e] = ldg(wv + eb + e);
         }
 #pragma unroll
@@ -515,9 +568,7 @@ __device__ void adj_flat(const Item& it, const Ptrs& P, const Ctx& c, int lane) 
     int q, l;
     flat_of(f, it, q, l);
     const int r = it.table + q;
-    const int slot = __ldg(c.arow_slot + r);
-    T* xb = static_cast<T*>(c.slots[slot]) +
-            (__ldg(c.arow_off + r) + l * __ldg(c.slot_ls + slot));
+    T* xb = static_cast<T*>(P.d) + (__ldg(c.arow_off + r) + l * it.dst_ls);
     const int e0 = (int)__ldg(c.adj_ptr + r), e1 = (int)__ldg(c.adj_ptr + r + 1);
     T acc = *xb;
     for (int eb = e0; eb < e1; eb += E) {
@@ -525,9 +576,14 @@ __device__ void adj_flat(const Item& it, const Ptrs& P, const Ctx& c, int lane) 
 #pragma unroll
       for (int e = 0; e < E; ++e)
         if (eb + e < e1) {
-          const int gs = __ldg(c.aent_slot + eb + e);
-          const T* yp = static_cast<const T*>(c.slots[gs]) +
-                        (__ldg(c.aent_off + eb + e) + l * __ldg(c.slot_ls + gs));
+          const T* yp;
+          if (P.s) {
+            yp = static_cast<const T*>(P.s) + (__ldg(c.aent_off + eb + e) + l * it.src_ls);
+          } else {
+            const int gs = __ldg(c.aent_slot + eb + e);
+            yp = static_cast<const T*>(c.slots[gs]) +
+                 (__ldg(c.aent_off + eb + e) + l * __ldg(c.slot_ls + gs));
+          }
           y[e] = *yp;
           a[e] = ldg(wv + eb + e);
         }
@@ -564,7 +620,9 @@ __device__ __forceinline__ void run_item(const Item& it, const Ptrs& P, const Ct
     else
       csr_chunk<T>(it, P, c, lane);
   } else {
-    if (flat)
+    if (it.kind == IK_ADD)
+      add_runs<T>(it, P, c, lane);
+    else if (flat)
       adj_flat<T>(it, P, c, lane);
     else
       adj_chunk<T>(it, P, c, lane);

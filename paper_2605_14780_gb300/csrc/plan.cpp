@@ -120,9 +120,17 @@ struct bc_plan {
   std::vector<int64_t> adj_ptr{0};
   std::vector<int32_t> aent_slot, aent_off;
   std::vector<double> aent_w;
+  int64_t adj_rows_total = 0, adj_nnz_total = 0;  // before unit copies leave the gather
+  // adjoint of unit copies: runs {data offset, ghost offset, length} of the
+  // transpose rows that hold one unit-weight entry, by (data slot, ghost slot)
+  struct AddSeg {
+    int32_t dslot, sslot, r0, nr;
+  };
+  std::vector<int4> add_runs;
+  std::vector<AddSeg> add_segs;
   bool has_adjoint = false;
   // work lists
-  std::vector<Item> items, adj_items, adj_zero;
+  std::vector<Item> items, adj_items, adj_zero, adj_add;
   std::vector<Item> fam_items[kFamilies];  // batched form: per family, sub-matrix order
   std::vector<int> sub_begin, sub_end;
   int type_begin[5] = {0, 0, 0, 0, 0}, type_end[5] = {0, 0, 0, 0, 0};
@@ -889,29 +897,130 @@ void build_items(bc_plan* P) {
         structured_emit(P->adj_zero, z, P->blocks[s.block], s.vol);
     }
   }
-  // adjoint gather items over the transpose rows, grouped by the level
-  // count and level layout of the data block
+  // adjoint of unit copies: add-run items, launched with the gather items
+  P->adj_add.clear();
+  for (const auto& g : P->add_segs) {
+    Item it{};
+    it.kind = IK_ADD;
+    it.dst_slot = g.dslot;
+    it.dst_slot2 = -1;
+    it.src_slot = g.sslot;
+    const int base = (int)P->runs.size();
+    P->runs.insert(P->runs.end(), P->add_runs.begin() + g.r0, P->add_runs.begin() + g.r0 + g.nr);
+    emit_runs(P->adj_add, it, P->runs, base, g.nr, per_run_item);
+  }
+  // adjoint gather items over the other transpose rows, one data slot per
+  // item (resolved once per item); when every entry of an item's rows reads
+  // one ghost slot, that slot is resolved once too
   P->adj_items.clear();
   const int nar = (int)P->arow_slot.size();
-  auto block_of_row = [&](int r) -> const bc_block& {
-    return P->blocks[P->slot_block[P->arow_slot[r]]];
-  };
   int r0 = 0;
   while (r0 < nar) {
-    const bc_block& B0 = block_of_row(r0);
-    const int mode0 = table_mode(B0, P->opts.unit_order);
+    const int ds = P->arow_slot[r0];
+    const bc_block& B0 = P->blocks[P->slot_block[ds]];
     int r1 = r0;
-    while (r1 < nar && block_of_row(r1).nlevels == B0.nlevels &&
-           table_mode(block_of_row(r1), P->opts.unit_order) == mode0)
-      ++r1;
+    while (r1 < nar && P->arow_slot[r1] == ds) ++r1;
+    int common = -2;
+    for (int64_t e = P->adj_ptr[r0]; e < P->adj_ptr[r1] && common != -1; ++e)
+      common = common == -2 ? P->aent_slot[e] : (common == P->aent_slot[e] ? common : -1);
     Item it{};
     it.kind = IK_ADJ;
     it.vol = make_div((uint32_t)(r1 - r0));
     it.lev = make_div((uint32_t)B0.nlevels);
     it.table = r0;
+    it.dst_slot = ds;
+    it.dst_slot2 = -1;
+    it.dst_ls = (int32_t)(B0.nlevels > 1 ? B0.level_stride : 0);
+    it.src_slot = common >= 0 ? common : -1;
+    if (common >= 0) {
+      const bc_block& G = P->blocks[P->slot_block[common]];
+      it.src_ls = (int32_t)(G.nlevels > 1 ? G.level_stride : 0);
+    }
     table_emit(P->adj_items, it, B0, r1 - r0);
     r0 = r1;
   }
+  P->adj_items.insert(P->adj_items.begin(), P->adj_add.begin(), P->adj_add.end());
+}
+
+// The adjoint of a unit copy is an add: a data value read by exactly one
+// ghost value, with weight 1, gets x_bar_j = x_bar_j + y_bar_i.  Such
+// transpose rows (consecutive in (data slot, offset) order, same ghost slot)
+// become add-runs, contiguous in the data and in the ghost values; every
+// other row stays in the gather.  A data value has one transpose row, so the
+// two sets of targets are disjoint and the result is the gather's, bit for
+// bit (x + 1 * y rounds once either way).
+void split_unit_copies(bc_plan* P) {
+  const int nar = (int)P->arow_slot.size();
+  std::vector<char> keep(nar, 1);
+  auto single = [&](int r) {
+    const int64_t e = P->adj_ptr[r];
+    return P->adj_ptr[r + 1] - e == 1 && P->aent_w[e] == 1.0;
+  };
+  int r = 0;
+  while (r < nar) {
+    if (!single(r)) {
+      ++r;
+      continue;
+    }
+    const int ds = P->arow_slot[r];
+    const int gs = P->aent_slot[P->adj_ptr[r]];
+    int r1 = r;
+    while (r1 < nar && single(r1) && P->arow_slot[r1] == ds && P->aent_slot[P->adj_ptr[r1]] == gs)
+      ++r1;
+    const bc_block& D = P->blocks[P->slot_block[ds]];
+    const bc_block& G = P->blocks[P->slot_block[gs]];
+    const int L = D.nlevels;
+    const int64_t dls = L > 1 ? D.level_stride : 0;
+    const int64_t gls = G.nlevels > 1 ? G.level_stride : 0;
+    const bool lev_fast = L == 1 || (dls == 1 && gls == 1);
+    std::vector<int4> runs;
+    bool fits = G.nlevels == L;
+    for (int l = 0; fits && l < (lev_fast ? 1 : L); ++l) {
+      for (int q = r; q < r1; ++q) {
+        const int64_t d = P->arow_off[q] + (lev_fast ? 0 : l * dls);
+        const int64_t g = P->aent_off[P->adj_ptr[q]] + (lev_fast ? 0 : l * gls);
+        const int len = lev_fast ? L : 1;
+        if (d + len > INT32_MAX || g + len > INT32_MAX) {
+          fits = false;
+          break;
+        }
+        if (!runs.empty() && d == runs.back().x + runs.back().z &&
+            g == runs.back().y + runs.back().z && runs.back().z + len <= 2048) {
+          runs.back().z += len;
+          continue;
+        }
+        runs.push_back(make_int4((int)d, (int)g, len, 0));
+      }
+    }
+    const int64_t total = (int64_t)(r1 - r) * L;
+    if (fits && !runs.empty() && total >= BC_RUN_MIN_AVG * (int64_t)runs.size()) {
+      P->add_segs.push_back({ds, gs, (int)P->add_runs.size(), (int)runs.size()});
+      P->add_runs.insert(P->add_runs.end(), runs.begin(), runs.end());
+      std::fill(keep.begin() + r, keep.begin() + r1, 0);
+    }
+    r = r1;
+  }
+  // the gather keeps the other rows
+  std::vector<int32_t> rs, ro, es, eo;
+  std::vector<int64_t> ptr{0};
+  std::vector<double> ew;
+  for (int q = 0; q < nar; ++q) {
+    if (!keep[q]) continue;
+    rs.push_back(P->arow_slot[q]);
+    ro.push_back(P->arow_off[q]);
+    for (int64_t e = P->adj_ptr[q]; e < P->adj_ptr[q + 1]; ++e) {
+      es.push_back(P->aent_slot[e]);
+      eo.push_back(P->aent_off[e]);
+      ew.push_back(P->aent_w[e]);
+    }
+    ptr.push_back((int64_t)ew.size());
+  }
+  P->arow_slot.swap(rs);
+  P->arow_off.swap(ro);
+  P->aent_slot.swap(es);
+  P->aent_off.swap(eo);
+  P->aent_w.swap(ew);
+  P->adj_ptr.swap(ptr);
 }
 
 void build_transpose(bc_plan* P) {
@@ -951,7 +1060,10 @@ void build_transpose(bc_plan* P) {
     P->aent_w.push_back(ents[e].w);
   }
   if (!ents.empty()) P->adj_ptr.push_back((int64_t)P->aent_w.size());
+  P->adj_rows_total = (int64_t)P->arow_slot.size();
+  P->adj_nnz_total = (int64_t)P->aent_w.size();
   P->has_adjoint = true;
+  if (!P->opts.no_runs) split_unit_copies(P);
 }
 
 // -- device upload -------------------------------------------------------------
@@ -1134,14 +1246,14 @@ void compute_stats(bc_plan* P) {
   for (auto& cc : csr_cols) bytes += L_of_slot(cc.first) * S;
   st.bytes_fwd = bytes;
   int64_t abytes = 4 * st.ghost_values * S;
-  abytes += (int64_t)P->arow_slot.size() * 16 + (int64_t)P->aent_w.size() * (8 + S);
+  abytes += P->adj_rows_total * 16 + P->adj_nnz_total * (8 + S);
   st.bytes_adj = abytes;
   st.nitems = (int64_t)P->items.size();
   st.nitems_adjoint = (int64_t)P->adj_items.size();
   st.nsubmatrices = (int64_t)P->subs.size();
   st.nslots = P->nslots;
   st.table_bytes = (int64_t)P->tables.bytes + (int64_t)P->work.bytes;
-  st.transpose_nnz = (int64_t)P->aent_w.size();
+  st.transpose_nnz = P->adj_nnz_total;
   st.element_size = P->esize;
   st.form_threads = P->opts.threads;
   st.form_ctas_per_sm = P->opts.ctas_per_sm;
@@ -1378,6 +1490,8 @@ bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs, void* stream) 
   c.slots = slot_ptrs;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int T = plan->opts.threads;
+  // one launch for the gather and the add-runs (disjoint targets), then the
+  // zero pass over the ghost values both of them read
   cudaError_t e = launch_family(plan->dtype, FAM_ADJ, c, plan->d_adj,
                                 (int)plan->adj_items.size(), T, stream_grid(plan, FAM_ADJ), s);
   if (e == cudaSuccess)
