@@ -421,6 +421,93 @@ __device__ __forceinline__ const T* csr_src(const Item& it, const Ptrs& P, const
   return static_cast<const T*>(c.slots[s]) + (__ldg(c.csr_off + e) + l * sls);
 }
 
+// A row of an ELL block of width W = 4 or 8 starts on a 16-byte boundary
+// (the host pads the widths and aligns the blocks): its offsets, weights
+// and (without a common slot) slots load as 16-byte vectors.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename T, int W>
+__device__ __forceinline__ void load_ell(const Ctx& c, int e0, bool common, int (&off)[W],
+                                         T (&a)[W], int (&slot)[W]) {
+  const int4* o4 = reinterpret_cast<const int4*>(c.csr_off + e0);
+#pragma unroll
+  for (int j = 0; j < W / 4; ++j) {
+    const int4 v = __ldg(o4 + j);
+    off[4 * j] = v.x;
+    off[4 * j + 1] = v.y;
+    off[4 * j + 2] = v.z;
+    off[4 * j + 3] = v.w;
+  }
+  using V = typename Vec16<T>::type;
+  constexpr int N = Vec16<T>::n;
+  const V* a4 = reinterpret_cast<const V*>(static_cast<const T*>(c.csr_val) + e0);
+#pragma unroll
+  for (int j = 0; j < W / N; ++j) {
+    const V v = __ldg(a4 + j);
+    const T* t = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int k = 0; k < N; ++k) a[N * j + k] = t[k];
+  }
+  if (!common) {
+    const int4* s4 = reinterpret_cast<const int4*>(c.csr_slot + e0);
+#pragma unroll
+    for (int j = 0; j < W / 4; ++j) {
+      const int4 v = __ldg(s4 + j);
+      slot[4 * j] = v.x;
+      slot[4 * j + 1] = v.y;
+      slot[4 * j + 2] = v.z;
+      slot[4 * j + 3] = v.w;
+    }
+  }
+}
+
+// A cell times a chunk of levels per lane, a whole ELL row of width W.
+template <typename T, int W>
+__device__ void csr_chunk_w(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
+  const int end = it.u0 + it.nunits;
+  const int ls = it.dst_ls;
+  const int chn = it.mode;
+  const T* sb = static_cast<const T*>(P.s);
+  const bool common = sb != nullptr;
+  for (int u = it.u0 + lane; u < end; u += 32) {
+    int q, ch;
+    unit_of(u, it, q, ch);
+    const int l0 = ch * chn;
+    const int nl = min(chn, (int)it.lev.d - l0);
+    const int row = it.table + q;
+    const int nnz = __ldg(c.csr_nnz + row);
+    int off[W], slot[W];
+    T a[W];
+    load_ell<T, W>(c, it.src_org + q * W, common, off, a, slot);
+    T* d = static_cast<T*>(P.d) + (dst_cell(it, c, q) + l0 * ls);
+    const T rhs = ldg(static_cast<const T*>(c.csr_rhs) + row);
+    T acc[kChunk];
+#pragma unroll
+    for (int l = 0; l < kChunk; ++l) acc[l] = T(0);
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+      if (j < nnz) {
+        const T* xs;
+        int sls;
+        if (common) {
+          xs = sb + (off[j] + l0 * it.src_ls);
+          sls = it.src_ls;
+        } else {
+          sls = __ldg(c.slot_ls + slot[j]);
+          xs = static_cast<const T*>(c.slots[slot[j]]) + (off[j] + l0 * sls);
+        }
+#pragma unroll
+        for (int l = 0; l < kChunk; ++l)
+          if (l < nl) acc[l] = fma(a[j], ldg(xs + l * sls), acc[l]);
+      }
+#pragma unroll
+    for (int l = 0; l < kChunk; ++l)
+      if (l < nl) d[l * ls] = acc[l] + rhs;
+  }
+}
+
 // Rows are processed E entries at a time: the E offsets and values load
 // together, then the E x E-level source loads, so one row costs two memory
 // latencies per E entries instead of two per entry.
@@ -615,8 +702,14 @@ __device__ __forceinline__ void run_item(const Item& it, const Ptrs& P, const Ct
         interp_scalar_chunk<T>(it, P, c, lane);
     }
   } else if constexpr (FAM == FAM_CSR) {
+    // lanes over levels share a row (its entries load as broadcasts); lanes
+    // over cells each own one, where vector loads of the entries pay
     if (flat)
       csr_flat<T>(it, P, c, lane);
+    else if (it.p == 8)
+      csr_chunk_w<T, 8>(it, P, c, lane);
+    else if (it.p == 4)
+      csr_chunk_w<T, 4>(it, P, c, lane);
     else
       csr_chunk<T>(it, P, c, lane);
   } else {

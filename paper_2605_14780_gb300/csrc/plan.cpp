@@ -361,8 +361,16 @@ bc_status add_csr(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
   // ELL width of this sub-matrix: its longest row
   int64_t w = 1;
   for (int64_t r = 0; r < nrows; ++r) w = std::max<int64_t>(w, m.row_ptr[r + 1] - m.row_ptr[r]);
+  // widths up to 8 are padded to 4 or 8 and rows start on 16-byte
+  // boundaries, so the kernels load a row's entries as vectors
+  if (w <= 8) w = w <= 4 ? 4 : 8;
   if (w * nrows > (int64_t(1) << 30))
     return fail(BC_ERR_UNSUPPORTED, "sub-matrix %d: CSR rows too long", idx);
+  while (P->csr_slot.size() % 4) {
+    P->csr_slot.push_back(0);
+    P->csr_off.push_back(0);
+    P->csr_val.push_back(0.0);
+  }
   s.ell_w = (int)w;
   s.ell_base = (int)P->csr_slot.size();
   P->csr_slot.resize(P->csr_slot.size() + nrows * w, 0);
