@@ -119,7 +119,7 @@ __device__ void structured_flat_t(const Item& it, const Ptrs& P, const Ctx& c, i
 // budget), as items of the same launch.
 template <typename T>
 __device__ void add_runs(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
-  constexpr int U = kRunUnroll;
+  constexpr int U = 8;  // two arrays of U values: 8 keeps the gather's budget
   const int nr = it.nunits;
   const int lg = __ffs(it.p) - 1;
   const int g = 1 << lg, side = 32 >> lg;
