@@ -223,7 +223,7 @@ def layout_views(buf, w, layout):
 
 
 def measure_forward(w, device, stream, steps, warmup, layout="level_outermost",
-                    adjoint=False, floor=False):
+                    adjoint=False, floor=False, stencil=None):
     """Device time of the batched forward (and optionally the adjoint) of a
     workload with rotating field copies; returns a dict of numbers."""
     from paper_2605_14780_gb300 import bc
@@ -231,7 +231,7 @@ def measure_forward(w, device, stream, steps, warmup, layout="level_outermost",
     field_bytes = sum(a.size for a in w["fields"]) * esize
     ncopies = int(min(8, max(2, np.ceil(3 * 256e6 / field_bytes) + 1)))
     copies = field_copies(w, ncopies, device, layout)
-    plan = bc.plan_for_workload(w, copies[0][1])
+    plan = bc.plan_for_workload(w, copies[0][1], stencil=stencil)
     tables = [bc.slot_table(v) for _, v in copies]
     st = plan.stats()
     hbm, _ = measured_peaks()
@@ -553,6 +553,22 @@ def run_ours(args, rank, world, local):
                                            adjoint=adj)
             del ww
         result["other_workloads"] = others
+        # dead-ghost elimination (Sec. IV-C): the same workloads, plans cut
+        # to the ghost values a following stencil reads
+        pruned = {}
+        for name, fn, lay, stc in (
+                ("batching_star5_levels_innermost", lambda: w, "level_innermost",
+                 bc.star_stencil(2, 1)),
+                ("batching_box9_levels_innermost", lambda: w, "level_innermost",
+                 bc.box_stencil(2, 1)),
+                ("hpcg_128_P_7pt", lambda: make_workload_named("hpcg"), "level_outermost",
+                 bc.star_stencil(3, 1))):
+            ww = fn()
+            pruned[name] = measure_forward(ww, device, stream, min(args.steps, 300), 5, lay,
+                                           stencil=stc)
+            pruned[name]["stencil_points"] = int(len(stc))
+            del ww
+        result["pruned_variants"] = pruned
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = oracle_timing(w)
     if rank == 0:

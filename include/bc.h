@@ -222,6 +222,25 @@ bc_status bc_plan_create(const bc_grid* grid, const bc_submatrix* subs,
                          int32_t nsubs, const bc_plan_opts* opts,
                          bc_plan** out);
 
+/*
+ * Dead-ghost elimination (Sec. IV-C: the effective space U(W) of the
+ * boundary writes a following stencil reads).  Like bc_plan_create, but the
+ * plan keeps only the ghost values that a stencil applied on the data cells
+ * reads: ghost cell g of a block is live when g - o is a data cell of that
+ * block for one of the stencil offsets o.  offsets: noffsets triples
+ * (di, dj, dk), host memory, read during the call only.  Every sub-matrix
+ * box is cut to its live cells, split into disjoint boxes that carry the
+ * matching slices of its per-cell payload; sub-matrices without live cells
+ * are dropped.  Apply then leaves dead ghost values untouched and the
+ * adjoint neither reads nor zeroes them.  With strict_cover every live ghost
+ * value must be covered.  Errors as bc_plan_create; BC_ERR_INVALID_ARG for
+ * an empty stencil.
+ */
+bc_status bc_plan_create_pruned(const bc_grid* grid, const bc_submatrix* subs,
+                                int32_t nsubs, const bc_plan_opts* opts,
+                                const int32_t* offsets, int32_t noffsets,
+                                bc_plan** out);
+
 /* Number of slots (sum of ncomp) the slot-pointer arrays must hold. */
 int32_t bc_plan_nslots(const bc_plan* plan);
 

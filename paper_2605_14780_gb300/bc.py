@@ -76,6 +76,10 @@ SIGNATURES = {
     "bc_plan_create": (c_i32, [ctypes.POINTER(BcGrid), ctypes.POINTER(BcSubmatrix),
                                c_i32, ctypes.POINTER(BcPlanOpts),
                                ctypes.POINTER(c_vp)]),
+    "bc_plan_create_pruned": (c_i32, [ctypes.POINTER(BcGrid), ctypes.POINTER(BcSubmatrix),
+                                      c_i32, ctypes.POINTER(BcPlanOpts),
+                                      ctypes.POINTER(c_i32), c_i32,
+                                      ctypes.POINTER(c_vp)]),
     "bc_plan_nslots": (c_i32, [c_vp]),
     "bc_apply": (c_i32, [c_vp, c_vp, c_vp]),
     "bc_apply_form": (c_i32, [c_vp, c_vp, c_i32, c_vp]),
@@ -146,10 +150,13 @@ class Plan:
 
     ``blocks``: list of dicts ``n, h, nlevels, ncomp, stride, level_stride``
     (element strides); ``subs``: list of sub-matrix dicts as produced by
-    :mod:`paper_2605_14780_gb300.specs`; ``dtype``: ``"f32"`` or ``"f64"``.
+    :mod:`paper_2605_14780_gb300.specs`; ``dtype``: ``"f32"`` or ``"f64"``;
+    ``stencil``: optional ``(n, 3)`` integer offsets of the stencil that
+    reads the ghost layers -- the plan then keeps only the ghost values it
+    reads (``bc_plan_create_pruned``, dead-ghost elimination).
     """
 
-    def __init__(self, blocks, subs, dtype, opts=None):
+    def __init__(self, blocks, subs, dtype, opts=None, stencil=None):
         lib = load_library()
         self._lib = lib
         self.dtype = dtype
@@ -207,8 +214,14 @@ class Plan:
         for key, v in (opts or {}).items():
             setattr(o, key, v)
         handle = c_vp()
-        st = lib.bc_plan_create(ctypes.byref(grid), cs, len(subs),
-                                ctypes.byref(o), ctypes.byref(handle))
+        if stencil is None:
+            st = lib.bc_plan_create(ctypes.byref(grid), cs, len(subs),
+                                    ctypes.byref(o), ctypes.byref(handle))
+        else:
+            so = arr(np.asarray(stencil, np.int32).reshape(-1, 3), np.int32)
+            st = lib.bc_plan_create_pruned(ctypes.byref(grid), cs, len(subs),
+                                           ctypes.byref(o), _ptr(so, c_i32), len(so),
+                                           ctypes.byref(handle))
         _check(st)
         self._h = handle
         self.nslots = lib.bc_plan_nslots(handle)
@@ -308,15 +321,35 @@ def block_descriptors(tensors, blocks):
     return out
 
 
-def plan_for_workload(w, tensors=None, opts=None):
+def plan_for_workload(w, tensors=None, opts=None, stencil=None):
     """Plan of a :mod:`synth` workload (strides of ``tensors`` if given,
-    contiguous ``(C, L, F2, F1, F0)`` otherwise)."""
+    contiguous ``(C, L, F2, F1, F0)`` otherwise), pruned to ``stencil``'s
+    reads if given."""
     from . import specs
     if tensors is not None:
         blocks = block_descriptors(tensors, w["blocks"])
     else:
         blocks = [specs.contiguous_block(b) for b in w["blocks"]]
-    return Plan(blocks, specs.submatrices(w), w["dtype"], opts)
+    return Plan(blocks, specs.submatrices(w), w["dtype"], opts, stencil)
+
+
+def star_stencil(ndim, radius=1):
+    """Offsets of the (2 * ndim * radius + 1)-point star stencil."""
+    out = [(0, 0, 0)]
+    for d in range(ndim):
+        for r in range(1, radius + 1):
+            for sgn in (-1, 1):
+                o = [0, 0, 0]
+                o[d] = sgn * r
+                out.append(tuple(o))
+    return np.array(out, np.int32)
+
+
+def box_stencil(ndim, radius=1):
+    """Offsets of the (2 * radius + 1)^ndim box stencil."""
+    rng = range(-radius, radius + 1)
+    z = [0] if ndim < 3 else rng
+    return np.array([(i, j, k) for k in z for j in rng for i in rng], np.int32)
 
 
 class BCFill:

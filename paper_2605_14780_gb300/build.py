@@ -1,6 +1,6 @@
 """Build ``libbcgb300.so`` in-tree with nvcc for sm_103a.
 
-Three translation units compiled in parallel, then linked with the static
+Four translation units compiled in parallel, then linked with the static
 CUDA runtime into ``paper_2605_14780_gb300/_lib/libbcgb300.so``.
 """
 from __future__ import annotations
@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
-SOURCES = ["plan.cpp", "kernels.cu", "geometry.cu"]
+SOURCES = ["plan.cpp", "prune.cpp", "kernels.cu", "geometry.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]
@@ -40,7 +40,8 @@ def build_library(force=False, extra_flags=()):
     os.makedirs(OUT_DIR, exist_ok=True)
     lib = os.path.join(OUT_DIR, "libbcgb300.so")
     srcs = [os.path.join(CSRC, s) for s in SOURCES] + [
-        os.path.join(CSRC, "bc_internal.h"), os.path.join(ROOT, "include", "bc.h")]
+        os.path.join(CSRC, "bc_internal.h"), os.path.join(CSRC, "prune.h"),
+        os.path.join(ROOT, "include", "bc.h")]
     if not force and os.path.exists(lib):
         newest = max(os.path.getmtime(s) for s in srcs)
         if os.path.getmtime(lib) >= newest and not extra_flags:

@@ -28,6 +28,7 @@
 
 #include "../../include/bc.h"
 #include "bc_internal.h"
+#include "prune.h"
 
 using namespace bcg;
 
@@ -1281,8 +1282,28 @@ bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
   return BC_OK;
 }
 
+// live ghost cells of a block for a stencil (dead-ghost elimination): ghost
+// cells g with g - o a data cell for some offset o
+size_t live_ghosts(const bc_block& B, const int32_t* off, int noff) {
+  size_t n = 0;
+  for (int k = -B.h[2]; k < B.n[2] + B.h[2]; ++k)
+    for (int j = -B.h[1]; j < B.n[1] + B.h[1]; ++j)
+      for (int i = -B.h[0]; i < B.n[0] + B.h[0]; ++i) {
+        if (i >= 0 && i < B.n[0] && j >= 0 && j < B.n[1] && k >= 0 && k < B.n[2]) continue;
+        for (int o = 0; o < noff; ++o) {
+          const int a = i - off[3 * o], b = j - off[3 * o + 1], c = k - off[3 * o + 2];
+          if (a >= 0 && a < B.n[0] && b >= 0 && b < B.n[1] && c >= 0 && c < B.n[2]) {
+            ++n;
+            break;
+          }
+        }
+      }
+  return n;
+}
+
 bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_t nsubs,
-                           const bc_plan_opts* opts, bc_plan* P) {
+                           const bc_plan_opts* opts, bc_plan* P,
+                           const int32_t* stencil = nullptr, int nstencil = 0) {
   bc_status st = normalise_opts(opts, P->opts);
   if (st != BC_OK) return st;
   if ((st = validate_grid(grid, P)) != BC_OK) return st;
@@ -1348,8 +1369,10 @@ bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_
       const size_t D = (size_t)B.n[0] * B.n[1] * B.n[2];
       const auto& mm = cov.map[slot];
       const size_t covered = mm.empty() ? 0 : (size_t)std::count(mm.begin(), mm.end(), (uint8_t)1);
-      if (covered != F - D)
-        return fail(BC_ERR_UNCOVERED, "slot %d: %zu ghost cells have no row", slot, F - D - covered);
+      // a pruned plan covers live ghost cells only, and must cover them all
+      const size_t want = stencil ? live_ghosts(B, stencil, nstencil) : F - D;
+      if (covered != want)
+        return fail(BC_ERR_UNCOVERED, "slot %d: %zu ghost cells have no row", slot, want - covered);
     }
   }
   // device from here on
@@ -1467,6 +1490,37 @@ bc_status bc_plan_create(const bc_grid* grid, const bc_submatrix* subs, int32_t 
   bc_status st;
   try {
     st = plan_create_impl(grid, subs, nsubs, opts, P);
+  } catch (const std::bad_alloc&) {
+    st = fail(BC_ERR_NOMEM, "host allocation while building the plan");
+  }
+  if (st != BC_OK) {
+    delete P;
+    return st;
+  }
+  *out = P;
+  return BC_OK;
+}
+
+bc_status bc_plan_create_pruned(const bc_grid* grid, const bc_submatrix* subs, int32_t nsubs,
+                                const bc_plan_opts* opts, const int32_t* offsets,
+                                int32_t noffsets, bc_plan** out) {
+  if (!out) return fail(BC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  g_last_error.clear();
+  if (!offsets || noffsets <= 0) return fail(BC_ERR_INVALID_ARG, "empty stencil");
+  if (!grid || !grid->blocks || grid->nblocks < 0)
+    return fail(BC_ERR_INVALID_ARG, "bad grid");
+  bc_plan* P = new (std::nothrow) bc_plan();
+  if (!P) return fail(BC_ERR_NOMEM, "host allocation of the plan");
+  bc_status st;
+  try {
+    PrunedSubs pr;
+    st = prune_submatrices(grid, subs, nsubs, offsets, noffsets, pr);
+    if (st != BC_OK)
+      st = fail(st, "bad sub-matrix list");
+    else
+      st = plan_create_impl(grid, pr.subs.data(), (int32_t)pr.subs.size(), opts, P, offsets,
+                            noffsets);
   } catch (const std::bad_alloc&) {
     st = fail(BC_ERR_NOMEM, "host allocation while building the plan");
   }
