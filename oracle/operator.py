@@ -18,7 +18,7 @@ import scipy.sparse as sp
 
 from .regions import Layout
 from .rows import (OracleError, concat_rowsets, const_rows, csr_rows,
-                   faces_rows, map_rows, zero_rows)
+                   faces_rows, map_rows, sync_rows, zero_rows)
 from .sphere import cubed_sphere_rows
 
 __all__ = ["OracleError", "Operator", "rowsets", "build_operator", "apply",
@@ -43,6 +43,8 @@ def rowsets(w, diagnostics=None):
             out.append(faces_rows(bc, blocks))
         elif k == "cubed_sphere_edges":
             out.extend(cubed_sphere_rows(bc, blocks, diagnostics))
+        elif k == "sync":
+            out.append(sync_rows(bc))
         else:
             raise OracleError(f"unknown boundary kind {k}")
     return [r for r in out if r is not None]
@@ -63,7 +65,13 @@ def _validate(layout, rs):
     b = rs["b"]
     nr = len(rs["c"])
     bb = np.full(nr, b)
-    if np.any(layout.in_data(bb, rs["ijk"])) or not np.all(layout.in_full(bb, rs["ijk"])):
+    if rs.get("data_rows"):
+        # Sync rows (Sec. III-B, block-edge averaging) overwrite data cells
+        if not np.all(layout.in_data(bb, rs["ijk"])):
+            raise OracleError("a Sync row is not a data cell of its block")
+        if np.any(rs["rhs"] != 0.0):
+            raise OracleError("a Sync row has b_i != 0")
+    elif np.any(layout.in_data(bb, rs["ijk"])) or not np.all(layout.in_full(bb, rs["ijk"])):
         raise OracleError("a row is not a ghost cell of its block")
     if np.any((rs["c"] < 0) | (rs["c"] >= layout.C[b])):
         raise OracleError("row component out of range")
@@ -98,7 +106,7 @@ def build_operator(w, levels=None, diagnostics=None):
         per_block[b] = rs
         key = layout.row(np.full(len(rs["c"]), b), rs["c"], 0, rs["ijk"])
         if len(np.unique(key)) != len(key):
-            raise OracleError("two sub-matrices cover the same ghost value")
+            raise OracleError("two sub-matrices cover the same value")
     R, Cc, V, Bv, Er = [], [], [], [], []
     row_off = 0
     for b, rs in sorted(per_block.items()):
@@ -155,13 +163,16 @@ def row_scale(op, fields):
 
 
 def apply_adjoint(op, cot):
-    """Adjoint of the in-place ghost fill applied to cotangent ``cot``:
-    ``x_D_bar = y_D_bar + A^T y_G_bar``, covered ghosts set to 0, uncovered
-    ghosts passed through."""
+    """Adjoint of the in-place fill ``out_i = (A x_D + b)_i`` on the covered
+    rows, ``out_j = x_j`` elsewhere, applied to cotangent ``cot``:
+    ``x_bar_j = [j not covered] y_bar_j + sum_i A_ij y_bar_i``.  Covered rows
+    are ghosts (whose x_bar is 0) and, with block-edge averaging, data cells
+    (whose own y_bar is consumed by their row); uncovered values pass through.
+    """
     lay = op.layout
     y = lay.flatten_full(cot)
     g = y[op.rows].copy()
     contrib = op.A.T @ g
-    y[lay.data_rows()] += contrib
     y[op.rows] = 0.0
+    y[lay.data_rows()] += contrib
     return lay.unflatten_full(y, cot)

@@ -164,6 +164,17 @@ def csr_rows(bc):
     return rs
 
 
+def sync_rows(bc):
+    """Block-edge averaging (``Sync`` of Sec. III-B): rows on data cells that
+    several blocks store for one physical location, ``A_ij = Sync_ij`` over
+    the shared data cells, ``b_i = 0``.  Laid out like a CSR sub-matrix whose
+    box lies in the data region; the row set is flagged so that validation
+    expects data-cell rows."""
+    rs = csr_rows(bc)
+    rs["data_rows"] = True
+    return rs
+
+
 # ----------------------------------------------------------------------------
 # per-face descriptions of one block
 # ----------------------------------------------------------------------------

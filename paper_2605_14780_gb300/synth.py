@@ -42,6 +42,9 @@ bc kinds (the descriptions; each side turns them into rows on its own)
                vector_pair | None}``: panel-edge sync of six equiangular
                gnomonic panels by ``p``-point interpolation along the
                neighbour row, with the ``vector_pair`` components rotated.
+    ``sync``   block-edge averaging (``Sync`` of Sec. III-B): the fields of
+               ``csr`` with the box inside the *data* region; the rows
+               overwrite those data cells.
 """
 from __future__ import annotations
 
@@ -457,3 +460,93 @@ def cotangent_like(w, seed):
 
 def copy_fields(w):
     return [a.copy() for a in w["fields"]]
+
+
+# ----------------------------------------------------------------------------
+# block-edge averaging: node-centred blocks that share their edge nodes
+# ----------------------------------------------------------------------------
+def sync_grid(bx=3, by=3, n=17, h=2, nlevels=4, ncomp=2, dtype="f64", seed=12):
+    """``bx`` x ``by`` node-centred 2-D blocks of ``n`` x ``n`` nodes; block
+    ``(a, b)`` holds the global nodes ``(a (n-1) + i, b (n-1) + j)``, so
+    neighbouring blocks store their common edge twice (corner nodes up to
+    four times), as in multi-block MCV grids.  Boundary descriptions:
+
+    * ``sync`` rows on every stored copy of a shared node: the mean of all
+      copies (weights ``1/k`` over the ``k`` copies, all components alike);
+    * ghost layers: a ``map`` from the neighbouring block across each inner
+      edge, skipping the shared node line (ghost depth ``r`` reads the
+      neighbour's node ``1 + r`` behind the edge); ``zero`` on the outer
+      boundary and on the corners.
+
+    Fields are uniform in [-1, 1] (so the copies of a node differ).
+    """
+    rng_blocks = [block2d(n, n, h, nlevels, ncomp) for _ in range(bx * by)]
+    bid = lambda a, b: b * bx + a  # noqa: E731
+    # copies of every node
+    copies = {}
+    for b in range(by):
+        for a in range(bx):
+            for j in range(n):
+                for i in range(n):
+                    X, Y = a * (n - 1) + i, b * (n - 1) + j
+                    copies.setdefault((X, Y), []).append((bid(a, b), i, j))
+    bcs = []
+    comps = list(range(ncomp))
+    for b in range(by):
+        for a in range(bx):
+            k = bid(a, b)
+            # shared nodes of this block, as boxes: the shared columns, then
+            # the rest of the shared rows
+            boxes = []
+            cols = [i for i, on in ((0, a > 0), (n - 1, a < bx - 1)) if on]
+            for i in cols:
+                boxes.append(((i, 0, 0), (i + 1, n, 1)))
+            i_lo = 1 if 0 in cols else 0
+            i_hi = n - 1 if (n - 1) in cols else n
+            for j, on in ((0, b > 0), (n - 1, b < by - 1)):
+                if on and i_hi > i_lo:
+                    boxes.append(((i_lo, j, 0), (i_hi, j + 1, 1)))
+            for lo, hi in boxes:
+                cells = [(i, j) for j in range(lo[1], hi[1]) for i in range(lo[0], hi[0])]
+                row_ptr, cb, cc, cijk, val = [0], [], [], [], []
+                for c in comps:
+                    for i, j in cells:
+                        grp = copies[(a * (n - 1) + i, b * (n - 1) + j)]
+                        for (ob, oi, oj) in grp:
+                            cb.append(ob)
+                            cc.append(c)
+                            cijk.append((oi, oj, 0))
+                            val.append(1.0 / len(grp))
+                        row_ptr.append(len(val))
+                bcs.append({"kind": "sync", "block": k, "lo": lo, "hi": hi,
+                            "comps": comps,
+                            "row_ptr": np.array(row_ptr, np.int64),
+                            "col_block": np.array(cb, np.int32),
+                            "col_comp": np.array(cc, np.int32),
+                            "col_ijk": np.array(cijk, np.int32).reshape(-1, 3),
+                            "val": np.array(val, np.float64), "rhs": None})
+            # ghost layers
+            for axis in (0, 1):
+                for side in (0, 1):
+                    lo = [0, 0, 0]
+                    hi = [n, n, 1]
+                    lo[axis], hi[axis] = (-h, 0) if side == 0 else (n, n + h)
+                    na = a + (1 if side else -1) if axis == 0 else a
+                    nb = b + (1 if side else -1) if axis == 1 else b
+                    if 0 <= na < bx and 0 <= nb < by:
+                        off = [0, 0, 0]
+                        off[axis] = (n - 1) if side == 0 else -(n - 1)
+                        bcs.append({"kind": "map", "block": k, "lo": tuple(lo),
+                                    "hi": tuple(hi), "comps": comps,
+                                    "src_block": bid(na, nb), "perm": (0, 1, 2),
+                                    "sign": (1, 1, 1), "offset": tuple(off)})
+                    else:
+                        bcs.append({"kind": "zero", "block": k, "lo": tuple(lo),
+                                    "hi": tuple(hi), "comps": comps})
+            for cx in ((-h, 0), (n, n + h)):
+                for cy in ((-h, 0), (n, n + h)):
+                    bcs.append({"kind": "zero", "block": k, "lo": (cx[0], cy[0], 0),
+                                "hi": (cx[1], cy[1], 1), "comps": comps})
+    fields = uniform_fields(rng_blocks, dtype, -1.0, 1.0, seed)
+    return {"name": f"sync{bx}x{by}_n{n}", "dtype": dtype, "blocks": rng_blocks,
+            "bcs": bcs, "fields": fields}
