@@ -177,6 +177,10 @@ def make_workload(name):
     if name == "adjoint":
         return synth.adjoint_cubed_sphere(), ("cubed sphere 6 x 768^2, h=3, "
                                               "(h,u,v) x 32 levels FP32, p=6")
+    if name == "sync":
+        return (synth.sync_grid(8, 8, 129, 3, 32, 3, "f32", seed=12),
+                "block-edge averaging: 8 x 8 node-centred blocks of 129^2 nodes "
+                "sharing their edges, h=3, 3 components x 32 levels FP32")
     if name == "hpcg":
         return synth.hpcg_block(128, "P"), "HPCG-like 128^3 FP64, h=1, x periodic"
     raise ValueError(name)
@@ -547,7 +551,8 @@ def run_ours(args, rank, world, local):
                 ("tiny_cubed_sphere_6x32", lambda: make_workload_named("tiny"), False),
                 ("hpcg_128_P", lambda: make_workload_named("hpcg"), False),
                 ("swe_cubed_sphere_6x384_L32", lambda: make_workload_named("swe"), False),
-                ("adjoint_cubed_sphere_6x768_L32", lambda: make_workload_named("adjoint"), True)):
+                ("adjoint_cubed_sphere_6x768_L32", lambda: make_workload_named("adjoint"), True),
+                ("sync_grid_8x8_n129_L32", lambda: make_workload_named("sync"), True)):
             ww = fn()
             others[name] = measure_forward(ww, device, stream, min(args.steps, 300), 5,
                                            adjoint=adj)
@@ -594,7 +599,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batching",
-                    choices=["batching", "swe", "adjoint", "hpcg"])
+                    choices=["batching", "swe", "adjoint", "hpcg", "sync"])
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--layout", default="level_innermost",
                     choices=["level_innermost", "level_outermost"])

@@ -71,7 +71,8 @@ typedef enum bc_kind {
   BC_CONST = 1,  /* A_ij = 0, b_i = values[i]  (pure-function boundary)    */
   BC_MAP = 2,    /* one unit entry at an affine image of the ghost index   */
   BC_INTERP = 3, /* p-point row along an axis of a source block            */
-  BC_CSR = 4     /* user CSR rows                                           */
+  BC_CSR = 4,    /* user CSR rows                                           */
+  BC_SYNC = 5    /* block-edge averaging: CSR rows on shared data cells     */
 } bc_kind;
 
 typedef enum bc_geometry {
@@ -135,6 +136,16 @@ typedef struct bc_grid {
  *              (col_block, col_comp, col_ijk[3]) and values val; rhs[r] (or
  *              NULL for zero) is added.  Rows repeat per level and read the
  *              same level of their column blocks.
+ * BC_SYNC   -- block-edge averaging (Sync of Sec. III-B): the fields of
+ *              BC_CSR, but the box lies in the *data* region and its rows
+ *              overwrite those data cells (cells several blocks store for
+ *              one physical location); rhs must be NULL or zero.  One apply
+ *              is one application of A: every row reads the input values, so
+ *              Sync rows are computed into a plan-owned staging buffer and
+ *              written after all other rows have read the data.  Two Sync
+ *              boxes must not share a data cell (BC_ERR_OVERLAP).  Because of
+ *              the staging buffer, applies of one plan with Sync rows must
+ *              not run concurrently on several streams.
  */
 typedef struct bc_submatrix {
   int32_t kind;
@@ -193,7 +204,7 @@ typedef struct bc_plan bc_plan;
 
 /* Plan statistics (byte counts use the plan's element size S). */
 typedef struct bc_stats {
-  int64_t ghost_values;       /* rows of A over all levels                  */
+  int64_t ghost_values;       /* ghost rows of A over all levels            */
   int64_t ghost_values_kind[5];
   int64_t nitems;             /* forward work items                         */
   int64_t nitems_adjoint;     /* adjoint gather items                       */
@@ -207,7 +218,8 @@ typedef struct bc_stats {
   int32_t form_threads;
   int32_t form_ctas_per_sm;
   int32_t units_per_lane;
-  int32_t reserved[4];
+  int32_t reserved[2];
+  int64_t sync_values;        /* Sync rows over all levels (data values)    */
 } bc_stats;
 
 /*
@@ -259,12 +271,14 @@ bc_status bc_apply_form(bc_plan* plan, void* const* slot_ptrs, int32_t form,
 
 /*
  * Adjoint of the in-place forward apply, in place on the cotangent fields
- * given by slot_ptrs (device array): x_D_bar = y_D_bar + A^T y_G_bar, then
- * every covered ghost value is set to 0; uncovered ghosts are left as they
- * are.  Deterministic: each data value sums its entries in ascending order
- * of (ghost slot, ghost offset), without atomics.  Two launches (gather,
- * then zero).  Fails with BC_ERR_UNSUPPORTED if the plan was built with
- * no_adjoint.
+ * given by slot_ptrs (device array): x_bar_j = y_bar_j + sum_i A_ij y_bar_i
+ * for every data value j that no row overwrites, x_bar_j = sum_i A_ij
+ * y_bar_i for the data values Sync rows overwrite, and 0 for covered ghost
+ * values; uncovered ghosts are left as they are.  Deterministic: each data
+ * value sums its entries in ascending order of (row slot, row offset),
+ * without atomics.  Two launches (gather, then zero), plus two for Sync
+ * rows (a snapshot of their cotangents before, their gather after).  Fails
+ * with BC_ERR_UNSUPPORTED if the plan was built with no_adjoint.
  */
 bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs,
                            void* stream);

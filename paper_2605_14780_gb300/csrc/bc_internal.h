@@ -136,6 +136,33 @@ cudaError_t launch_cs_geometry(const CsPanels& pan, const int4* cells,
 // Sets the message bc_last_error() returns on this thread (plan.cpp).
 void set_last_error(const char* msg);
 
+// Block-edge averaging (Sync rows on data cells, Sec. III-B), device side.
+// Rows {slot, offset (level 0), staging offset, levels}, entries
+// {slot, offset} with weights in the plan's dtype; for the adjoint, the
+// columns the rows read {slot, offset, levels, 0} with their entries
+// {staging offset of the row} and weights.  `stage` holds one value per row
+// and level.
+struct SyncCtx {
+  int nrows = 0, ncols = 0;
+  const int4* row = nullptr;
+  const int32_t* ptr = nullptr;
+  const int2* ent = nullptr;
+  const void* w = nullptr;
+  const int4* col = nullptr;
+  const int32_t* cptr = nullptr;
+  const int32_t* cstage = nullptr;
+  const void* cw = nullptr;
+  void* stage = nullptr;
+};
+enum SyncStep : int32_t {
+  SYNC_ROWS = 0,      // stage = A_sync x (reads data)
+  SYNC_COMMIT = 1,    // data = stage
+  SYNC_SNAPSHOT = 2,  // stage = y_bar of the Sync rows, then y_bar = 0
+  SYNC_ADJOINT = 3    // x_bar += A_sync^T stage
+};
+cudaError_t launch_sync(int dtype, int step, const SyncCtx& s, void* const* slots,
+                        const int32_t* slot_ls, cudaStream_t stream);
+
 enum CsError : unsigned {
   CS_ERR_NOT_EDGE = 1u,     // a cell is not an edge ghost
   CS_ERR_DEPTH = 2u,        // ghost point is not on a neighbour data row

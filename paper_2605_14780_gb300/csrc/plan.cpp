@@ -130,6 +130,21 @@ struct bc_plan {
   std::vector<int4> add_runs;
   std::vector<AddSeg> add_segs;
   bool has_adjoint = false;
+  // block-edge averaging (Sync rows on data cells): rows {slot, offset,
+  // staging offset, levels}, CSR entries, and for the adjoint the columns
+  // they read with {staging offset of the row, weight} entries
+  struct SyncTabs {
+    std::vector<int4> row;
+    std::vector<int32_t> ptr{0};
+    std::vector<int2> ent;
+    std::vector<double> w;
+    std::vector<int4> col;
+    std::vector<int32_t> cptr{0};
+    std::vector<int32_t> cstage;
+    std::vector<double> cw;
+    int64_t stage = 0;  // staging values (rows x levels)
+  } sync;
+  SyncCtx sync_ctx{};
   // work lists
   std::vector<Item> items, adj_items, adj_zero, adj_add;
   std::vector<Item> fam_items[kFamilies];  // batched form: per family, sub-matrix order
@@ -244,7 +259,7 @@ void for_box(const Sub& s, F f) {
 bc_status read_sub(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
   s.kind = m.kind;
   s.block = m.block;
-  if (m.kind < BC_ZERO || m.kind > BC_CSR)
+  if (m.kind < BC_ZERO || m.kind > BC_SYNC)
     return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: unknown kind %d", idx, m.kind);
   if (m.block < 0 || m.block >= (int)P->blocks.size())
     return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: bad block %d", idx, m.block);
@@ -438,6 +453,106 @@ bc_status add_csr(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
 
 // INTERP rows are appended after the geometry is known (cubed sphere: after
 // the GPU kernel); this records the stencil tables.
+// Block-edge averaging (Sync of Sec. III-B): CSR rows on data cells of the
+// box; every data cell may be overwritten by at most one Sync row.
+bc_status add_sync(bc_plan* P, const bc_submatrix& m, int idx, Coverage& dcov) {
+  Sub s;
+  bc_status st = read_sub(P, m, idx, s);
+  if (st != BC_OK) return st;
+  const bc_block& B = P->blocks[s.block];
+  if (!m.row_ptr || !m.col_block || !m.col_comp || !m.col_ijk || !m.val)
+    return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: Sync arrays missing", idx);
+  const int64_t nrows = (int64_t)s.comps.size() * s.vol;
+  if (m.row_ptr[0] != 0) return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: row_ptr[0] != 0", idx);
+  for (int64_t r = 0; r < nrows; ++r)
+    if (m.row_ptr[r + 1] < m.row_ptr[r])
+      return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: row_ptr not monotone", idx);
+  if (m.row_ptr[nrows] + (int64_t)P->sync.ent.size() > INT32_MAX)
+    return fail(BC_ERR_UNSUPPORTED, "sub-matrix %d: too many Sync entries", idx);
+  for (size_t c = 0; c < s.comps.size(); ++c) {
+    const int slot = P->slot_base[s.block] + s.comps[c];
+    bc_status err = BC_OK;
+    for_box(s, [&](int q, int i, int j, int k) {
+      if (err != BC_OK) return;
+      if (!in_data(B, i, j, k)) {
+        err = fail(BC_ERR_OUT_OF_RANGE, "sub-matrix %d: Sync box contains ghost cells", idx);
+        return;
+      }
+      if (!dcov.mark(slot, i, j, k)) {
+        err = fail(BC_ERR_OVERLAP, "sub-matrix %d: Sync rows overlap an earlier Sync box", idx);
+        return;
+      }
+      const int64_t r = (int64_t)c * s.vol + q;
+      if (m.rhs && m.rhs[r] != 0.0) {
+        err = fail(BC_ERR_INVALID_ARG, "sub-matrix %d: Sync rows have b = 0", idx);
+        return;
+      }
+      for (int64_t e = m.row_ptr[r]; e < m.row_ptr[r + 1]; ++e) {
+        const int cb = m.col_block[e], cc = m.col_comp[e];
+        const int ci = m.col_ijk[3 * e], cj = m.col_ijk[3 * e + 1], ck = m.col_ijk[3 * e + 2];
+        if (cb < 0 || cb >= (int)P->blocks.size() || cc < 0 || cc >= P->blocks[cb].ncomp) {
+          err = fail(BC_ERR_INVALID_ARG, "sub-matrix %d: bad column block/component", idx);
+          return;
+        }
+        const bc_block& C = P->blocks[cb];
+        if (!in_data(C, ci, cj, ck)) {
+          err = fail(BC_ERR_COLUMN_NOT_DATA, "sub-matrix %d: column (%d,%d,%d) of block %d is not data",
+                     idx, ci, cj, ck, cb);
+          return;
+        }
+        if (C.nlevels != B.nlevels) {
+          err = fail(BC_ERR_INVALID_ARG, "sub-matrix %d: column block has another level count", idx);
+          return;
+        }
+        if (!std::isfinite(m.val[e])) {
+          err = fail(BC_ERR_INVALID_ARG, "sub-matrix %d: non-finite value", idx);
+          return;
+        }
+        P->sync.ent.push_back(make_int2(P->slot_base[cb] + cc, (int)cell_offset(C, ci, cj, ck)));
+        P->sync.w.push_back(m.val[e]);
+      }
+      P->sync.row.push_back(make_int4(slot, (int)cell_offset(B, i, j, k), (int)P->sync.stage,
+                                      B.nlevels));
+      P->sync.ptr.push_back((int32_t)P->sync.ent.size());
+      P->sync.stage += B.nlevels;
+    });
+    if (err != BC_OK) return err;
+  }
+  if (P->sync.stage > INT32_MAX) return fail(BC_ERR_UNSUPPORTED, "too many Sync values");
+  return BC_OK;
+}
+
+// Columns read by Sync rows and their entries {staging offset, weight}, in
+// ascending (row) order per column: the adjoint's gather table.
+void build_sync_transpose(bc_plan* P) {
+  auto& S = P->sync;
+  struct E {
+    int32_t slot, off, stage;
+    double w;
+    int L;
+  };
+  std::vector<E> ents;
+  for (size_t r = 0; r < S.row.size(); ++r)
+    for (int32_t e = S.ptr[r]; e < S.ptr[r + 1]; ++e)
+      ents.push_back({S.ent[e].x, S.ent[e].y, S.row[r].z, S.w[e], S.row[r].w});
+  std::stable_sort(ents.begin(), ents.end(), [](const E& a, const E& b) {
+    return a.slot != b.slot ? a.slot < b.slot : a.off < b.off;
+  });
+  S.col.clear();
+  S.cptr.assign(1, 0);
+  S.cstage.clear();
+  S.cw.clear();
+  for (size_t e = 0; e < ents.size(); ++e) {
+    if (e == 0 || ents[e].slot != ents[e - 1].slot || ents[e].off != ents[e - 1].off) {
+      if (e) S.cptr.push_back((int32_t)S.cstage.size());
+      S.col.push_back(make_int4(ents[e].slot, ents[e].off, ents[e].L, 0));
+    }
+    S.cstage.push_back(ents[e].stage);
+    S.cw.push_back(ents[e].w);
+  }
+  if (!ents.empty()) S.cptr.push_back((int32_t)S.cstage.size());
+}
+
 bc_status read_interp(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
   if (m.p < 1 || m.p > kPMax)
     return fail(BC_ERR_UNSUPPORTED, "sub-matrix %d: p must be in 1..%d", idx, kPMax);
@@ -1117,7 +1232,23 @@ bc_status upload_tables(bc_plan* P) {
   const size_t o_es = L.take(P->aent_slot.size() * 4);
   const size_t o_eo = L.take(P->aent_off.size() * 4);
   const size_t o_ew = L.take(P->aent_w.size() * S);
+  const auto& Y = P->sync;
+  const size_t o_yr = L.take(Y.row.size() * sizeof(int4));
+  const size_t o_yp = L.take(Y.ptr.size() * 4);
+  const size_t o_ye = L.take(Y.ent.size() * sizeof(int2));
+  const size_t o_yw = L.take(Y.w.size() * S);
+  const size_t o_yc = L.take(Y.col.size() * sizeof(int4));
+  const size_t o_ycp = L.take(Y.cptr.size() * 4);
+  const size_t o_ycs = L.take(Y.cstage.size() * 4);
+  const size_t o_ycw = L.take(Y.cw.size() * S);
+  const size_t o_yst = L.take((size_t)Y.stage * S);
   std::vector<char> host(L.off + 256, 0);
+  put_raw(host, o_yr, Y.row);
+  put_raw(host, o_yp, Y.ptr);
+  put_raw(host, o_ye, Y.ent);
+  put_raw(host, o_yc, Y.col);
+  put_raw(host, o_ycp, Y.cptr);
+  put_raw(host, o_ycs, Y.cstage);
   put_raw(host, o_ls, P->slot_ls);
   put_raw(host, o_cd, P->ctab_d);
   put_raw(host, o_cs2, P->ctab_s);
@@ -1137,6 +1268,8 @@ bc_status upload_tables(bc_plan* P) {
     put_dtype<double>(host, o_cr, P->csr_rhs);
     put_dtype<double>(host, o_k, P->const_val);
     put_dtype<double>(host, o_ew, P->aent_w);
+    put_dtype<double>(host, o_yw, Y.w);
+    put_dtype<double>(host, o_ycw, Y.cw);
   } else {
     put_dtype<float>(host, o_w, P->itp_w);
     put_dtype<float>(host, o_m, P->itp_m);
@@ -1144,6 +1277,8 @@ bc_status upload_tables(bc_plan* P) {
     put_dtype<float>(host, o_cr, P->csr_rhs);
     put_dtype<float>(host, o_k, P->const_val);
     put_dtype<float>(host, o_ew, P->aent_w);
+    put_dtype<float>(host, o_yw, Y.w);
+    put_dtype<float>(host, o_ycw, Y.cw);
   }
   cudaError_t e = cudaMalloc(&P->tables.base, host.size());
   if (e != cudaSuccess) {
@@ -1173,6 +1308,18 @@ bc_status upload_tables(bc_plan* P) {
   c.aent_slot = reinterpret_cast<const int32_t*>(b + o_es);
   c.aent_off = reinterpret_cast<const int32_t*>(b + o_eo);
   c.aent_w = b + o_ew;
+  SyncCtx& y = P->sync_ctx;
+  y.nrows = (int)Y.row.size();
+  y.ncols = (int)Y.col.size();
+  y.row = reinterpret_cast<const int4*>(b + o_yr);
+  y.ptr = reinterpret_cast<const int32_t*>(b + o_yp);
+  y.ent = reinterpret_cast<const int2*>(b + o_ye);
+  y.w = b + o_yw;
+  y.col = reinterpret_cast<const int4*>(b + o_yc);
+  y.cptr = reinterpret_cast<const int32_t*>(b + o_ycp);
+  y.cstage = reinterpret_cast<const int32_t*>(b + o_ycs);
+  y.cw = b + o_ycw;
+  y.stage = b + o_yst;
   return BC_OK;
 }
 
@@ -1253,9 +1400,20 @@ void compute_stats(bc_plan* P) {
   std::sort(csr_cols.begin(), csr_cols.end());
   csr_cols.erase(std::unique(csr_cols.begin(), csr_cols.end()), csr_cols.end());
   for (auto& cc : csr_cols) bytes += L_of_slot(cc.first) * S;
+  // Sync rows: written once, entries read per level, tables once
+  const auto& Y = P->sync;
+  st.sync_values = Y.stage;
+  for (size_t q = 0; q < Y.row.size(); ++q)
+    bytes += (int64_t)Y.row[q].w * S * (1 + Y.ptr[q + 1] - Y.ptr[q]) + 20 +
+             (int64_t)(Y.ptr[q + 1] - Y.ptr[q]) * (8 + S);
   st.bytes_fwd = bytes;
   int64_t abytes = 4 * st.ghost_values * S;
   abytes += P->adj_rows_total * 16 + P->adj_nnz_total * (8 + S);
+  // Sync: the rows' cotangents move to staging and back out through the
+  // column entries (read-modify-write of every column value)
+  for (size_t q = 0; q < Y.row.size(); ++q) abytes += 3 * (int64_t)Y.row[q].w * S;
+  for (size_t q = 0; q < Y.col.size(); ++q)
+    abytes += (int64_t)Y.col[q].z * S * (2 + Y.cptr[q + 1] - Y.cptr[q]);
   st.bytes_adj = abytes;
   st.nitems = (int64_t)P->items.size();
   st.nitems_adjoint = (int64_t)P->adj_items.size();
@@ -1314,11 +1472,15 @@ bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_
   cov.slot_block = &P->slot_block;
   std::vector<const bc_submatrix*> cs_subs;
   std::vector<int> cs_idx;
-  P->subs.resize(nsubs);
+  // Sync rows (data cells) are kept apart from the ghost sub-matrices
+  std::vector<int> reg, syn;
+  for (int si = 0; si < nsubs; ++si) (subs[si].kind == BC_SYNC ? syn : reg).push_back(si);
+  P->subs.resize(reg.size());
   // pass 1: validation, coverage, tables of every kind but cubed-sphere rows
-  for (int si = 0; si < nsubs; ++si) {
+  for (size_t t = 0; t < reg.size(); ++t) {
+    const int si = reg[t];
     const bc_submatrix& m = subs[si];
-    Sub& s = P->subs[si];
+    Sub& s = P->subs[t];
     if ((st = read_sub(P, m, si, s)) != BC_OK) return st;
     const bc_block& B = P->blocks[s.block];
     bool ok = true, ghost = true;
@@ -1340,11 +1502,20 @@ bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_
         st = read_interp(P, m, si, s);
         if (st == BC_OK && m.geometry == BC_GEOM_CUBED_SPHERE) {
           cs_subs.push_back(&m);
-          cs_idx.push_back(si);
+          cs_idx.push_back((int)t);
         }
         break;
     }
     if (st != BC_OK) return st;
+  }
+  {
+    Coverage dcov;
+    dcov.map.resize(P->nslots);
+    dcov.blocks = &P->blocks;
+    dcov.slot_block = &P->slot_block;
+    for (int si : syn)
+      if ((st = add_sync(P, subs[si], si, dcov)) != BC_OK) return st;
+    build_sync_transpose(P);
   }
   // cell tables: every box cell's offset, and the source cell of maps
   for (Sub& s2 : P->subs) {
@@ -1441,6 +1612,11 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
   c.slots = slots;
   cudaError_t e = cudaSuccess;
   const int T = P->opts.threads;
+  // Sync rows read the input data: evaluate them into the staging buffer
+  // before any ghost is written, write them back after every kernel that
+  // reads data has run
+  if ((e = launch_sync(P->dtype, SYNC_ROWS, P->sync_ctx, slots, c.slot_ls, s)) != cudaSuccess)
+    return cuda_fail(e, "Sync rows");
   if (form == BC_FORM_BATCHED) {
     // one launch per kernel family, the families side by side
     int fams[kFamilies], nf = 0;
@@ -1469,6 +1645,7 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
   } else {
     return fail(BC_ERR_INVALID_ARG, "unknown form %d", form);
   }
+  if (e == cudaSuccess) e = launch_sync(P->dtype, SYNC_COMMIT, P->sync_ctx, slots, c.slot_ls, s);
   if (e != cudaSuccess) return cuda_fail(e, "forward launch");
   return BC_OK;
 }
@@ -1552,10 +1729,17 @@ bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs, void* stream) 
   c.slots = slot_ptrs;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int T = plan->opts.threads;
+  // Sync rows: their data cells' cotangents move to the staging buffer
+  // (consumed by the rows that overwrite them) before the gathers run
+  cudaError_t e =
+      launch_sync(plan->dtype, SYNC_SNAPSHOT, plan->sync_ctx, slot_ptrs, c.slot_ls, s);
   // one launch for the gather and the add-runs (disjoint targets), then the
-  // zero pass over the ghost values both of them read
-  cudaError_t e = launch_family(plan->dtype, FAM_ADJ, c, plan->d_adj,
-                                (int)plan->adj_items.size(), T, stream_grid(plan, FAM_ADJ), s);
+  // Sync columns, then the zero pass over the ghost values they read
+  if (e == cudaSuccess)
+    e = launch_family(plan->dtype, FAM_ADJ, c, plan->d_adj, (int)plan->adj_items.size(), T,
+                      stream_grid(plan, FAM_ADJ), s);
+  if (e == cudaSuccess)
+    e = launch_sync(plan->dtype, SYNC_ADJOINT, plan->sync_ctx, slot_ptrs, c.slot_ls, s);
   if (e == cudaSuccess)
     e = launch_family(plan->dtype, FAM_STRUCT, c, plan->d_adj_zero,
                       (int)plan->adj_zero.size(), T, stream_grid(plan, FAM_STRUCT), s);
@@ -1678,7 +1862,14 @@ bc_status bc_plan_export_csr(const bc_plan* plan, int64_t* nrows, int64_t* nnz, 
                              int64_t* row_off, int64_t* row_ptr, int32_t* col_slot,
                              int64_t* col_off, double* val, double* rhs) {
   if (!plan || !nrows || !nnz) return fail(BC_ERR_INVALID_ARG, "NULL argument");
-  const ExplicitRows& R = plan->rows;
+  // ghost rows, then the Sync rows (data cells) in one explicit row list
+  ExplicitRows R = plan->rows;
+  const auto& Y = plan->sync;
+  for (size_t q = 0; q < Y.row.size(); ++q) {
+    R.begin_row(Y.row[q].x, Y.row[q].y, 0.0);
+    for (int32_t e = Y.ptr[q]; e < Y.ptr[q + 1]; ++e) R.entry(Y.ent[e].x, Y.ent[e].y, Y.w[e]);
+    R.end_row();
+  }
   *nrows = (int64_t)R.slot.size();
   *nnz = (int64_t)R.val.size();
   if (!row_slot) return BC_OK;

@@ -93,8 +93,9 @@ bc_status prune_submatrices(const bc_grid* grid, const bc_submatrix* subs, int n
   out.subs.clear();
   for (int si = 0; si < nsubs; ++si) {
     const bc_submatrix& m = subs[si];
-    // anything the plan would reject is passed through for it to report
-    if (m.block < 0 || m.block >= grid->nblocks || m.ncomps < 0) {
+    // anything the plan would reject is passed through for it to report;
+    // Sync rows are data cells, not ghost writes, and stay as they are
+    if (m.kind == BC_SYNC || m.block < 0 || m.block >= grid->nblocks || m.ncomps < 0) {
       out.subs.push_back(m);
       continue;
     }

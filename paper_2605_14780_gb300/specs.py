@@ -25,7 +25,7 @@ import itertools
 
 import numpy as np
 
-BC_ZERO, BC_CONST, BC_MAP, BC_INTERP, BC_CSR = range(5)
+BC_ZERO, BC_CONST, BC_MAP, BC_INTERP, BC_CSR, BC_SYNC = range(6)
 BC_GEOM_USER, BC_GEOM_CUBED_SPHERE = 0, 1
 
 
@@ -209,6 +209,11 @@ def submatrices(w):
                             sign=tuple(bc["sign"]), offset=tuple(bc["offset"])))
         elif k == "csr":
             out.append(_sub(BC_CSR, bc["block"], bc["lo"], bc["hi"], bc["comps"],
+                            row_ptr=bc["row_ptr"], col_block=bc["col_block"],
+                            col_comp=bc["col_comp"], col_ijk=bc["col_ijk"],
+                            val=bc["val"], rhs=bc.get("rhs")))
+        elif k == "sync":
+            out.append(_sub(BC_SYNC, bc["block"], bc["lo"], bc["hi"], bc["comps"],
                             row_ptr=bc["row_ptr"], col_block=bc["col_block"],
                             col_comp=bc["col_comp"], col_ijk=bc["col_ijk"],
                             val=bc["val"], rhs=bc.get("rhs")))

@@ -157,3 +157,43 @@ def test_specs_halo_and_faces_cover_every_ghost():
         assert np.all(inner == 0)
         c[2:2 + b["n"][1], 2:2 + b["n"][0]] = 1
         assert np.all(c == 1)
+
+
+def _sync_workload():
+    return synth.sync_grid(2, 2, 5, 1, nlevels=2, ncomp=1, dtype="f32", seed=3)
+
+
+def test_rejects_sync_box_in_the_ghost_region(lib):
+    w = _sync_workload()
+    s = next(b for b in w["bcs"] if b["kind"] == "sync")
+    n = w["blocks"][s["block"]]["n"]
+    # move the box one cell past the data: its cells become ghosts
+    hi = list(s["hi"])
+    if s["lo"][0] == n[0] - 1:
+        s["lo"], hi[0] = (n[0], s["lo"][1], 0), n[0] + 1
+    else:
+        s["lo"], hi[1] = (s["lo"][0], n[1], 0), n[1] + 1
+    s["hi"] = tuple(hi)
+    _expect(w, "BC_ERR_OUT_OF_RANGE")
+
+
+def test_rejects_overlapping_sync_rows(lib):
+    w = _sync_workload()
+    s = next(b for b in w["bcs"] if b["kind"] == "sync")
+    w["bcs"].append(dict(s))
+    _expect(w, "BC_ERR_OVERLAP")
+
+
+def test_rejects_sync_rows_with_a_constant(lib):
+    w = _sync_workload()
+    s = next(b for b in w["bcs"] if b["kind"] == "sync")
+    s["rhs"] = np.full(len(s["row_ptr"]) - 1, 0.5)
+    _expect(w, "BC_ERR_INVALID_ARG")
+
+
+def test_rejects_sync_rows_reading_ghosts(lib):
+    w = _sync_workload()
+    s = next(b for b in w["bcs"] if b["kind"] == "sync")
+    s["col_ijk"] = s["col_ijk"].copy()
+    s["col_ijk"][0] = (-1, 0, 0)
+    _expect(w, "BC_ERR_COLUMN_NOT_DATA")
