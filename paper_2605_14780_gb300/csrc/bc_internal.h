@@ -144,6 +144,10 @@ void set_last_error(const char* msg);
 // and level.
 struct SyncCtx {
   int nrows = 0, ncols = 0;
+  int lmax = 0;         // most levels of any Sync row / column
+  int level_fast = 0;   // 1: consecutive threads take consecutive levels
+                        //    (levels contiguous in memory), 0: consecutive
+                        //    rows at one level
   const int4* row = nullptr;
   const int32_t* ptr = nullptr;
   const int2* ent = nullptr;

@@ -1311,6 +1311,12 @@ bc_status upload_tables(bc_plan* P) {
   SyncCtx& y = P->sync_ctx;
   y.nrows = (int)Y.row.size();
   y.ncols = (int)Y.col.size();
+  y.lmax = 0;
+  y.level_fast = 1;
+  for (const int4& r : Y.row) {
+    y.lmax = std::max(y.lmax, r.w);
+    if (r.w > 1 && P->slot_ls[r.x] != 1) y.level_fast = 0;
+  }
   y.row = reinterpret_cast<const int4*>(b + o_yr);
   y.ptr = reinterpret_cast<const int32_t*>(b + o_yp);
   y.ent = reinterpret_cast<const int2*>(b + o_ye);
@@ -1613,17 +1619,28 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
   cudaError_t e = cudaSuccess;
   const int T = P->opts.threads;
   // Sync rows read the input data: evaluate them into the staging buffer
-  // before any ghost is written, write them back after every kernel that
-  // reads data has run
-  if ((e = launch_sync(P->dtype, SYNC_ROWS, P->sync_ctx, slots, c.slot_ls, s)) != cudaSuccess)
+  // while the ghost kernels run (they write only ghosts), write them back
+  // after every kernel that reads data has run
+  const bool sync = P->sync_ctx.nrows > 0;
+  if (sync && form != BC_FORM_BATCHED &&
+      (e = launch_sync(P->dtype, SYNC_ROWS, P->sync_ctx, slots, c.slot_ls, s)) != cudaSuccess)
     return cuda_fail(e, "Sync rows");
   if (form == BC_FORM_BATCHED) {
     // one launch per kernel family, the families side by side
     int fams[kFamilies], nf = 0;
     for (int f = 0; f < kFamilies; ++f)
       if (!P->fam_items[f].empty()) fams[nf++] = f;
-    if (nf > 1 && (e = cudaEventRecord(P->ev_fork, s)) != cudaSuccess)
+    // the Sync rows take the last plan stream (the forward has at most three
+    // kernel families, so it is free)
+    cudaStream_t ys = P->aux[kFamilies - 2];
+    if ((nf > 1 || sync) && (e = cudaEventRecord(P->ev_fork, s)) != cudaSuccess)
       return cuda_fail(e, "fork event");
+    if (sync) {
+      if ((e = cudaStreamWaitEvent(ys, P->ev_fork, 0)) != cudaSuccess ||
+          (e = launch_sync(P->dtype, SYNC_ROWS, P->sync_ctx, slots, c.slot_ls, ys)) != cudaSuccess ||
+          (e = cudaEventRecord(P->ev_join[kFamilies - 2], ys)) != cudaSuccess)
+        return cuda_fail(e, "Sync rows");
+    }
     for (int t = 0; t < nf && e == cudaSuccess; ++t) {
       cudaStream_t st = t == 0 ? s : P->aux[t - 1];
       if (t > 0 && (e = cudaStreamWaitEvent(st, P->ev_fork, 0)) != cudaSuccess) break;
@@ -1633,6 +1650,7 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
     }
     for (int t = 1; t < nf && e == cudaSuccess; ++t)
       e = cudaStreamWaitEvent(s, P->ev_join[t - 1], 0);
+    if (sync && e == cudaSuccess) e = cudaStreamWaitEvent(s, P->ev_join[kFamilies - 2], 0);
   } else if (form == BC_FORM_TYPEWIDE) {
     for (int k = 0; k < 5 && e == cudaSuccess; ++k)
       e = launch_family(P->dtype, family_of_kind(k), c, P->d_items + P->type_begin[k],
