@@ -114,8 +114,12 @@ typedef struct bc_grid {
  *              with axis 0 fastest; rounded to the plan's dtype.
  * BC_MAP    -- the ghost g of component c reads component c of src_block at
  *              src[d] = sign[d] * g[perm[d]] + offset[d]  (perm a permutation
- *              of 0..2, sign +-1): halo copy, circular and symmetric maps
- *              (Sec. III-B fmap), and the rotated map of Alg. 1.
+ *              of 0..2): with sign +-1 the halo copy, circular and symmetric
+ *              maps (Sec. III-B fmap) and the rotated map of Alg. 1; with
+ *              |sign| > 1 (up to 65536) an injection that reads every
+ *              |sign|-th cell, for blocks whose regions are slices of one
+ *              global grid with different steps (Sec. III-A: staggered and
+ *              multigrid layouts).  sign = 0 is rejected.
  * BC_INTERP -- row of cell q reads p consecutive data cells of one source
  *              block along one axis, y = sum_k w[q][k] x[node_k].
  *              geometry = BC_GEOM_USER: itp_src_block[vol], itp_start[vol*3]

@@ -315,6 +315,8 @@ bc_status add_zero_const(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
   return BC_OK;
 }
 
+constexpr int kMaxMapScale = 1 << 16;
+
 bc_status add_map(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
   const bc_block& B = P->blocks[s.block];
   if (m.src_block < 0 || m.src_block >= (int)P->blocks.size())
@@ -326,8 +328,11 @@ bc_status add_map(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
     if (m.perm[d] < 0 || m.perm[d] > 2 || seen[m.perm[d]])
       return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: perm is not a permutation", idx);
     seen[m.perm[d]] = true;
-    if (m.sign[d] != 1 && m.sign[d] != -1)
-      return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: sign must be +-1", idx);
+    // +-1: halo copies and reflections; |s| > 1: injection between blocks
+    // whose grids are slices of one global grid with steps in ratio |s|
+    if (m.sign[d] == 0 || m.sign[d] > kMaxMapScale || m.sign[d] < -kMaxMapScale)
+      return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: map scale must be nonzero, |scale| <= %d",
+                  idx, kMaxMapScale);
     s.perm[d] = m.perm[d];
     s.sign[d] = m.sign[d];
     s.offset[d] = m.offset[d];

@@ -27,7 +27,8 @@ bc kinds (the descriptions; each side turns them into rows on its own)
     ``const``  ``{block, lo, hi, comps, values[ncomp_sel, box_volume]}``.
     ``map``    ``{block, lo, hi, comps, src_block, perm, sign, offset}``:
                the source cell of ghost ``g`` is
-               ``src[d] = sign[d] * g[perm[d]] + offset[d]``.
+               ``src[d] = sign[d] * g[perm[d]] + offset[d]`` (``|sign| > 1``
+               injects from a finer grid).
     ``csr``    ``{block, lo, hi, comps, row_ptr, col_block, col_comp,
                col_ijk[nnz, 3], val[nnz], rhs[nrows] | None}``; row order is
                comp-major, then the box cells with axis 0 fastest.  A row is
@@ -550,3 +551,53 @@ def sync_grid(bx=3, by=3, n=17, h=2, nlevels=4, ncomp=2, dtype="f64", seed=12):
     fields = uniform_fields(rng_blocks, dtype, -1.0, 1.0, seed)
     return {"name": f"sync{bx}x{by}_n{n}", "dtype": dtype, "blocks": rng_blocks,
             "bcs": bcs, "fields": fields}
+
+
+# ----------------------------------------------------------------------------
+# two grid levels side by side: region steps 1 and 2 (Sec. III-A)
+# ----------------------------------------------------------------------------
+def two_level(nx=32, ny=24, h=2, nlevels=3, ncomp=1, dtype="f64", seed=13):
+    """A fine cell-centred block (``nx`` x ``ny``, step 1) and, to its right,
+    a coarse one (``nx/2`` x ``ny/2``, step 2) of one global grid.  The
+    coarse block's left ghosts inject the fine cell at the lower-left corner
+    of each coarse cell (a ``map`` with scale 2); the fine block's right
+    ghosts copy the coarse cell that contains them (``csr`` rows, piecewise
+    constant prolongation); every other ghost is zero."""
+    assert nx % 2 == 0 and ny % 2 == 0
+    fine = block2d(nx, ny, h, nlevels, ncomp)
+    coarse = block2d(nx // 2, ny // 2, h, nlevels, ncomp)
+    comps = list(range(ncomp))
+    bcs = [{"kind": "map", "block": 1, "lo": (-h, 0, 0), "hi": (0, ny // 2, 1),
+            "comps": comps, "src_block": 0, "perm": (0, 1, 2), "sign": (2, 2, 1),
+            "offset": (nx, 0, 0)}]
+    cells = [(i, j) for j in range(ny) for i in range(nx, nx + h)]
+    row_ptr, cb, cc, cijk, val = [0], [], [], [], []
+    for c in comps:
+        for i, j in cells:
+            cb.append(1)
+            cc.append(c)
+            cijk.append(((i - nx) // 2, j // 2, 0))
+            val.append(1.0)
+            row_ptr.append(len(val))
+    bcs.append({"kind": "csr", "block": 0, "lo": (nx, 0, 0), "hi": (nx + h, ny, 1),
+                "comps": comps, "row_ptr": np.array(row_ptr, np.int64),
+                "col_block": np.array(cb, np.int32), "col_comp": np.array(cc, np.int32),
+                "col_ijk": np.array(cijk, np.int32).reshape(-1, 3),
+                "val": np.array(val, np.float64), "rhs": None})
+    for b, blk in enumerate((fine, coarse)):
+        n = blk["n"]
+        for axis in (0, 1):
+            for side in (0, 1):
+                if (b, axis, side) in ((0, 0, 1), (1, 0, 0)):
+                    continue
+                lo, hi = [0, 0, 0], [n[0], n[1], 1]
+                lo[axis], hi[axis] = (-h, 0) if side == 0 else (n[axis], n[axis] + h)
+                bcs.append({"kind": "zero", "block": b, "lo": tuple(lo), "hi": tuple(hi),
+                            "comps": comps})
+        for cx in ((-h, 0), (n[0], n[0] + h)):
+            for cy in ((-h, 0), (n[1], n[1] + h)):
+                bcs.append({"kind": "zero", "block": b, "lo": (cx[0], cy[0], 0),
+                            "hi": (cx[1], cy[1], 1), "comps": comps})
+    blocks = [fine, coarse]
+    return {"name": f"two_level{nx}x{ny}", "dtype": dtype, "blocks": blocks, "bcs": bcs,
+            "fields": uniform_fields(blocks, dtype, -1.0, 1.0, seed)}

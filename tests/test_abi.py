@@ -197,3 +197,10 @@ def test_rejects_sync_rows_reading_ghosts(lib):
     s["col_ijk"] = s["col_ijk"].copy()
     s["col_ijk"][0] = (-1, 0, 0)
     _expect(w, "BC_ERR_COLUMN_NOT_DATA")
+
+
+def test_rejects_zero_map_scale(lib):
+    w = synth.two_level(8, 6, 1, nlevels=1, ncomp=1, dtype="f32", seed=1)
+    m = next(b for b in w["bcs"] if b["kind"] == "map")
+    m["sign"] = (0, 2, 1)
+    _expect(w, "BC_ERR_INVALID_ARG")

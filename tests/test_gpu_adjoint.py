@@ -67,6 +67,7 @@ def _level_mask(w, levels):
                            lev_hi=19, h=2, seed=2, dtype="f32"),
     lambda: synth.cubed_sphere(9, 3, 6, 3, ("h", "u", "v"), "f64", seed=4),
     lambda: synth.cubed_sphere(16, 3, 6, 10, ("h", "u", "v"), "f32", seed=4),
+    lambda: synth.two_level(20, 14, 2, nlevels=3, ncomp=2, dtype="f64", seed=5),
 ])
 def test_adjoint_vs_oracle(make):
     w = make()

@@ -296,3 +296,16 @@ def _unflat(v, like):
         out.append(v[k:k + a.size].reshape(a.shape))
         k += a.size
     return out
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("layout", ["outermost", "innermost"])
+def test_two_level_scaled_maps(dtype, layout):
+    """Blocks of region steps 1 and 2: scale-2 injection maps and CSR
+    prolongation rows, against the oracle (copies bit-exact)."""
+    import torch
+    w = synth.two_level(40, 26, 2, nlevels=5, ncomp=2, dtype=dtype, seed=14)
+    ts = to_device_innermost(w["fields"]) if layout == "innermost" else to_device(w["fields"])
+    run(w, tensors=ts)
+    torch.cuda.synchronize()
+    compare(w, [t.cpu().numpy() for t in ts])

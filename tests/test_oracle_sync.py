@@ -101,3 +101,22 @@ def test_sync_rows_must_be_data_cells():
     s["hi"] = (0, s["hi"][1], 1)
     with pytest.raises(OracleError):
         build_operator(w)
+
+
+def test_two_level_injection_and_prolongation():
+    """Region steps 1 and 2 (Sec. III-A): the coarse block's left ghosts are
+    the fine cells at the lower-left corner of each coarse cell, the fine
+    block's right ghosts the coarse cells containing them."""
+    nx, ny, h = 12, 8, 2
+    w = synth.two_level(nx, ny, h, nlevels=2, ncomp=2, dtype="f64", seed=3)
+    out = apply(build_operator(w), w["fields"])
+    f, c = w["fields"][0], w["fields"][1]
+    for r in range(h):
+        for j in range(ny // 2):
+            # coarse ghost i = -1 - r  <-  fine data x = nx - 2 - 2 r, y = 2 j
+            assert np.array_equal(out[1][:, :, 0, h + j, h - 1 - r],
+                                  f[:, :, 0, h + 2 * j, h + nx - 2 - 2 * r])
+        for j in range(ny):
+            # fine ghost i = nx + r  <-  coarse data (r // 2, j // 2)
+            assert np.array_equal(out[0][:, :, 0, h + j, h + nx + r],
+                                  c[:, :, 0, h + j // 2, h + r // 2])
