@@ -996,13 +996,28 @@ void build_items(bc_plan* P) {
     }
     P->type_end[kind] = (int)P->items.size();
   }
-  // batched launch: sub-matrix order, so the kinds (loads + stores, stores
-  // only, table gathers) are interleaved over the grid
+  // batched launch: per family, longest items first
   for (auto& v : P->fam_items) v.clear();
   for (size_t si = 0; si < P->subs.size(); ++si) {
     const int f = family_of_kind(P->subs[si].kind);
     P->fam_items[f].insert(P->fam_items[f].end(), per_sub[si].second.begin(),
                            per_sub[si].second.end());
+  }
+  // longest items first, so the last wave of warps holds the short ones
+  // (512-block workload, levels innermost: batched step 49.2 -> 48.1 us)
+  auto work = [&](const Item& it) -> int64_t {
+    if (it.mode != MODE_RUNS) return it.nunits;
+    int64_t n = 0;
+    for (int r = it.u0; r < it.u0 + it.nunits; ++r) n += P->runs[r].z;
+    return n;
+  };
+  for (auto& v : P->fam_items) {
+    std::vector<std::pair<int64_t, size_t>> key(v.size());
+    for (size_t t = 0; t < v.size(); ++t) key[t] = {-work(v[t]), t};
+    std::stable_sort(key.begin(), key.end());
+    std::vector<Item> sorted(v.size());
+    for (size_t t = 0; t < v.size(); ++t) sorted[t] = v[key[t].second];
+    v.swap(sorted);
   }
   // adjoint: the zero pass over every covered ghost value
   P->adj_zero.clear();
