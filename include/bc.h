@@ -222,7 +222,8 @@ typedef struct bc_stats {
   int32_t form_threads;
   int32_t form_ctas_per_sm;
   int32_t units_per_lane;
-  int32_t reserved[2];
+  int32_t launches_fwd;       /* kernel launches of one batched forward      */
+  int32_t launches_adj;       /* kernel launches of one adjoint              */
   int64_t sync_values;        /* Sync rows over all levels (data values)    */
 } bc_stats;
 

@@ -68,7 +68,8 @@ class BcStats(ctypes.Structure):
                 ("table_bytes", c_i64), ("transpose_nnz", c_i64),
                 ("element_size", c_i32), ("form_threads", c_i32),
                 ("form_ctas_per_sm", c_i32), ("units_per_lane", c_i32),
-                ("reserved", c_i32 * 2), ("sync_values", c_i64)]
+                ("launches_fwd", c_i32), ("launches_adj", c_i32),
+                ("sync_values", c_i64)]
 
 
 #: every function the header declares, with (restype, argtypes)

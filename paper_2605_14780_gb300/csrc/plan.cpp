@@ -1451,6 +1451,10 @@ void compute_stats(bc_plan* P) {
   st.form_threads = P->opts.threads;
   st.form_ctas_per_sm = P->opts.ctas_per_sm;
   st.units_per_lane = P->opts.units_per_lane;
+  const int ys = P->sync_ctx.nrows > 0 ? 2 : 0;
+  st.launches_fwd = ys;
+  for (const auto& v : P->fam_items) st.launches_fwd += v.empty() ? 0 : 1;
+  st.launches_adj = P->has_adjoint ? ys + !P->adj_items.empty() + !P->adj_zero.empty() : 0;
 }
 
 bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
