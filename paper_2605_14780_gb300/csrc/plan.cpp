@@ -896,18 +896,28 @@ void build_items(bc_plan* P) {
   P->runs.clear();
   // units per warp item: single-level values (flat) or 8-level chunks
   const int upl = std::max(1, std::min(P->opts.units_per_lane, 64));
+  // A small plan still gets enough items to keep every SM busy: the value
+  // budget of an item shrinks (down to one value per lane) until the plan's
+  // values make about 16 items per SM (128^3 HPCG-like faces: 98 items of
+  // 1024 values took 26.7 us; 1560 items of 64 values take far less).
+  int64_t total_values = 0;
+  for (const Sub& s : P->subs)
+    total_values += (int64_t)s.comps.size() * s.vol * P->blocks[s.block].nlevels;
+  const int64_t want_items = (int64_t)std::max(1, P->num_sms) * 16;
+  const int small = (int)std::min<int64_t>(
+      1 << 30, std::max<int64_t>(32, (total_values + want_items - 1) / want_items + 31) / 32 * 32);
   const int per_chunk_item = 32 * upl;
-  const int per_flat_item = 32 * kFlatUnroll * upl;
+  const int per_flat_item = std::min(32 * kFlatUnroll * upl, small);
   // table-driven kinds (interpolation, CSR, transpose): one unit per lane, so
   // a warp's dependent table -> data chains run side by side, not in series
   const int per_table_item = 32;
-  const int per_table_flat_item = 32 * 8;
+  const int per_table_flat_item = std::min(32 * 8, small);
   auto structured_emit = [&](std::vector<Item>& out, const Item& it, const bc_block& B, int vol) {
     const int mode = structured_mode(B, P->opts.unit_order);
     emit_units(out, it, vol, B.nlevels, mode, mode < 2 ? per_flat_item : per_chunk_item);
   };
   // zero / map sub-matrices: runs when they are long, cached per sub-matrix
-  const int per_run_item = BC_RUN_ITEM * upl;
+  const int per_run_item = std::min(BC_RUN_ITEM * upl, small);
   std::vector<int> run_r0(P->subs.size(), -1), run_n(P->subs.size(), 0);
   for (size_t si = 0; si < P->subs.size(); ++si) {
     const Sub& s = P->subs[si];
