@@ -24,7 +24,10 @@ enum ItemKind : int32_t {
 };
 
 constexpr int kPMax = 8;         // largest interpolation stencil
-constexpr int kChunk = 8;        // levels of one unit (blocks with >= 8 levels)
+constexpr int kChunk = 8;  // levels of one unit (blocks with >= 8 levels)
+constexpr int kInterpChunk = 4;   // levels of one interpolation unit (6x768^2
+                                  // cubed sphere, levels outermost: forward
+                                  // 75.8 -> 65.0 us against 8)
 constexpr int kFlatUnroll = 8;   // single-level units in flight per lane
 #ifndef BC_RUN_UNROLL
 #define BC_RUN_UNROLL 8

@@ -254,38 +254,38 @@ __device__ void interp_scalar_chunk(const Item& it, const Ptrs& P, const Ctx& c,
     if (ix.w & kFlagSnap) {  // unit row: exact copy of node 0
       const B* s = reinterpret_cast<const B*>(x);
       B* db = reinterpret_cast<B*>(d);
-      B v[kChunk];
+      B v[kInterpChunk];
 #pragma unroll
-      for (int l = 0; l < kChunk; ++l)
+      for (int l = 0; l < kInterpChunk; ++l)
         if (l < nl) v[l] = ldg(s + l * sls);
 #pragma unroll
-      for (int l = 0; l < kChunk; ++l)
+      for (int l = 0; l < kInterpChunk; ++l)
         if (l < nl) db[l * ls] = v[l];
       continue;
     }
     const T* wr = static_cast<const T*>(c.itp_w) + row * kPMax;
-    T acc[kChunk];
+    T acc[kInterpChunk];
 #pragma unroll
-    for (int l = 0; l < kChunk; ++l) acc[l] = T(0);
+    for (int l = 0; l < kInterpChunk; ++l) acc[l] = T(0);
 #pragma unroll
     for (int n = 0; n < kPMax; ++n) {
       if (n < p) {
         const T w = ldg(wr + n);
         const T* xn = x + n * ix.z;
 #pragma unroll
-        for (int l = 0; l < kChunk; ++l)
+        for (int l = 0; l < kInterpChunk; ++l)
           if (l < nl) acc[l] = fma(w, ldg(xn + l * sls), acc[l]);
       }
     }
 #pragma unroll
-    for (int l = 0; l < kChunk; ++l)
+    for (int l = 0; l < kInterpChunk; ++l)
       if (l < nl) d[l * ls] = acc[l];
   }
 }
 
 template <typename T>
 __device__ void interp_pair_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
-  constexpr int LU = kChunk / 2;
+  constexpr int LU = kInterpChunk / 2;
   const int end = it.u0 + it.nunits;
   const int ls = it.dst_ls;
   const int p = it.p;

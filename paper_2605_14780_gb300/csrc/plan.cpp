@@ -931,7 +931,11 @@ void build_items(bc_plan* P) {
     }
   }
   auto table_emit = [&](std::vector<Item>& out, const Item& it, const bc_block& B, int vol) {
-    const int mode = table_mode(B, P->opts.unit_order);
+    int mode = table_mode(B, P->opts.unit_order);
+    // interpolation units hold kInterpChunk levels (smaller per-lane arrays
+    // in the interpolation kernels)
+    if (mode >= 2 && (it.kind == IK_INTERP || it.kind == IK_INTERP_PAIR))
+      mode = std::min(mode, kInterpChunk);
     emit_units(out, it, vol, B.nlevels, mode, mode < 2 ? per_table_flat_item : per_table_item);
   };
   std::vector<std::pair<int, std::vector<Item>>> per_sub(P->subs.size());
