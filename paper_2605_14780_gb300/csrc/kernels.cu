@@ -776,11 +776,6 @@ __device__ __forceinline__ void run_item(const Item& it, const Ptrs& P, const Ct
 
 static_assert(sizeof(Item) == 32 * 4, "an Item is loaded as one word per lane");
 
-__device__ __forceinline__ void load_item(Item* dst, const Item* src, int lane) {
-  reinterpret_cast<int*>(dst)[lane] = __ldg(reinterpret_cast<const int*>(src) + lane);
-  __syncwarp();
-}
-
 // Resident CTAs the register budget is set for: the structured family is
 // lean (48 registers, 40 warps per SM); the table families get 64.
 template <int FAM, int THREADS> struct Occ {
@@ -788,7 +783,10 @@ template <int FAM, int THREADS> struct Occ {
 #define BC_STRUCT_WARPS 40
 #endif
   static constexpr int kWarps = FAM == FAM_STRUCT ? BC_STRUCT_WARPS : 32;
-  static constexpr int kMinBlocks = (kWarps * 32) / THREADS > 0 ? (kWarps * 32) / THREADS : 1;
+  // resident CTAs asked of the register allocator: the warp budget in CTAs,
+  // at least 1 and at most 32 (the SM's CTA limit)
+  static constexpr int kBlocksRaw = (kWarps * 32) / THREADS;
+  static constexpr int kMinBlocks = kBlocksRaw < 1 ? 1 : (kBlocksRaw > 32 ? 32 : kBlocksRaw);
 };
 
 constexpr int kWordDst = offsetof(Item, dst_slot) / 4;
