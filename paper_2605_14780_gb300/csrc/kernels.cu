@@ -3,8 +3,8 @@
 //
 // Every launch works on a list of work items (bc_internal.h), one warp per
 // item: as a plain grid (warp w of CTA b takes item b * warps + w; used by
-// every launch form) or as a persistent grid whose warps claim items from an
-// atomic counter.  No warp ever waits on another; there is no CTA barrier.
+// every launch form) or as a resident grid whose warps walk the items with a
+// fixed stride.  No warp ever waits on another; there is no CTA barrier.
 //
 // The path is a sparse gather/scatter bounded by HBM bandwidth, so it runs on
 // the CUDA cores.  The lanes of a warp are laid over the item's (cell, level)
