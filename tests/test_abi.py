@@ -204,3 +204,13 @@ def test_rejects_zero_map_scale(lib):
     m = next(b for b in w["bcs"] if b["kind"] == "map")
     m["sign"] = (0, 2, 1)
     _expect(w, "BC_ERR_INVALID_ARG")
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the compiled library the binding raises."""
+    monkeypatch.setattr(bc, "_LIB", None)
+    monkeypatch.setattr(bc, "library_path", lambda: str(tmp_path / "libbcgb300.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        bc.load_library()
+    with pytest.raises(RuntimeError):
+        bc.plan_for_workload(synth.alg1_example())
