@@ -13,7 +13,10 @@
  * iterator): zero padding, tabulated constants (pure-function boundary),
  * index maps (halo copies, circular and symmetric maps, rotated maps of
  * Alg. 1), interpolation rows (user Itp, or cubed-sphere panel edges
- * generated on the GPU) and user CSR rows (Table III: F_NNZ/F_COL/F_DATA).
+ * generated on the GPU) and user CSR rows (Table III: F_NNZ/F_COL/F_DATA);
+ * block-edge averaging rows (Sync) overwrite data cells that several blocks
+ * store for one location, and bc_plan_create_pruned keeps only the ghost
+ * values a given stencil reads (Sec. IV-C).
  *
  * Memory model
  *   * Fields are caller-owned device memory.  Each (block, component) pair is
@@ -30,7 +33,11 @@
  *   * A plan owns its device tables; every host array passed to
  *     bc_plan_create is copied and may be freed afterwards.
  *   * bc_apply, bc_apply_form and bc_apply_adjoint allocate nothing, never
- *     synchronise the host, and only enqueue kernels on the given stream.
+ *     synchronise the host, and only enqueue kernels on the given stream
+ *     (the batched form forks them onto plan-owned streams and joins them
+ *     back, so it is graph-capturable).  One plan's applies must not run
+ *     concurrently on several streams: the fork/join events, and the
+ *     staging buffer of Sync rows, belong to the plan.
  *
  * Errors
  *   Every entry point returns a bc_status.  The message of the last error of
@@ -51,11 +58,12 @@ extern "C" {
 typedef enum bc_status {
   BC_OK = 0,
   BC_ERR_INVALID_ARG = 1,     /* malformed description or argument          */
-  BC_ERR_OVERLAP = 2,         /* two sub-matrices cover one ghost value      */
+  BC_ERR_OVERLAP = 2,         /* two sub-matrices cover one value            */
   BC_ERR_COLUMN_NOT_DATA = 3, /* a column is not a data cell (Sec. III-B)    */
   BC_ERR_UNCOVERED = 4,       /* strict cover: a ghost value has no row      */
   BC_ERR_HALO_TOO_WIDE = 5,   /* a map's ghost depth exceeds the data extent */
-  BC_ERR_OUT_OF_RANGE = 6,    /* a row is not a ghost cell of its block      */
+  BC_ERR_OUT_OF_RANGE = 6,    /* a row lies outside its region (ghost cells,
+                                 data cells for Sync rows)                  */
   BC_ERR_NOMEM = 7,           /* a host or device allocation failed          */
   BC_ERR_CUDA = 8,            /* a CUDA runtime call failed                  */
   BC_ERR_UNSUPPORTED = 9,     /* valid, but outside what this build handles  */
@@ -187,7 +195,9 @@ typedef struct bc_submatrix {
 /* Plan options; a zero-filled struct (or NULL) selects the defaults. */
 typedef struct bc_plan_opts {
   int32_t units_per_lane;  /* work per lane of one warp item: 8-level units
-                              (or 8 single-level values) (default 4)        */
+                              (or 8 single-level values) (default 4); small
+                              plans use smaller items so that they make
+                              about 16 items per SM                         */
   int32_t unit_order;      /* 0: auto (levels fastest when they are adjacent
                               in memory), 1: cells fastest, 2: levels
                               fastest                                       */
