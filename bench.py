@@ -21,6 +21,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -82,7 +83,9 @@ class ClockSampler:
     def __init__(self, device_index):
         self.idx = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # the samples file: BC_CLOCKS_DIR if set, else the system temp dir
+        out = os.environ.get("BC_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"bc_clocks_rank{device_index}.csv")
 
     def start(self):
         try:
