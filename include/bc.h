@@ -211,7 +211,12 @@ typedef struct bc_plan_opts {
                               per-value units; 0 (default): they copy
                               contiguous runs when the average run holds 16
                               values or more                                */
-  int32_t reserved[1];
+  int32_t host_only;       /* 1: build the plan on the host only, with no
+                              device work (no tables uploaded, no streams):
+                              bc_plan_stats and bc_plan_export_csr work,
+                              the apply entry points return
+                              BC_ERR_UNSUPPORTED; cubed-sphere geometry
+                              (generated on the GPU) is BC_ERR_UNSUPPORTED */
 } bc_plan_opts;
 
 typedef struct bc_plan bc_plan;

@@ -57,7 +57,7 @@ class BcPlanOpts(ctypes.Structure):
     _fields_ = [("units_per_lane", c_i32), ("unit_order", c_i32),
                 ("threads", c_i32), ("ctas_per_sm", c_i32),
                 ("strict_cover", c_i32), ("no_adjoint", c_i32),
-                ("no_runs", c_i32), ("reserved", c_i32 * 1)]
+                ("no_runs", c_i32), ("host_only", c_i32)]
 
 
 class BcStats(ctypes.Structure):

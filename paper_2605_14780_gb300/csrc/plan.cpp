@@ -1479,7 +1479,8 @@ bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
       o.threads != 512)
     return fail(BC_ERR_INVALID_ARG, "threads must be 32, 64, 128, 256 or 512");
   if (o.units_per_lane == 0) o.units_per_lane = 4;
-  if (o.units_per_lane < 1 || o.ctas_per_sm < 0 || o.unit_order < 0 || o.unit_order > 2)
+  if (o.units_per_lane < 1 || o.ctas_per_sm < 0 || o.unit_order < 0 || o.unit_order > 2 ||
+      o.host_only < 0 || o.host_only > 1)
     return fail(BC_ERR_INVALID_ARG, "bad work-item options");
   return BC_OK;
 }
@@ -1590,21 +1591,29 @@ bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_
         return fail(BC_ERR_UNCOVERED, "slot %d: %zu ghost cells have no row", slot, want - covered);
     }
   }
-  // device from here on
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return cuda_fail(e, "device attributes");
-  for (auto& a : P->aux)
-    if ((e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking)) != cudaSuccess)
-      return cuda_fail(e, "plan streams");
-  if ((e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming)) != cudaSuccess)
-    return cuda_fail(e, "plan events");
-  for (auto& ev : P->ev_join)
-    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+  if (P->opts.host_only) {
+    // no device work: the rows, the transpose and the work lists are built
+    // on the host for inspection (stats, explicit rows)
+    if (!cs_subs.empty())
+      return fail(BC_ERR_UNSUPPORTED, "cubed-sphere geometry needs the GPU (host_only plan)");
+    P->num_sms = 152;
+  } else {
+    // device from here on
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device attributes");
+    for (auto& a : P->aux)
+      if ((e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "plan streams");
+    if ((e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming)) != cudaSuccess)
       return cuda_fail(e, "plan events");
-  if ((st = run_cubed_sphere(P, cs_subs, cs_idx)) != BC_OK) return st;
+    for (auto& ev : P->ev_join)
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "plan events");
+    if ((st = run_cubed_sphere(P, cs_subs, cs_idx)) != BC_OK) return st;
+  }
   // explicit rows of interpolation sub-matrices, in sub-matrix order
   {
     ExplicitRows all;
@@ -1637,8 +1646,10 @@ bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_
   }
   if (!P->opts.no_adjoint) build_transpose(P);
   build_items(P);
-  if ((st = upload_tables(P)) != BC_OK) return st;
-  if ((st = upload_work(P)) != BC_OK) return st;
+  if (!P->opts.host_only) {
+    if ((st = upload_tables(P)) != BC_OK) return st;
+    if ((st = upload_work(P)) != BC_OK) return st;
+  }
   compute_stats(P);
   return BC_OK;
 }
@@ -1769,6 +1780,7 @@ int32_t bc_plan_nslots(const bc_plan* plan) { return plan ? plan->nslots : 0; }
 
 bc_status bc_apply_form(bc_plan* plan, void* const* slot_ptrs, int32_t form, void* stream) {
   if (!plan) return fail(BC_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->opts.host_only) return fail(BC_ERR_UNSUPPORTED, "host_only plan");
   if (!slot_ptrs && plan->nslots > 0) return fail(BC_ERR_INVALID_ARG, "slot_ptrs is NULL");
   return launch_forward(plan, slot_ptrs, form, static_cast<cudaStream_t>(stream));
 }
@@ -1779,6 +1791,7 @@ bc_status bc_apply(bc_plan* plan, void* const* slot_ptrs, void* stream) {
 
 bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs, void* stream) {
   if (!plan) return fail(BC_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->opts.host_only) return fail(BC_ERR_UNSUPPORTED, "host_only plan");
   if (!plan->has_adjoint) return fail(BC_ERR_UNSUPPORTED, "plan was built without the transpose");
   if (!slot_ptrs && plan->nslots > 0) return fail(BC_ERR_INVALID_ARG, "slot_ptrs is NULL");
   Ctx c = plan->ctx;
@@ -1807,6 +1820,7 @@ bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs, void* const* dev_
                         void* const* slot_ptrs, void* stream) {
   if (!plan || !host_ptrs || !dev_ptrs || !slot_ptrs)
     return fail(BC_ERR_INVALID_ARG, "NULL argument");
+  if (plan->opts.host_only) return fail(BC_ERR_UNSUPPORTED, "host_only plan");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // span of every slot, merged when host and device runs are both contiguous
   struct Run {
@@ -1840,6 +1854,7 @@ bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs, void* const* dev_
 }
 
 bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) {
+  if (plan && plan->opts.host_only) return fail(BC_ERR_UNSUPPORTED, "host_only plan");
   if (!plan || !slot_ptrs) return fail(BC_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int dev = 0, l2 = 0;

@@ -1,0 +1,102 @@
+"""The library's own plan construction on the CPU (host_only plans, no
+device work): its explicit rows of A and b, read back with
+bc_plan_export_csr, against the oracle's A and b for every workload type
+except the GPU-generated cubed-sphere geometry -- maps, CSR, Sync rows,
+scaled maps and pruned plans.  Pins the host half of the library (validation,
+index maps, ELL packing, box cutting) without a GPU."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle.operator import Operator, build_operator
+from paper_2605_14780_gb300 import bc, synth
+from pruning import live_mask
+
+HOST = {"host_only": 1}
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _library():
+    import os
+    if not os.path.exists(bc.library_path()):
+        from paper_2605_14780_gb300.build import build_library
+        build_library()
+
+
+def _plan_matrix(w, plan):
+    """(rows, A, b) of the plan in the oracle's numbering, level 0."""
+    ex = plan.export_csr()
+    op = build_operator(w, levels=[0])
+    lay = op.layout
+    slot_b, slot_c = [], []
+    for b, blk in enumerate(w["blocks"]):
+        for c in range(blk["ncomp"]):
+            slot_b.append(b)
+            slot_c.append(c)
+    slot_b, slot_c = np.array(slot_b), np.array(slot_c)
+    plane = lay.F.prod(axis=1)
+    rb = slot_b[ex["row_slot"]]
+    rows = lay.full_base[rb] + slot_c[ex["row_slot"]] * lay.L[rb] * plane[rb] + ex["row_off"]
+    cb = slot_b[ex["col_slot"]]
+    F, h, o = lay.F[cb], lay.h[cb], ex["col_off"]
+    ijk = np.stack([o % F[:, 0] - h[:, 0], (o // F[:, 0]) % F[:, 1] - h[:, 1],
+                    o // (F[:, 0] * F[:, 1]) - h[:, 2]], 1)
+    cols = lay.col(cb, slot_c[ex["col_slot"]], 0, ijk)
+    order = np.argsort(rows, kind="stable")
+    A = sp.csr_matrix((ex["val"], cols, ex["row_ptr"]), shape=(len(rows), lay.n_data))[order]
+    A.sum_duplicates()
+    A.sort_indices()
+    return rows[order], A, np.asarray(ex["rhs"])[order], op
+
+
+def _same(rows, A, b, op):
+    assert np.array_equal(rows, op.rows)
+    assert A.nnz == op.A.nnz
+    assert np.array_equal(A.indptr, op.A.indptr) and np.array_equal(A.indices, op.A.indices)
+    assert np.allclose(A.data, op.A.data, rtol=0, atol=1e-15)
+    assert np.allclose(b, op.b, rtol=0, atol=1e-15)
+
+
+CASES = [
+    ("alg1", lambda: synth.alg1_example(dtype="f64")),
+    ("hpcg_Z", lambda: synth.hpcg_block((7, 5, 6), "Z", seed=1)),
+    ("hpcg_P", lambda: synth.hpcg_block((7, 5, 6), "P", seed=1)),
+    ("hpcg_S", lambda: synth.hpcg_block((6, 7, 5), "S", seed=2)),
+    ("sync", lambda: synth.sync_grid(3, 2, 6, 2, 2, 2, "f64", seed=3)),
+    ("two_level", lambda: synth.two_level(14, 10, 2, 2, 2, "f64", seed=4)),
+] + [(f"batching{s}", (lambda s=s: synth.batching(
+    nblocks=12, side_lo=2, side_hi=20, lev_lo=1, lev_hi=6, h=1 + s % 3, seed=s, dtype="f32")))
+    for s in range(8)]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_host_plan_rows_equal_the_oracle(name, make):
+    w = make()
+    plan = bc.plan_for_workload(w, opts=HOST)
+    _same(*_plan_matrix(w, plan))
+    st = plan.stats()
+    op_all = build_operator(w)
+    assert st["ghost_values"] + st["sync_values"] == len(op_all.rows)
+
+
+@pytest.mark.parametrize("stencil", [bc.star_stencil(2, 1), bc.box_stencil(2, 1),
+                                     np.array([(1, 0, 0), (0, -2, 0)])])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_host_pruned_rows_are_the_live_rows(stencil, seed):
+    w = synth.batching(nblocks=10, side_lo=2, side_hi=16, lev_lo=1, lev_hi=4, h=2,
+                       seed=seed, dtype="f32")
+    plan = bc.plan_for_workload(w, opts=HOST, stencil=stencil)
+    rows, A, b, op = _plan_matrix(w, plan)
+    keep = live_mask(w, stencil)[op.rows]
+    _same(rows, A, b, Operator(op.layout, op.rows[keep], op.A[keep], op.b[keep]))
+
+
+def test_host_plans_refuse_device_work():
+    w = synth.alg1_example()
+    plan = bc.plan_for_workload(w, opts=HOST)
+    import ctypes
+    st = plan._lib.bc_apply_form(plan._h, ctypes.c_void_p(1), 0, None)
+    assert bc.STATUS.get(st) == "BC_ERR_UNSUPPORTED"
+    with pytest.raises(bc.BCError) as e:
+        bc.plan_for_workload(synth.tiny_cubed_sphere(), opts=HOST)
+    assert e.value.status == "BC_ERR_UNSUPPORTED"
