@@ -100,3 +100,22 @@ def test_host_plans_refuse_device_work():
     with pytest.raises(bc.BCError) as e:
         bc.plan_for_workload(synth.tiny_cubed_sphere(), opts=HOST)
     assert e.value.status == "BC_ERR_UNSUPPORTED"
+
+
+def test_algorithmic_bytes_closed_forms():
+    """The roofline numerator: bc_plan_stats' forward bytes per ghost value
+    are S for zero rows and 2S for copies (S = element size)."""
+    for variant, per_value in (("Z", 1), ("P", None)):
+        w = synth.hpcg_block((6, 5, 4), variant, seed=1, dtype="f64")
+        st = bc.plan_for_workload(w, opts=HOST).stats()
+        kinds = st["ghost_values_kind"]
+        S = 8
+        if per_value is not None:
+            assert st["bytes_fwd"] == per_value * S * st["ghost_values"]
+        else:
+            # zero rows write S, map rows read and write S each
+            assert st["bytes_fwd"] == S * kinds[0] + 2 * S * kinds[2]
+    w = synth.sync_grid(2, 1, 5, 1, 3, 1, "f32", seed=2)
+    st = bc.plan_for_workload(w, opts=HOST).stats()
+    # the Sync rows (1 row per copy of the 5 shared nodes) at 3 levels
+    assert st["sync_values"] == 2 * 5 * 3
