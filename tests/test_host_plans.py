@@ -119,3 +119,14 @@ def test_algorithmic_bytes_closed_forms():
     st = bc.plan_for_workload(w, opts=HOST).stats()
     # the Sync rows (1 row per copy of the 5 shared nodes) at 3 levels
     assert st["sync_values"] == 2 * 5 * 3
+
+
+@pytest.mark.parametrize("stencil", [bc.star_stencil(3, 1), bc.box_stencil(3, 1),
+                                     np.array([(0, 0, 0), (1, 1, 0), (0, -1, 1)])])
+@pytest.mark.parametrize("variant", ["Z", "P", "S"])
+def test_host_pruned_3d(stencil, variant):
+    w = synth.hpcg_block((6, 5, 4), variant, seed=3, dtype="f64")
+    plan = bc.plan_for_workload(w, opts=HOST, stencil=stencil)
+    rows, A, b, op = _plan_matrix(w, plan)
+    keep = live_mask(w, stencil)[op.rows]
+    _same(rows, A, b, Operator(op.layout, op.rows[keep], op.A[keep], op.b[keep]))
