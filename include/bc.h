@@ -40,6 +40,10 @@
  *     staging buffer of Sync rows, belong to the plan.
  *
  * Errors
+ *   For tests of the error paths, BC_FAULT_INJECT=alloc:<n> in the
+ *   environment makes the n-th device allocation of a bc_plan_create,
+ *   bc_plan_create_pruned or bc_plan_autotune call fail (BC_ERR_NOMEM); the
+ *   failure is made on the host, not on the GPU.
  *   Every entry point returns a bc_status.  The message of the last error of
  *   the calling thread is returned by bc_last_error().  Invalid descriptions
  *   are rejected by bc_plan_create before any device work.  Launch errors are

@@ -15,6 +15,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -44,6 +45,26 @@ bc_status fail(bc_status st, const char* fmt, ...) {
   va_end(ap);
   g_last_error = buf;
   return st;
+}
+
+// Fault injection on the host, for tests of the error paths: with
+// BC_FAULT_INJECT=alloc:<n> in the environment, the n-th device allocation
+// of a plan creation or autotune call (counting from 1) fails with
+// cudaErrorMemoryAllocation instead of allocating.  No GPU fault is made.
+thread_local int g_alloc_countdown = 0;  // 0: off
+
+void arm_fault_injection() {
+  g_alloc_countdown = 0;
+  const char* v = std::getenv("BC_FAULT_INJECT");
+  if (v && std::strncmp(v, "alloc:", 6) == 0) g_alloc_countdown = std::max(0, std::atoi(v + 6));
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (g_alloc_countdown > 0 && --g_alloc_countdown == 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
 }
 
 bc_status cuda_fail(cudaError_t e, const char* what) {
@@ -706,11 +727,11 @@ bc_status run_cubed_sphere(bc_plan* P, const std::vector<const bc_submatrix*>& c
     cudaFree(d_err);
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&d_cells, cells.size() * sizeof(int4))) != cudaSuccess ||
-      (e = cudaMalloc(&d_idx, nrow * sizeof(int4))) != cudaSuccess ||
-      (e = cudaMalloc(&d_w, nrow * kPMax * sizeof(double))) != cudaSuccess ||
-      (e = cudaMalloc(&d_m, nrow * 4 * sizeof(double))) != cudaSuccess ||
-      (e = cudaMalloc(&d_err, sizeof(unsigned))) != cudaSuccess) {
+  if ((e = dev_malloc(reinterpret_cast<void**>(&d_cells), cells.size() * sizeof(int4))) != cudaSuccess ||
+      (e = dev_malloc(reinterpret_cast<void**>(&d_idx), nrow * sizeof(int4))) != cudaSuccess ||
+      (e = dev_malloc(reinterpret_cast<void**>(&d_w), nrow * kPMax * sizeof(double))) != cudaSuccess ||
+      (e = dev_malloc(reinterpret_cast<void**>(&d_m), nrow * 4 * sizeof(double))) != cudaSuccess ||
+      (e = dev_malloc(reinterpret_cast<void**>(&d_err), sizeof(unsigned))) != cudaSuccess) {
     cleanup();
     return cuda_fail(e, "cubed-sphere geometry allocation");
   }
@@ -1314,7 +1335,7 @@ bc_status upload_tables(bc_plan* P) {
     put_dtype<float>(host, o_yw, Y.w);
     put_dtype<float>(host, o_ycw, Y.cw);
   }
-  cudaError_t e = cudaMalloc(&P->tables.base, host.size());
+  cudaError_t e = dev_malloc(&P->tables.base, host.size());
   if (e != cudaSuccess) {
     P->tables.base = nullptr;
     return cuda_fail(e, "device tables");
@@ -1381,7 +1402,7 @@ bc_status upload_work(bc_plan* P) {
   put_raw(host, o_r, P->runs);
   put_raw(host, o_a, P->adj_items);
   put_raw(host, o_z, P->adj_zero);
-  cudaError_t e = cudaMalloc(&P->work.base, host.size());
+  cudaError_t e = dev_malloc(&P->work.base, host.size());
   if (e != cudaSuccess) {
     P->work.base = nullptr;
     return cuda_fail(e, "device work list");
@@ -1729,6 +1750,7 @@ bc_status bc_plan_create(const bc_grid* grid, const bc_submatrix* subs, int32_t 
   if (!out) return fail(BC_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   g_last_error.clear();
+  arm_fault_injection();
   bc_plan* P = new (std::nothrow) bc_plan();
   if (!P) return fail(BC_ERR_NOMEM, "host allocation of the plan");
   bc_status st;
@@ -1752,6 +1774,7 @@ bc_status bc_plan_create_pruned(const bc_grid* grid, const bc_submatrix* subs, i
   *out = nullptr;
   g_last_error.clear();
   if (!offsets || noffsets <= 0) return fail(BC_ERR_INVALID_ARG, "empty stencil");
+  arm_fault_injection();
   if (!grid || !grid->blocks || grid->nblocks < 0)
     return fail(BC_ERR_INVALID_ARG, "bad grid");
   bc_plan* P = new (std::nothrow) bc_plan();
@@ -1856,13 +1879,14 @@ bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs, void* const* dev_
 bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) {
   if (plan && plan->opts.host_only) return fail(BC_ERR_UNSUPPORTED, "host_only plan");
   if (!plan || !slot_ptrs) return fail(BC_ERR_INVALID_ARG, "NULL argument");
+  arm_fault_injection();
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int dev = 0, l2 = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
   const size_t flush_bytes = std::max<size_t>((size_t)l2 * 2, size_t(64) << 20);
   void* flush = nullptr;
-  cudaError_t e = cudaMalloc(&flush, flush_bytes);
+  cudaError_t e = dev_malloc(&flush, flush_bytes);
   if (e != cudaSuccess) return cuda_fail(e, "autotune flush buffer");
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
