@@ -130,3 +130,45 @@ def test_host_pruned_3d(stencil, variant):
     rows, A, b, op = _plan_matrix(w, plan)
     keep = live_mask(w, stencil)[op.rows]
     _same(rows, A, b, Operator(op.layout, op.rows[keep], op.A[keep], op.b[keep]))
+
+
+def _random_host_workload(seed):
+    rng = np.random.default_rng(seed)
+    kind = seed % 4
+    dtype = ("f32", "f64")[int(rng.integers(2))]
+    if kind == 0:
+        h = int(rng.integers(1, 4))
+        return synth.batching(nblocks=int(rng.integers(1, 16)), side_lo=h,
+                              side_hi=int(rng.integers(h, 24)), lev_lo=1,
+                              lev_hi=int(rng.integers(1, 9)), h=h, seed=seed, dtype=dtype)
+    if kind == 1:
+        return synth.sync_grid(int(rng.integers(1, 4)), int(rng.integers(1, 4)),
+                               int(rng.integers(3, 8)), int(rng.integers(1, 3)),
+                               int(rng.integers(1, 4)), int(rng.integers(1, 3)), dtype, seed=seed)
+    if kind == 2:
+        return synth.two_level(2 * int(rng.integers(2, 9)), 2 * int(rng.integers(2, 8)),
+                               int(rng.integers(1, 3)), int(rng.integers(1, 4)),
+                               int(rng.integers(1, 3)), dtype, seed=seed)
+    n = tuple(int(x) for x in rng.integers(2, 7, size=3))
+    return synth.hpcg_block(n, "ZPS"[int(rng.integers(3))], seed=seed, dtype=dtype)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_host_plan_random_sweep(seed):
+    """40 seeded random workloads, plain and pruned for a random stencil."""
+    w = _random_host_workload(seed)
+    rng = np.random.default_rng(100 + seed)
+    plan = bc.plan_for_workload(w, opts=HOST)
+    _same(*_plan_matrix(w, plan))
+    ndim = 3 if w["blocks"][0]["n"][2] > 1 else 2
+    offs = rng.integers(-2, 3, size=(int(rng.integers(1, 6)), 3))
+    if ndim == 2:
+        offs[:, 2] = 0
+    plan = bc.plan_for_workload(w, opts=HOST, stencil=offs.astype(np.int32))
+    rows, A, b, op = _plan_matrix(w, plan)
+    keep = live_mask(w, offs)[op.rows]
+    # Sync rows (data cells) are kept by a pruned plan whatever the stencil
+    datarow = np.zeros(live_mask(w, offs).size, bool)
+    datarow[op.layout.data_rows()] = True
+    keep |= datarow[op.rows]
+    _same(rows, A, b, Operator(op.layout, op.rows[keep], op.A[keep], op.b[keep]))
