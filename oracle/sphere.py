@@ -26,6 +26,17 @@ throughout the project:
   sphere.  The ghost value is ``u_own = M u_nb`` with ``u_nb`` the
   interpolated components of ``Q`` and ``M_ij = e_own_i . e_Q^j``, ``e^j``
   being ``Q``'s dual basis at the ghost point (interpolate, then rotate).
+* Reconstruction-and-quadrature rows (``quad = nq``, the finite-volume form
+  of Sec. II-B written as ``Itp = Agg . Recons``, Sec. III-B): data values
+  are cell averages in the panel's angle coordinates.  An edge ghost cell is
+  the average of ``nq x nq`` Gauss-Legendre points of the cell in its own
+  panel's angles (weights ``w_a w_b / 4``); each point is carried to ``Q``
+  and evaluated there by the tensor-product polynomial of degree ``p - 1``
+  per axis whose averages over a ``p x p`` patch of ``Q``'s data cells are
+  the data values.  The patch is chosen once per ghost from its centre:
+  normal cells from ``clamp(r' - (p/2 - 1), 0, N - p)``, along cells from
+  ``clamp(floor(t + 1e-9) - (p/2 - 1), 0, N - p)``.  Vector pairs are
+  rotated by ``M`` at every point before the average.
 """
 from __future__ import annotations
 
@@ -180,7 +191,11 @@ def rotation(P, Q, a, b, aq, bq):
 
 
 def cubed_sphere_rows(bc, blocks, diagnostics=None):
-    """Row sets (one per panel) of the panel-edge interpolation."""
+    """Row sets (one per panel) of the panel-edge interpolation; with a
+    ``quad`` entry, the reconstruction-and-quadrature rows of
+    :func:`cubed_sphere_quad_rows`."""
+    if bc.get("quad"):
+        return cubed_sphere_quad_rows(bc, blocks)
     panels = list(bc["panels"])
     N, h, p = int(bc["N"]), int(bc["h"]), int(bc["p"])
     if p > N:
@@ -246,6 +261,144 @@ def cubed_sphere_rows(bc, blocks, diagnostics=None):
                                         "s": g["s"], "rq": g["rq"], "t": g["t"],
                                         "snapped": snapped, "start": start,
                                         "w": w})
+        from .rows import concat_rowsets
+        out.append(concat_rowsets(sets))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Reconstruction at quadrature points (Sec. II-B, the HOPE example; Sec. III-B,
+# Itp = Agg . Recons)
+# ----------------------------------------------------------------------------
+def patch_starts(rq, t, N, p):
+    """First node of the ``p x p`` reconstruction patch on the neighbour panel
+    along its normal axis (from the depth row ``rq``) and along the edge (from
+    the along position ``t`` of the ghost centre)."""
+    sn = np.clip(np.asarray(rq, np.int64) - (p // 2 - 1), 0, N - p)
+    st = np.clip(np.floor(np.asarray(t) + SNAP_TOL).astype(np.int64) - (p // 2 - 1), 0, N - p)
+    return sn, st
+
+
+def average_reconstruction_weights(x, p):
+    """Weights ``c_k(x)`` (n, p) of the polynomial of degree ``p - 1`` whose
+    averages over the unit cells ``[k - 1/2, k + 1/2]``, ``k = 0..p-1``, are
+    given: ``P(x) = sum_k c_k(x) avg_k``.
+
+    Written from the primitive ``Phi(x) = int_{-1/2}^x P``: ``Phi`` is known
+    at the cell edges ``e_m = m - 1/2`` (``Phi(e_m) = sum_{k<m} avg_k``), is
+    the degree-``p`` Lagrange interpolant ``sum_m Phi(e_m) l_m(x)`` through
+    them, and ``P = Phi'``, so ``c_k = sum_{m > k} l_m'``."""
+    x = np.asarray(x, np.float64).reshape(-1)
+    e = np.arange(p + 1, dtype=np.float64) - 0.5
+    dl = np.zeros((len(x), p + 1))
+    for m in range(p + 1):
+        for j in range(p + 1):
+            if j == m:
+                continue
+            term = np.full(len(x), 1.0 / (e[m] - e[j]))
+            for i in range(p + 1):
+                if i != m and i != j:
+                    term *= (x - e[i]) / (e[m] - e[i])
+            dl[:, m] += term
+    c = np.zeros((len(x), p))
+    for k in range(p):
+        for m in range(k + 1, p + 1):
+            c[:, k] += dl[:, m]
+    return c
+
+
+def quad_strip(P, N, h, p, nq, d, side, vector):
+    """Weights of the ghost cells of one edge strip.
+
+    Each ghost cell is averaged over its ``nq x nq`` Gauss-Legendre points in
+    the panel's own angles (``Agg``: weights ``w_a w_b / 4``); each point is
+    carried to the neighbour panel ``Q`` and reconstructed there from the
+    cell averages of the ``p x p`` data cells of the ghost's patch, one
+    :func:`average_reconstruction_weights` factor per axis (``Recons``).  Returns the strip geometry, the patch
+    starts and ``W[R, p, p]`` (scalar rows, normal node first) and, for a
+    vector pair, ``V[R, 2, 2, p, p]`` with ``V[:, i, j]`` the weights of
+    neighbour component ``j`` in own component ``i`` (rotation applied at
+    every point)."""
+    g = strip_geometry(P, N, h, d, side)
+    Q, dq = g["Q"], g["dq"]
+    sn, st = patch_starts(g["rq"], g["t"], N, p)
+    xg, wg = np.polynomial.legendre.leggauss(nq)
+    delta = math.pi / (2 * N)
+    R = len(g["cells"])
+    W = np.zeros((R, p, p))
+    V = np.zeros((R, 2, 2, p, p)) if vector else None
+    for ia in range(nq):
+        for ib in range(nq):
+            a = g["a"] + xg[ia] * delta / 2
+            b = g["b"] + xg[ib] * delta / 2
+            Qc, aq, bq = locate(sphere_point(P, a, b))
+            if np.any(Qc != Q):
+                raise OracleError("a quadrature point leaves the neighbour panel")
+            f = [(aq + math.pi / 4) / delta - 0.5, (bq + math.pi / 4) / delta - 0.5]
+            Ln = average_reconstruction_weights(f[dq] - sn, p)
+            Lt = average_reconstruction_weights(f[1 - dq] - st, p)
+            omega = wg[ia] * wg[ib] / 4.0
+            T = omega * Ln[:, :, None] * Lt[:, None, :]
+            W += T
+            if vector:
+                M = rotation(P, Q, a, b, aq, bq)
+                for i in range(2):
+                    for j in range(2):
+                        V[:, i, j] += M[:, i, j, None, None] * T
+    return g, sn, st, W, V
+
+
+def cubed_sphere_quad_rows(bc, blocks):
+    """Row sets (one per panel) of the reconstruction-and-quadrature rows:
+    every edge ghost reads the ``p x p`` patch of neighbour data cells
+    (entries normal node major, along node minor)."""
+    panels = list(bc["panels"])
+    N, h, p, nq = int(bc["N"]), int(bc["h"]), int(bc["p"]), int(bc["quad"])
+    if p < 2 or p > N:
+        raise OracleError("reconstruction order must be in 2..N")
+    if nq < 1:
+        raise OracleError("at least one quadrature point per axis")
+    scal = list(bc["scalar_comps"])
+    vpair = bc.get("vector_pair")
+    for pb in panels:
+        blk = blocks[pb]
+        if tuple(blk["n"][:2]) != (N, N) or tuple(blk["h"][:2]) != (h, h):
+            raise OracleError("panel block shape does not match N, h")
+    kn, kt = np.meshgrid(np.arange(p), np.arange(p), indexing="ij")
+    kn, kt = kn.reshape(-1), kt.reshape(-1)
+    out = []
+    for P in range(6):
+        sets = []
+        for d in (0, 1):
+            for side in (0, 1):
+                g, sn, st, W, V = quad_strip(P, N, h, p, nq, d, side, bool(vpair))
+                R = len(g["cells"])
+                src = np.zeros((R, p * p, 3), np.int64)
+                src[:, :, g["dq"]] = sn[:, None] + kn[None, :]
+                src[:, :, 1 - g["dq"]] = st[:, None] + kt[None, :]
+                e_row = np.repeat(np.arange(R), p * p)
+                e_src = src.reshape(-1, 3)
+                Qb = panels[g["Q"]]
+                for c in scal:
+                    rs = empty_rowset(panels[P], np.full(R, c), g["cells"])
+                    rs["e_row"] = e_row.copy()
+                    rs["e_b"] = np.full(len(e_row), Qb, np.int64)
+                    rs["e_c"] = np.full(len(e_row), c, np.int64)
+                    rs["e_ijk"] = e_src.copy()
+                    rs["e_w"] = W.reshape(-1).copy()
+                    sets.append(rs)
+                if vpair:
+                    cu, cv = vpair
+                    for i, c_row in enumerate((cu, cv)):
+                        rs = empty_rowset(panels[P], np.full(R, c_row), g["cells"])
+                        rs["e_row"] = np.concatenate([e_row, e_row])
+                        rs["e_b"] = np.full(2 * len(e_row), Qb, np.int64)
+                        rs["e_c"] = np.concatenate([np.full(len(e_row), cu, np.int64),
+                                                    np.full(len(e_row), cv, np.int64)])
+                        rs["e_ijk"] = np.concatenate([e_src, e_src])
+                        rs["e_w"] = np.concatenate([V[:, i, 0].reshape(-1),
+                                                    V[:, i, 1].reshape(-1)])
+                        sets.append(rs)
         from .rows import concat_rowsets
         out.append(concat_rowsets(sets))
     return out

@@ -379,8 +379,13 @@ def _corner_csr(N, h, panel, corner, ncomp, scalar_comps, vector_pair):
 
 
 def cubed_sphere(N=32, h=2, p=4, nlevels=1, fields=("scalar",), dtype="f64",
-                 seed=1):
+                 seed=1, quad=None):
     """Six equiangular gnomonic panels of N x N cells with halo h.
+
+    ``quad = nq`` asks for reconstruction-and-quadrature edge rows (each
+    edge ghost the average of nq x nq Gauss points, each point reconstructed
+    from a p x p patch of the neighbour panel, Sec. II-B) instead of the 1-D
+    Lagrange rows along the neighbour row.
 
     ``fields`` is ``("scalar",)`` (one component uniform in [-1, 1]) or
     ``("h", "u", "v")`` (a smooth height field of 1e4 +- 100 m built from a
@@ -424,13 +429,16 @@ def cubed_sphere(N=32, h=2, p=4, nlevels=1, fields=("scalar",), dtype="f64",
     bcs = [{"kind": "cubed_sphere_edges", "panels": list(range(6)), "N": N,
             "h": h, "p": p, "scalar_comps": scalar_comps,
             "vector_pair": vpair}]
+    if quad:
+        bcs[0]["quad"] = int(quad)
     for pnl in range(6):
         for corner in range(4):
             bcs.append(_corner_csr(N, h, pnl, corner, ncomp, scalar_comps,
                                    vpair))
-    return {"name": f"cubed_sphere{N}_h{h}_p{p}_L{nlevels}", "dtype": dtype,
+    qtag = f"_q{int(quad)}" if quad else ""
+    return {"name": f"cubed_sphere{N}_h{h}_p{p}{qtag}_L{nlevels}", "dtype": dtype,
             "blocks": blocks, "bcs": bcs, "fields": arrs,
-            "sphere": {"N": N, "h": h, "p": p, "fields": tuple(fields)}}
+            "sphere": {"N": N, "h": h, "p": p, "quad": quad, "fields": tuple(fields)}}
 
 
 # ----------------------------------------------------------------------------
@@ -449,6 +457,13 @@ def swe_cubed_sphere(N=384, nlevels=32, seed=3):
 def adjoint_cubed_sphere(N=768, nlevels=32, seed=5):
     """6 x 768^2, h = 3, (h, u, v) x 32 levels FP32, p = 6."""
     return cubed_sphere(N, 3, 6, nlevels, ("h", "u", "v"), "f32", seed)
+
+
+def hope_cubed_sphere(N=384, nlevels=32, seed=3):
+    """6 x 384^2, h = 3, (h, u, v) x 32 levels FP32; every edge ghost the
+    2 x 2 Gauss-point average of a 4 x 4 tensor-product reconstruction on the
+    neighbour panel (16 entries per scalar row, 32 per vector row)."""
+    return cubed_sphere(N, 3, 4, nlevels, ("h", "u", "v"), "f32", seed, quad=2)
 
 
 def cotangent_like(w, seed):
