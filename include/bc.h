@@ -88,8 +88,10 @@ typedef enum bc_kind {
 } bc_kind;
 
 typedef enum bc_geometry {
-  BC_GEOM_USER = 0,        /* interpolation tables given by the caller     */
-  BC_GEOM_CUBED_SPHERE = 1 /* generated on the GPU for gnomonic panels     */
+  BC_GEOM_USER = 0,              /* interpolation tables given by the caller */
+  BC_GEOM_CUBED_SPHERE = 1,      /* generated on the GPU for gnomonic panels */
+  BC_GEOM_CUBED_SPHERE_QUAD = 2  /* cell averages by reconstruction and
+                                    Gauss quadrature, generated on the host */
 } bc_geometry;
 
 /* Execution forms of the forward apply. */
@@ -142,11 +144,29 @@ typedef struct bc_grid {
  *              must be an edge ghost (exactly one index out of range), and
  *              the GPU computes the neighbour panel, depth row, stencil and
  *              Lagrange weights in FP64 at plan creation.
+ *              geometry = BC_GEOM_CUBED_SPHERE_QUAD: the finite-volume form
+ *              of the user-defined interpolation (Sec. II-B; Itp = Agg .
+ *              Recons, Sec. III-B).  Data values are cell averages in the
+ *              panel's angle coordinates; the ghost value is the average of
+ *              nquad x nquad Gauss-Legendre points of the ghost cell, each
+ *              point evaluated on the neighbour panel by the tensor-product
+ *              polynomial of degree p - 1 per axis whose averages over a
+ *              p x p patch of data cells are the data (2 <= p <= 8,
+ *              p <= N, 1 <= nquad <= 8).  The patch is chosen from the ghost
+ *              centre (normal cells clamp(r - (p/2 - 1), 0, N - p) from its
+ *              depth row r, along cells clamp(floor(t + 1e-9) - (p/2 - 1), 0,
+ *              N - p) from its along position t).  Panel rules as for
+ *              BC_GEOM_CUBED_SPHERE.  The rows are built in FP64 at plan
+ *              creation and executed as user CSR rows (p^2 entries, 2 p^2
+ *              for a vector pair); plan statistics and export count them as
+ *              BC_CSR, and later error messages number sub-matrices after
+ *              this expansion (one or two CSR sub-matrices each).
  *              rot_comp = {cu, cv} (or {-1, -1}) names two listed components
  *              that form a covariant vector: for them the interpolated pair
  *              is multiplied by the 2x2 matrix M (user: itp_rot[vol*4],
- *              row-major; cubed sphere: generated) -- interpolate, then
- *              rotate.  All other listed components use the plain row.
+ *              row-major; cubed sphere: generated, for the quadrature form at
+ *              every point before the average) -- interpolate, then rotate.
+ *              All other listed components use the plain row.
  * BC_CSR    -- row r = (listed comp r / volume, box cell r % volume) has the
  *              entries row_ptr[r] .. row_ptr[r+1]-1 with columns
  *              (col_block, col_comp, col_ijk[3]) and values val; rhs[r] (or
@@ -194,6 +214,8 @@ typedef struct bc_submatrix {
   const int32_t* col_ijk;
   const double* val;
   const double* rhs;
+  /* BC_INTERP with BC_GEOM_CUBED_SPHERE_QUAD: Gauss points per axis */
+  int32_t nquad;
 } bc_submatrix;
 
 /* Plan options; a zero-filled struct (or NULL) selects the defaults. */

@@ -50,7 +50,8 @@ class BcSubmatrix(ctypes.Structure):
                 ("itp_src_block", P_i32), ("itp_start", P_i32),
                 ("itp_axis", P_i32), ("itp_w", P_dbl), ("itp_rot", P_dbl),
                 ("row_ptr", P_i64), ("col_block", P_i32), ("col_comp", P_i32),
-                ("col_ijk", P_i32), ("val", P_dbl), ("rhs", P_dbl)]
+                ("col_ijk", P_i32), ("val", P_dbl), ("rhs", P_dbl),
+                ("nquad", c_i32)]
 
 
 class BcPlanOpts(ctypes.Structure):
@@ -198,6 +199,7 @@ class Plan:
             m.geometry = s.get("geometry", 0)
             m.rot_comp[:] = list(s.get("rot_comp", (-1, -1)))
             m.cs_panels[:] = list(s.get("cs_panels", (0, 0, 0, 0, 0, 0)))
+            m.nquad = s.get("nquad", 0)
             for key, dt, ct in (("itp_src_block", np.int32, c_i32),
                                 ("itp_start", np.int32, c_i32),
                                 ("itp_axis", np.int32, c_i32),

@@ -30,6 +30,7 @@
 #include "../../include/bc.h"
 #include "bc_internal.h"
 #include "prune.h"
+#include "quadrature.h"
 
 using namespace bcg;
 
@@ -1743,6 +1744,16 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
 // ============================================================================
 // C ABI
 // ============================================================================
+// Reconstruction-and-quadrature cubed-sphere sub-matrices become user CSR
+// sub-matrices before anything else sees the list.
+bc_status lower_subs(const bc_grid* grid, const bc_submatrix* subs, int32_t nsubs,
+                     SubStore& low) {
+  if (!has_cs_quadrature(subs, nsubs)) return BC_OK;
+  std::string msg;
+  const bc_status st = lower_cs_quadrature(grid, subs, nsubs, low, msg);
+  return st == BC_OK ? st : fail(st, "%s", msg.c_str());
+}
+
 extern "C" {
 
 bc_status bc_plan_create(const bc_grid* grid, const bc_submatrix* subs, int32_t nsubs,
@@ -1755,7 +1766,13 @@ bc_status bc_plan_create(const bc_grid* grid, const bc_submatrix* subs, int32_t 
   if (!P) return fail(BC_ERR_NOMEM, "host allocation of the plan");
   bc_status st;
   try {
-    st = plan_create_impl(grid, subs, nsubs, opts, P);
+    SubStore low;
+    st = lower_subs(grid, subs, nsubs, low);
+    if (st == BC_OK) {
+      const bool lowered = has_cs_quadrature(subs, nsubs);
+      st = plan_create_impl(grid, lowered ? low.subs.data() : subs,
+                            lowered ? (int32_t)low.subs.size() : nsubs, opts, P);
+    }
   } catch (const std::bad_alloc&) {
     st = fail(BC_ERR_NOMEM, "host allocation while building the plan");
   }
@@ -1781,7 +1798,16 @@ bc_status bc_plan_create_pruned(const bc_grid* grid, const bc_submatrix* subs, i
   if (!P) return fail(BC_ERR_NOMEM, "host allocation of the plan");
   bc_status st;
   try {
-    PrunedSubs pr;
+    SubStore low, pr;
+    st = lower_subs(grid, subs, nsubs, low);
+    if (st != BC_OK) {
+      delete P;
+      return st;
+    }
+    if (has_cs_quadrature(subs, nsubs)) {
+      subs = low.subs.data();
+      nsubs = (int32_t)low.subs.size();
+    }
     st = prune_submatrices(grid, subs, nsubs, offsets, noffsets, pr);
     if (st != BC_OK)
       st = fail(st, "bad sub-matrix list");

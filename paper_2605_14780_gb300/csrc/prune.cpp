@@ -86,7 +86,7 @@ std::vector<Box> live_boxes(const bc_block& B, const Box& box, const int32_t* of
 }  // namespace
 
 bc_status prune_submatrices(const bc_grid* grid, const bc_submatrix* subs, int nsubs,
-                            const int32_t* offsets, int noffsets, PrunedSubs& out) {
+                            const int32_t* offsets, int noffsets, SubStore& out) {
   if (!grid || !grid->blocks || grid->nblocks < 0 || nsubs < 0 || (nsubs > 0 && !subs))
     return BC_ERR_INVALID_ARG;
   if (noffsets <= 0 || !offsets) return BC_ERR_INVALID_ARG;

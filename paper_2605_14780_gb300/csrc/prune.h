@@ -10,9 +10,10 @@
 
 namespace bcg {
 
-// The pieces and the payload slices they point into (deque elements keep
-// their addresses while more are added).
-struct PrunedSubs {
+// A sub-matrix list built on the host (pruned pieces, lowered rows) and the
+// payload arrays it points into (deque elements keep their addresses while
+// more are added).
+struct SubStore {
   std::vector<bc_submatrix> subs;
   std::deque<std::vector<double>> dbl;
   std::deque<std::vector<int32_t>> i32;
@@ -24,6 +25,6 @@ struct PrunedSubs {
 // noffsets stencil offsets o = offsets[3n .. 3n+2]); sub-matrices with no
 // live cell are dropped, and ones the plan would reject pass unchanged.
 bc_status prune_submatrices(const bc_grid* grid, const bc_submatrix* subs, int nsubs,
-                            const int32_t* offsets, int noffsets, PrunedSubs& out);
+                            const int32_t* offsets, int noffsets, SubStore& out);
 
 }  // namespace bcg

@@ -26,7 +26,7 @@ import itertools
 import numpy as np
 
 BC_ZERO, BC_CONST, BC_MAP, BC_INTERP, BC_CSR, BC_SYNC = range(6)
-BC_GEOM_USER, BC_GEOM_CUBED_SPHERE = 0, 1
+BC_GEOM_USER, BC_GEOM_CUBED_SPHERE, BC_GEOM_CUBED_SPHERE_QUAD = 0, 1, 2
 
 
 def contiguous_block(blk):
@@ -186,9 +186,12 @@ def cubed_sphere_submatrices(bc, blocks):
                 lo = [0, 0, 0]
                 hi = [N, N, 1]
                 lo[d], hi[d] = (-h, 0) if side == 0 else (N, N + h)
-                out.append(_sub(BC_INTERP, panels[P], lo, hi, comps, p=p,
-                                geometry=BC_GEOM_CUBED_SPHERE, rot_comp=rot,
-                                cs_panels=tuple(panels)))
+                if bc.get("quad"):
+                    geom = {"geometry": BC_GEOM_CUBED_SPHERE_QUAD, "nquad": int(bc["quad"])}
+                else:
+                    geom = {"geometry": BC_GEOM_CUBED_SPHERE}
+                out.append(_sub(BC_INTERP, panels[P], lo, hi, comps, p=p, rot_comp=rot,
+                                cs_panels=tuple(panels), **geom))
     return out
 
 

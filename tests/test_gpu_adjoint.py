@@ -68,6 +68,8 @@ def _level_mask(w, levels):
     lambda: synth.cubed_sphere(9, 3, 6, 3, ("h", "u", "v"), "f64", seed=4),
     lambda: synth.cubed_sphere(16, 3, 6, 10, ("h", "u", "v"), "f32", seed=4),
     lambda: synth.two_level(20, 14, 2, nlevels=3, ncomp=2, dtype="f64", seed=5),
+    lambda: synth.cubed_sphere(9, 3, 4, 3, ("h", "u", "v"), "f64", seed=4, quad=2),
+    lambda: synth.cubed_sphere(14, 2, 6, 6, ("h", "u", "v"), "f32", seed=4, quad=3),
 ])
 def test_adjoint_vs_oracle(make):
     w = make()
@@ -80,6 +82,7 @@ def test_adjoint_vs_oracle(make):
     lambda: synth.batching(nblocks=30, side_lo=3, side_hi=30, lev_lo=1,
                            lev_hi=20, h=2, seed=3, dtype="f32"),
     lambda: synth.cubed_sphere(10, 3, 6, 9, ("h", "u", "v"), "f64", seed=4),
+    lambda: synth.cubed_sphere(8, 2, 4, 7, ("h", "u", "v"), "f32", seed=4, quad=2),
 ])
 def test_adjoint_level_innermost(make):
     import torch

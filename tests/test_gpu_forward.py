@@ -98,6 +98,29 @@ def test_cubed_sphere_vector(N, L, dtype):
     compare(w, out)
 
 
+@pytest.mark.parametrize("N,h,p,nq,fields", [(6, 2, 4, 2, ("h", "u", "v")), (9, 3, 3, 1, ("scalar",)),
+                                              (10, 3, 6, 3, ("h", "u", "v")),
+                                              (12, 2, 8, 4, ("scalar",)), (7, 1, 2, 5, ("h", "u", "v"))])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("layout", ["outermost", "innermost"])
+def test_cubed_sphere_quadrature(N, h, p, nq, fields, dtype, layout):
+    """Reconstruction-and-quadrature edge rows (user CSR rows of p^2 and
+    2 p^2 entries, built on the host) against the oracle."""
+    from gpu_util import to_device_innermost
+    w = synth.cubed_sphere(N, h, p, 5, fields, dtype, seed=N + p, quad=nq)
+    ts = to_device_innermost(w["fields"]) if layout == "innermost" else None
+    _, out = run(w, tensors=ts)
+    compare(w, out)
+
+
+def test_hope_cubed_sphere_sampled():
+    """6 x 384^2, h = 3, (h, u, v) x 32 levels FP32, 4 x 4 reconstruction at
+    2 x 2 Gauss points: levels 0, 17 and 31 compared with the oracle."""
+    w = synth.hope_cubed_sphere()
+    _, out = run(w)
+    compare(w, out, levels=[0, 17, 31])
+
+
 def test_tiny_cubed_sphere_full():
     """6 x 32^2, h = 2, p = 4, FP64 scalar, corners by CSR."""
     w = synth.tiny_cubed_sphere()

@@ -172,3 +172,67 @@ def test_host_plan_random_sweep(seed):
     datarow[op.layout.data_rows()] = True
     keep |= datarow[op.rows]
     _same(rows, A, b, Operator(op.layout, op.rows[keep], op.A[keep], op.b[keep]))
+
+
+# -- reconstruction-and-quadrature cubed-sphere rows (built on the host) --------
+def _close(rows, A, b, op, atol=1e-13):
+    """Same rows and sparsity; weights within FP64 rounding of the oracle
+    (the rows are sums of products computed in another order)."""
+    assert np.array_equal(rows, op.rows)
+    assert np.array_equal(A.indptr, op.A.indptr) and np.array_equal(A.indices, op.A.indices)
+    assert np.allclose(A.data, op.A.data, rtol=0, atol=atol)
+    assert np.allclose(b, op.b, rtol=0, atol=1e-15)
+
+
+QUAD_CASES = [(8, 2, 4, 2, ("h", "u", "v"), "f64"), (9, 3, 3, 1, ("scalar",), "f32"),
+              (10, 1, 6, 3, ("h", "u", "v"), "f32"), (12, 3, 8, 4, ("scalar",), "f64"),
+              (6, 2, 2, 8, ("h", "u", "v"), "f64"), (7, 3, 5, 2, ("h", "u", "v"), "f64"),
+              (5, 1, 2, 5, ("scalar",), "f64"), (6, 2, 3, 6, ("h", "u", "v"), "f32"),
+              (8, 1, 7, 7, ("scalar",), "f64")]
+
+
+@pytest.mark.parametrize("N,h,p,nq,fields,dtype", QUAD_CASES)
+def test_host_quadrature_rows_equal_the_oracle(N, h, p, nq, fields, dtype):
+    w = synth.cubed_sphere(N, h, p, 2, fields, dtype, seed=5, quad=nq)
+    plan = bc.plan_for_workload(w, opts=HOST)
+    _close(*_plan_matrix(w, plan))
+    st = plan.stats()
+    # every edge ghost is a CSR row of p^2 (scalar) or 2 p^2 (vector) entries
+    assert st["ghost_values_kind"][3] == 0
+    assert st["ghost_values"] == len(build_operator(w).rows)
+
+
+@pytest.mark.parametrize("stencil", [bc.star_stencil(2, 1), bc.box_stencil(2, 2)])
+def test_host_quadrature_pruned(stencil):
+    w = synth.cubed_sphere(9, 3, 4, 1, ("h", "u", "v"), "f64", seed=6, quad=2)
+    plan = bc.plan_for_workload(w, opts=HOST, stencil=stencil)
+    rows, A, b, op = _plan_matrix(w, plan)
+    keep = live_mask(w, stencil)[op.rows]
+    _close(rows, A, b, Operator(op.layout, op.rows[keep], op.A[keep], op.b[keep]))
+
+
+def _quad_subs(**change):
+    from paper_2605_14780_gb300 import specs
+    w = synth.cubed_sphere(6, 2, 4, 1, ("h", "u", "v"), "f64", seed=7, quad=2)
+    subs = specs.submatrices(w)
+    subs[0].update(change)
+    return w, subs
+
+
+@pytest.mark.parametrize("change,status", [
+    ({"nquad": 0}, "BC_ERR_UNSUPPORTED"), ({"nquad": 9}, "BC_ERR_UNSUPPORTED"),
+    ({"p": 1}, "BC_ERR_UNSUPPORTED"), ({"p": 9}, "BC_ERR_UNSUPPORTED"),
+    ({"p": 7}, "BC_ERR_INVALID_ARG"),                       # wider than N = 6
+    ({"rot_comp": (1, 1)}, "BC_ERR_INVALID_ARG"), ({"rot_comp": (1, -1)}, "BC_ERR_INVALID_ARG"),
+    ({"comps": [0, 1, 2, 3]}, "BC_ERR_INVALID_ARG"),
+    ({"cs_panels": (0, 1, 2, 3, 4, 6)}, "BC_ERR_INVALID_ARG"),
+    ({"lo": (-2, -1, 0)}, "BC_ERR_GEOMETRY"),               # a corner ghost in the box
+    ({"lo": (-2, 0, 0), "hi": (1, 6, 1)}, "BC_ERR_GEOMETRY"),  # a data cell in the box
+])
+def test_host_quadrature_rejects(change, status):
+    w, subs = _quad_subs(**change)
+    from paper_2605_14780_gb300 import specs
+    blocks = [specs.contiguous_block(b) for b in w["blocks"]]
+    with pytest.raises(bc.BCError) as e:
+        bc.Plan(blocks, subs, w["dtype"], opts=HOST)
+    assert e.value.status == status, e.value
