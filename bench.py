@@ -570,6 +570,16 @@ def run_ours(args, rank, world, local):
             others[name] = measure_forward(ww, device, stream, min(args.steps, 300), 5,
                                            adjoint=adj)
             del ww
+        # reconstruction-and-quadrature rows (user CSR rows of 16 / 32
+        # entries); recorded as an error entry rather than losing the line
+        # if this newer path fails
+        try:
+            ww = make_workload_named("hope")
+            others["hope_cubed_sphere_6x384_L32_p4_q2"] = measure_forward(
+                ww, device, stream, min(args.steps, 300), 5, adjoint=True)
+            del ww
+        except Exception as e:  # noqa: BLE001
+            others["hope_cubed_sphere_6x384_L32_p4_q2"] = {"error": f"{type(e).__name__}: {e}"}
         result["other_workloads"] = others
         # dead-ghost elimination (Sec. IV-C): the same workloads, plans cut
         # to the ghost values a following stencil reads

@@ -71,3 +71,43 @@ def test_random_adjoint(seed):
     scale = np.abs(y).copy()
     scale[op.layout.data_rows()] += abs(op.A).T @ np.abs(y[op.rows])
     assert np.all(np.abs(got - ref) <= TOL[w["dtype"]] * scale)
+
+
+def _random_quadrature(seed):
+    rng = np.random.default_rng(seed)
+    N = int(rng.integers(4, 15))
+    h = int(rng.integers(1, min(3, N // 2) + 1))
+    p = int(rng.integers(2, min(8, N) + 1))
+    nq = int(rng.integers(1, 5))
+    fields = (("scalar",), ("h", "u", "v"))[int(rng.integers(2))]
+    dtype = ("f32", "f64")[int(rng.integers(2))]
+    return synth.cubed_sphere(N, h, p, int(rng.integers(1, 7)), fields, dtype, seed=seed,
+                              quad=nq)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_quadrature(seed):
+    """Reconstruction-and-quadrature rows of random order, Gauss points,
+    halo, levels, layout, launch form and item shape: forward and adjoint."""
+    import torch
+    w = _random_quadrature(300 + seed)
+    rng = np.random.default_rng(2000 + seed)
+    layout = int(rng.integers(2))
+    form = [bc.BC_FORM_BATCHED, bc.BC_FORM_TYPEWIDE, bc.BC_FORM_PER_BC][int(rng.integers(3))]
+    opts = {"units_per_lane": int(rng.choice([1, 2, 4, 8])),
+            "threads": int(rng.choice([64, 128, 256]))}
+    dev = to_device_innermost if layout else to_device
+    ts = dev(w["fields"])
+    plan, _ = run(w, form=form, opts=opts, tensors=ts)
+    compare(w, [t.cpu().numpy() for t in ts])
+    cot = synth.cotangent_like(w, 700 + seed)
+    cs = dev(cot)
+    plan.adjoint(bc.slot_table(cs))
+    torch.cuda.synchronize()
+    got = flat([c.cpu().numpy() for c in cs]).astype(np.float64)
+    op = build_operator(w)
+    ref = flat(apply_adjoint(op, cot))
+    y = flat(cot).astype(np.float64)
+    scale = np.abs(y).copy()
+    scale[op.layout.data_rows()] += abs(op.A).T @ np.abs(y[op.rows])
+    assert np.all(np.abs(got - ref) <= TOL[w["dtype"]] * scale)

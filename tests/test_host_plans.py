@@ -236,3 +236,24 @@ def test_host_quadrature_rejects(change, status):
     with pytest.raises(bc.BCError) as e:
         bc.Plan(blocks, subs, w["dtype"], opts=HOST)
     assert e.value.status == status, e.value
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_host_quadrature_random(seed):
+    """Random order, Gauss points, halo and fields; plain and pruned to a
+    random stencil."""
+    rng = np.random.default_rng(900 + seed)
+    N = int(rng.integers(4, 15))
+    h = int(rng.integers(1, min(3, N // 2) + 1))
+    p = int(rng.integers(2, min(8, N) + 1))
+    fields = (("scalar",), ("h", "u", "v"))[int(rng.integers(2))]
+    w = synth.cubed_sphere(N, h, p, int(rng.integers(1, 4)), fields,
+                           ("f32", "f64")[int(rng.integers(2))], seed=seed,
+                           quad=int(rng.integers(1, 9)))
+    _close(*_plan_matrix(w, bc.plan_for_workload(w, opts=HOST)))
+    offs = rng.integers(-2, 3, size=(int(rng.integers(1, 6)), 3))
+    offs[:, 2] = 0
+    rows, A, b, op = _plan_matrix(w, bc.plan_for_workload(w, opts=HOST,
+                                                          stencil=offs.astype(np.int32)))
+    keep = live_mask(w, offs)[op.rows]
+    _close(rows, A, b, Operator(op.layout, op.rows[keep], op.A[keep], op.b[keep]))
