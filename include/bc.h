@@ -160,7 +160,10 @@ typedef struct bc_grid {
  *              creation and executed as user CSR rows (p^2 entries, 2 p^2
  *              for a vector pair); plan statistics and export count them as
  *              BC_CSR, and later error messages number sub-matrices after
- *              this expansion (one or two CSR sub-matrices each).
+ *              this expansion (one or two CSR sub-matrices each).  Errors:
+ *              bad p or nquad BC_ERR_UNSUPPORTED (p > N: INVALID_ARG), a
+ *              box beyond the panel's full region BC_ERR_OUT_OF_RANGE, a box
+ *              cell that is not an edge ghost BC_ERR_GEOMETRY.
  *              rot_comp = {cu, cv} (or {-1, -1}) names two listed components
  *              that form a covariant vector: for them the interpolated pair
  *              is multiplied by the 2x2 matrix M (user: itp_rot[vol*4],

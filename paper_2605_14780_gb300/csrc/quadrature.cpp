@@ -318,6 +318,10 @@ bc_status lower_cs_quadrature(const bc_grid* grid, const bc_submatrix* subs, int
     for (int d = 0; d < 3; ++d) vol *= std::max(0, m.hi[d] - m.lo[d]);
     if (vol <= 0) return bad(msg, BC_ERR_INVALID_ARG, si, "empty box");
     if (m.lo[2] != 0 || m.hi[2] != 1) return bad(msg, BC_ERR_GEOMETRY, si, "panels are 2-D");
+    const int hh = grid->blocks[m.block].h[0];
+    for (int d = 0; d < 2; ++d)
+      if (m.lo[d] < -hh || m.hi[d] > N + hh)
+        return bad(msg, BC_ERR_OUT_OF_RANGE, si, "box outside the panel's full region");
     double xg[kQuadMax], wg[kQuadMax];
     gauss_legendre(m.nquad, xg, wg);
     const int p = m.p, pp = p * p;

@@ -228,6 +228,8 @@ def _quad_subs(**change):
     ({"cs_panels": (0, 1, 2, 3, 4, 6)}, "BC_ERR_INVALID_ARG"),
     ({"lo": (-2, -1, 0)}, "BC_ERR_GEOMETRY"),               # a corner ghost in the box
     ({"lo": (-2, 0, 0), "hi": (1, 6, 1)}, "BC_ERR_GEOMETRY"),  # a data cell in the box
+    ({"lo": (-3, 0, 0)}, "BC_ERR_OUT_OF_RANGE"),            # deeper than h = 2
+    ({"hi": (0, 1 << 20, 1)}, "BC_ERR_OUT_OF_RANGE"),
 ])
 def test_host_quadrature_rejects(change, status):
     w, subs = _quad_subs(**change)
