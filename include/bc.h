@@ -244,8 +244,10 @@ typedef struct bc_plan_opts {
                               device work (no tables uploaded, no streams):
                               bc_plan_stats and bc_plan_export_csr work,
                               the apply entry points return
-                              BC_ERR_UNSUPPORTED; cubed-sphere geometry
-                              (generated on the GPU) is BC_ERR_UNSUPPORTED */
+                              BC_ERR_UNSUPPORTED; BC_GEOM_CUBED_SPHERE
+                              geometry (generated on the GPU) is
+                              BC_ERR_UNSUPPORTED, the host-built
+                              BC_GEOM_CUBED_SPHERE_QUAD rows are not      */
 } bc_plan_opts;
 
 typedef struct bc_plan bc_plan;
