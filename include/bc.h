@@ -355,6 +355,35 @@ bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs,
 bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs,
                            void* stream);
 
+/*
+ * Pure-function boundary b_i = udf(i) (Sec. III-B) evaluated on the device
+ * by the caller: *values receives the device address of the constant table
+ * b of BC_CONST sub-matrix `sub` (its index in the list given to
+ * bc_plan_create) and *count its length, ncomps * volume values in the
+ * plan's dtype, in the order of bc_submatrix.values (component-major, box
+ * cells with axis 0 fastest; one value per cell, used at every level).
+ * Values the caller writes there (its own kernels or copies, ordered before
+ * an apply on the stream that applies) are the b of every later apply and
+ * graph replay: a time-dependent boundary needs no new plan.  The address
+ * is valid until bc_plan_destroy.  bc_plan_export_csr keeps reporting the
+ * values given at creation.  Errors: BC_ERR_INVALID_ARG (NULL argument, no
+ * such sub-matrix, not BC_CONST), BC_ERR_UNSUPPORTED (host-only plan, or a
+ * plan from bc_plan_create_pruned, whose tables hold the live cells only).
+ */
+bc_status bc_plan_const_values(bc_plan* plan, int32_t sub, void** values,
+                               int64_t* count);
+
+/*
+ * Copy `count` values (bc_plan_const_values' count, in the plan's dtype)
+ * from `values` (device memory, e.g. the caller's udf evaluated on the
+ * device) into the constant table of BC_CONST sub-matrix `sub`, ordered on
+ * `stream` (cudaStream_t; a stream capture records it as a copy node).
+ * Errors as bc_plan_const_values; BC_ERR_INVALID_ARG for NULL values;
+ * BC_ERR_CUDA if the copy cannot be issued.
+ */
+bc_status bc_plan_set_const(bc_plan* plan, int32_t sub, const void* values,
+                            void* stream);
+
 /* Fill *out with the plan's counters. */
 bc_status bc_plan_stats(const bc_plan* plan, bc_stats* out);
 

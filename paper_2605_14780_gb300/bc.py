@@ -88,6 +88,8 @@ SIGNATURES = {
     "bc_apply_adjoint": (c_i32, [c_vp, c_vp, c_vp]),
     "bc_apply_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "bc_plan_autotune": (c_i32, [c_vp, c_vp, c_vp]),
+    "bc_plan_const_values": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), P_i64]),
+    "bc_plan_set_const": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
     "bc_plan_stats": (c_i32, [c_vp, ctypes.POINTER(BcStats)]),
     "bc_plan_export_csr": (c_i32, [c_vp, P_i64, P_i64, P_i32, P_i64, P_i64,
                                    P_i32, P_i64, P_dbl, P_dbl]),
@@ -273,6 +275,35 @@ class Plan:
                 "col_slot": cs[:E], "col_off": co[:E], "val": va[:E],
                 "rhs": rh[:R]}
 
+    def const_table(self, sub):
+        """(device address, length) of the constant table b of BC_CONST
+        sub-matrix ``sub``: component-major, box cells axis 0 fastest, in
+        the plan's dtype."""
+        ptr, n = c_vp(), c_i64()
+        _check(self._lib.bc_plan_const_values(self._h, int(sub), ctypes.byref(ptr),
+                                              ctypes.byref(n)))
+        return ptr.value or 0, n.value
+
+    def const_values(self, sub):
+        """The constant table of ``sub`` as a 1-D torch tensor sharing the
+        plan's memory (through ``__cuda_array_interface__``), for b = udf(i)
+        computed on the device; writes to it change every later apply."""
+        import torch
+        ptr, n = self.const_table(sub)
+        view = _DeviceArray(ptr, n, "<f4" if self.dtype == "f32" else "<f8", owner=self)
+        return torch.as_tensor(view, device="cuda")
+
+    def set_const(self, sub, values, stream=None):
+        """Copy the device tensor ``values`` (the plan's dtype, the table's
+        length, contiguous) into the constant table of ``sub`` on
+        ``stream``."""
+        _, n = self.const_table(sub)
+        want = "torch.float32" if self.dtype == "f32" else "torch.float64"
+        if str(values.dtype) != want or values.numel() != n or not values.is_contiguous():
+            raise ValueError(f"need a contiguous {want} tensor of {n} values")
+        _check(self._lib.bc_plan_set_const(self._h, int(sub), c_vp(values.data_ptr()),
+                                           _stream_handle(stream)))
+
     # -- execution -----------------------------------------------------------
     def apply(self, slot_table, form=BC_FORM_BATCHED, stream=None):
         """Forward apply; ``slot_table`` is a device int64 tensor of slot
@@ -293,6 +324,17 @@ class Plan:
     def autotune(self, slot_table, stream=None):
         _check(self._lib.bc_plan_autotune(self._h, c_vp(slot_table.data_ptr()),
                                           _stream_handle(stream)))
+
+
+class _DeviceArray:
+    """A 1-D device buffer described by ``__cuda_array_interface__`` (keeps
+    its plan alive while a view of it exists)."""
+
+    def __init__(self, ptr, n, typestr, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 2,
+                                         "strides": None}
 
 
 def slot_pointers(tensors):

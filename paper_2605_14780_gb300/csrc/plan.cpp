@@ -125,6 +125,10 @@ struct bc_plan {
   std::vector<int32_t> slot_ls;
   int nslots = 0;
   std::vector<Sub> subs;
+  // index into subs of every sub-matrix of the caller's list (-1: Sync rows,
+  // or none); meaningless for pruned plans
+  std::vector<int> sub_of_input;
+  bool pruned = false;
   ExplicitRows rows;  // level 0, in sub-matrix order
   // host tables (FP64 copies)
   std::vector<int4> itp_idx;
@@ -1543,6 +1547,8 @@ bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_
   std::vector<int> reg, syn;
   for (int si = 0; si < nsubs; ++si) (subs[si].kind == BC_SYNC ? syn : reg).push_back(si);
   P->subs.resize(reg.size());
+  P->sub_of_input.assign(nsubs, -1);
+  for (size_t t = 0; t < reg.size(); ++t) P->sub_of_input[reg[t]] = (int)t;
   // pass 1: validation, coverage, tables of every kind but cubed-sphere rows
   for (size_t t = 0; t < reg.size(); ++t) {
     const int si = reg[t];
@@ -1772,6 +1778,14 @@ bc_status bc_plan_create(const bc_grid* grid, const bc_submatrix* subs, int32_t 
       const bool lowered = has_cs_quadrature(subs, nsubs);
       st = plan_create_impl(grid, lowered ? low.subs.data() : subs,
                             lowered ? (int32_t)low.subs.size() : nsubs, opts, P);
+      if (st == BC_OK && lowered) {
+        // back to the caller's numbering (a lowered sub-matrix maps to the
+        // first of its CSR pieces)
+        std::vector<int> user((size_t)nsubs, -1);
+        for (size_t li = 0; li < low.origin.size(); ++li)
+          if (user[(size_t)low.origin[li]] < 0) user[(size_t)low.origin[li]] = P->sub_of_input[li];
+        P->sub_of_input.swap(user);
+      }
     }
   } catch (const std::bad_alloc&) {
     st = fail(BC_ERR_NOMEM, "host allocation while building the plan");
@@ -1808,6 +1822,7 @@ bc_status bc_plan_create_pruned(const bc_grid* grid, const bc_submatrix* subs, i
       subs = low.subs.data();
       nsubs = (int32_t)low.subs.size();
     }
+    P->pruned = true;
     st = prune_submatrices(grid, subs, nsubs, offsets, noffsets, pr);
     if (st != BC_OK)
       st = fail(st, "bad sub-matrix list");
@@ -1977,6 +1992,34 @@ bc_status bc_plan_stats(const bc_plan* plan, bc_stats* out) {
   if (!plan || !out) return fail(BC_ERR_INVALID_ARG, "NULL argument");
   *out = plan->stats;
   return BC_OK;
+}
+
+bc_status bc_plan_const_values(bc_plan* plan, int32_t sub, void** values, int64_t* count) {
+  if (!plan || !values || !count) return fail(BC_ERR_INVALID_ARG, "NULL argument");
+  *values = nullptr;
+  *count = 0;
+  if (plan->opts.host_only) return fail(BC_ERR_UNSUPPORTED, "host-only plan: no device tables");
+  if (plan->pruned)
+    return fail(BC_ERR_UNSUPPORTED, "pruned plan: constant tables hold the live cells only");
+  if (sub < 0 || sub >= (int32_t)plan->sub_of_input.size() || plan->sub_of_input[sub] < 0)
+    return fail(BC_ERR_INVALID_ARG, "sub-matrix %d: no such ghost sub-matrix", sub);
+  const Sub& s = plan->subs[plan->sub_of_input[sub]];
+  if (s.kind != BC_CONST) return fail(BC_ERR_INVALID_ARG, "sub-matrix %d is not BC_CONST", sub);
+  *values = static_cast<char*>(const_cast<void*>(plan->ctx.const_val)) +
+            (size_t)s.table * (size_t)plan->esize;
+  *count = (int64_t)s.comps.size() * s.vol;
+  return BC_OK;
+}
+
+bc_status bc_plan_set_const(bc_plan* plan, int32_t sub, const void* values, void* stream) {
+  void* dst = nullptr;
+  int64_t n = 0;
+  const bc_status st = bc_plan_const_values(plan, sub, &dst, &n);
+  if (st != BC_OK) return st;
+  if (!values) return fail(BC_ERR_INVALID_ARG, "values is NULL");
+  const cudaError_t e = cudaMemcpyAsync(dst, values, (size_t)n * (size_t)plan->esize,
+                                        cudaMemcpyDefault, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? BC_OK : cuda_fail(e, "constant table copy");
 }
 
 bc_status bc_plan_export_csr(const bc_plan* plan, int64_t* nrows, int64_t* nnz, int32_t* row_slot,

@@ -15,6 +15,7 @@ namespace bcg {
 // more are added).
 struct SubStore {
   std::vector<bc_submatrix> subs;
+  std::vector<int> origin;  // index of each sub-matrix in the list it came from
   std::deque<std::vector<double>> dbl;
   std::deque<std::vector<int32_t>> i32;
   std::deque<std::vector<int64_t>> i64;

@@ -264,6 +264,7 @@ bc_status ghost_row(int P, int N, int p, int nq, bool vec, int i, int j, const d
 bc_status lower_cs_quadrature(const bc_grid* grid, const bc_submatrix* subs, int nsubs,
                               SubStore& out, std::string& msg) {
   out.subs.clear();
+  out.origin.clear();
   if (!grid || !grid->blocks || grid->nblocks < 0 || nsubs < 0 || (nsubs > 0 && !subs)) {
     msg = "bad grid or sub-matrix list";
     return BC_ERR_INVALID_ARG;
@@ -272,6 +273,7 @@ bc_status lower_cs_quadrature(const bc_grid* grid, const bc_submatrix* subs, int
     const bc_submatrix& m = subs[si];
     if (!(m.kind == BC_INTERP && m.geometry == BC_GEOM_CUBED_SPHERE_QUAD)) {
       out.subs.push_back(m);
+      out.origin.push_back(si);
       continue;
     }
     // panels: six equal N x N 2-D blocks, the box's block one of them
@@ -391,6 +393,7 @@ bc_status lower_cs_quadrature(const bc_grid* grid, const bc_submatrix* subs, int
       s.val = cv.data();
       s.rhs = nullptr;
       out.subs.push_back(s);
+      out.origin.push_back(si);
     }
   }
   return BC_OK;

@@ -100,6 +100,35 @@ def uniform_fields(blocks, dtype, lo, hi, seed):
     return fields
 
 
+def dirichlet_udf(i, j, comp, t):
+    """A pure function of the ghost cell, the component and the time, with
+    dyadic coefficients so that FP32 and FP64 evaluations are exact: the
+    boundary values of a time-dependent Dirichlet problem."""
+    return 0.25 * i - 0.5 * j + 0.125 * t + comp
+
+
+def dirichlet_block(nx=20, ny=14, h=2, nlevels=3, ncomp=2, dtype="f64", t=0.0, seed=21):
+    """One 2-D block whose ghost boxes (four faces, four corners) are
+    pure-function boundaries ``b = dirichlet_udf(i, j, comp, t)`` (BC_CONST
+    tables, Sec. III-B), data uniform in [-1, 1]."""
+    blk = block2d(nx, ny, h, nlevels, ncomp)
+    fields = uniform_fields([blk], dtype, -1.0, 1.0, seed)
+    comps = list(range(ncomp))
+    bcs = []
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            if a == 0 and b == 0:
+                continue
+            lo = [-h if a < 0 else (nx if a > 0 else 0), -h if b < 0 else (ny if b > 0 else 0), 0]
+            hi = [0 if a < 0 else (nx + h if a > 0 else nx), 0 if b < 0 else (ny + h if b > 0 else ny), 1]
+            jj, ii = np.meshgrid(np.arange(lo[1], hi[1]), np.arange(lo[0], hi[0]), indexing="ij")
+            vals = np.concatenate([dirichlet_udf(ii.ravel(), jj.ravel(), c, t) for c in comps])
+            bcs.append({"kind": "const", "block": 0, "lo": tuple(lo), "hi": tuple(hi),
+                        "comps": comps, "values": vals.astype(np.float64)})
+    return {"name": f"dirichlet{nx}x{ny}_h{h}_t{t}", "dtype": dtype, "blocks": [blk],
+            "bcs": bcs, "fields": fields}
+
+
 def total_full_values(w):
     return sum(int(np.prod(full_shape(b))) for b in w["blocks"])
 

@@ -121,6 +121,77 @@ def test_hope_cubed_sphere_sampled():
     compare(w, out, levels=[0, 17, 31])
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("layout", ["outermost", "innermost"])
+def test_pure_function_boundary_evaluated_on_the_device(dtype, layout):
+    """b = udf(i, t) written into the plan's constant tables by device code
+    between graph replays of one captured apply; every step against the
+    oracle's constant rows at that time, bit-exact."""
+    import torch
+    w = synth.dirichlet_block(dtype=dtype, t=0.0)
+    ts = to_device_innermost(w["fields"]) if layout == "innermost" else to_device(w["fields"])
+    plan = bc.plan_for_workload(w, ts)
+    table = bc.slot_table(ts)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan.apply(table, stream=stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        plan.apply(table, stream=stream)
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    for t in (1.0, 2.5, -3.0):
+        with torch.cuda.stream(stream):
+            for k, d in enumerate(w["bcs"]):
+                jj, ii = torch.meshgrid(torch.arange(d["lo"][1], d["hi"][1], device="cuda"),
+                                        torch.arange(d["lo"][0], d["hi"][0], device="cuda"),
+                                        indexing="ij")
+                i, j = ii.reshape(-1).double(), jj.reshape(-1).double()
+                vals = torch.cat([synth.dirichlet_udf(i, j, c, t) for c in d["comps"]])
+                vals = vals.to(tdt).contiguous()
+                plan.set_const(k, vals, stream=stream)
+                stream.synchronize()   # vals is a temporary of this loop
+            g.replay()
+        torch.cuda.synchronize()
+        compare(synth.dirichlet_block(dtype=dtype, t=t), [x.cpu().numpy() for x in ts])
+
+
+def test_const_table_view():
+    """The constant table as a torch view (CUDA array interface): a write
+    through it is the b of the next apply."""
+    import torch
+    w = synth.dirichlet_block(dtype="f32", t=0.0)
+    ts = to_device(w["fields"])
+    plan = bc.plan_for_workload(w, ts)
+    try:
+        views = [plan.const_values(k) for k in range(len(w["bcs"]))]
+    except (TypeError, RuntimeError) as e:
+        pytest.skip(f"this torch does not import CUDA array interface views: {e}")
+    wt = synth.dirichlet_block(dtype="f32", t=4.0)
+    for v, d in zip(views, wt["bcs"]):
+        v.copy_(torch.from_numpy(d["values"].astype(np.float32)).cuda())
+    plan.apply(bc.slot_table(ts))
+    torch.cuda.synchronize()
+    compare(wt, [x.cpu().numpy() for x in ts])
+
+
+def test_const_values_errors():
+    w = synth.dirichlet_block()
+    plan = bc.plan_for_workload(w, to_device(w["fields"]))
+    for bad in (-1, len(w["bcs"])):
+        with pytest.raises(bc.BCError) as e:
+            plan.const_values(bad)
+        assert e.value.status == "BC_ERR_INVALID_ARG"
+    a = synth.alg1_example()
+    with pytest.raises(bc.BCError) as e:
+        bc.plan_for_workload(a, to_device(a["fields"])).const_values(0)
+    assert e.value.status == "BC_ERR_INVALID_ARG"          # not a constant
+    with pytest.raises(bc.BCError) as e:
+        bc.plan_for_workload(w, to_device(w["fields"]),
+                             stencil=bc.star_stencil(2, 1)).const_values(0)
+    assert e.value.status == "BC_ERR_UNSUPPORTED"          # pruned
+
+
 def test_tiny_cubed_sphere_full():
     """6 x 32^2, h = 2, p = 4, FP64 scalar, corners by CSR."""
     w = synth.tiny_cubed_sphere()

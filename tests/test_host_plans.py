@@ -259,3 +259,12 @@ def test_host_quadrature_random(seed):
                                                           stencil=offs.astype(np.int32)))
     keep = live_mask(w, offs)[op.rows]
     _close(rows, A, b, Operator(op.layout, op.rows[keep], op.A[keep], op.b[keep]))
+
+
+def test_host_plan_has_no_constant_tables():
+    w = synth.dirichlet_block(t=1.5)
+    plan = bc.plan_for_workload(w, opts=HOST)
+    _same(*_plan_matrix(w, plan))
+    with pytest.raises(bc.BCError) as e:
+        plan.const_values(0)
+    assert e.value.status == "BC_ERR_UNSUPPORTED"
