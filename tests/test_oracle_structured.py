@@ -273,3 +273,21 @@ def test_pin_catches_planted_fmap_error(monkeypatch):
     y = apply(build_operator(w), w["fields"])[0][0, 0]
     data = synth.data_view(w["fields"][0], w["blocks"][0])[0, 0].astype(np.float64)
     assert not np.array_equal(y, _pad_reference(data, "S"))
+
+
+def test_pure_function_boundary_closed_form():
+    """Constant rows (A = 0, b = udf(i), Sec. III-B): every ghost value of the
+    Dirichlet block equals the function at its cell, every data value is
+    untouched."""
+    t = 1.75
+    w = synth.dirichlet_block(nx=9, ny=7, h=2, nlevels=2, ncomp=2, t=t)
+    y = apply(build_operator(w), w["fields"])[0]
+    C, L, _, F1, F0 = y.shape
+    h = 2
+    jj, ii = np.meshgrid(np.arange(F1) - h, np.arange(F0) - h, indexing="ij")
+    ghost = (ii < 0) | (ii >= 9) | (jj < 0) | (jj >= 7)
+    for c in range(C):
+        for lev in range(L):
+            want = 0.25 * ii - 0.5 * jj + 0.125 * t + c
+            assert np.array_equal(y[c, lev, 0][ghost], want[ghost])
+            assert np.array_equal(y[c, lev, 0][~ghost], w["fields"][0][c, lev, 0][~ghost])
