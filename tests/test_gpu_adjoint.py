@@ -106,6 +106,28 @@ def test_adjoint_full_768_sampled():
     _check_adjoint(w, cot, out, levels=[2, 29])
 
 
+def test_sync_grid_bench_size_sampled():
+    """The bench's block-edge averaging workload (8 x 8 blocks of 129^2
+    nodes, h = 3, 3 components x 32 levels FP32): forward and adjoint,
+    levels 0 and 31 against the oracle."""
+    from gpu_util import compare
+    w = synth.sync_grid(8, 8, 129, 3, 32, 3, "f32", seed=12)
+    _, out = run(w)
+    compare(w, out, levels=[0, 31])
+    cot = synth.cotangent_like(w, 12)
+    _, adj = _adjoint_gpu(w, cot)
+    _check_adjoint(w, cot, adj, levels=[0, 31])
+
+
+def test_hope_adjoint_sampled():
+    """The 6 x 384^2 reconstruction-and-quadrature workload's adjoint (as the
+    bench times it), levels 3 and 30 against the oracle's transpose."""
+    w = synth.hope_cubed_sphere()
+    cot = synth.cotangent_like(w, 31)
+    _, out = _adjoint_gpu(w, cot)
+    _check_adjoint(w, cot, out, levels=[3, 30])
+
+
 def _fd_setup(N=10, L=3):
     w = synth.cubed_sphere(N, 3, 6, L, ("h", "u", "v"), "f64", seed=6)
     for a in w["fields"]:

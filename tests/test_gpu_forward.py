@@ -81,6 +81,29 @@ def test_batching_full_512():
     compare(w, out)
 
 
+def test_batching_full_512_bench_configuration():
+    """The 512-block workload as the bench times it: levels innermost,
+    default plan options, the batched apply captured in a CUDA graph on a
+    side stream and replayed; every ghost value against the oracle."""
+    import torch
+    w = synth.batching()
+    ts = to_device_innermost(w["fields"])
+    plan = bc.plan_for_workload(w, ts)
+    table = bc.slot_table(ts)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan.apply(table, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.apply(table, stream=s)
+    for t, a in zip(ts, w["fields"]):
+        t.copy_(torch.from_numpy(a))         # back to the input, ghosts NaN
+    g.replay()
+    torch.cuda.synchronize()
+    compare(w, [t.cpu().numpy() for t in ts])
+
+
 @pytest.mark.parametrize("N,h,p", [(5, 2, 4), (8, 3, 6), (16, 2, 4), (7, 1, 2),
                                    (9, 3, 8)])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
