@@ -44,7 +44,7 @@ import math
 
 import numpy as np
 
-from .rows import OracleError, empty_rowset
+from .rows import OracleError, concat_rowsets, empty_rowset
 
 # outward normal, x axis and y axis of each panel
 PANEL_FRAME = np.array([
@@ -261,7 +261,6 @@ def cubed_sphere_rows(bc, blocks, diagnostics=None):
                                         "s": g["s"], "rq": g["rq"], "t": g["t"],
                                         "snapped": snapped, "start": start,
                                         "w": w})
-        from .rows import concat_rowsets
         out.append(concat_rowsets(sets))
     return out
 
@@ -399,6 +398,5 @@ def cubed_sphere_quad_rows(bc, blocks):
                         rs["e_w"] = np.concatenate([V[:, i, 0].reshape(-1),
                                                     V[:, i, 1].reshape(-1)])
                         sets.append(rs)
-        from .rows import concat_rowsets
         out.append(concat_rowsets(sets))
     return out
