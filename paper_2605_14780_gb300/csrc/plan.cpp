@@ -1814,21 +1814,19 @@ bc_status bc_plan_create_pruned(const bc_grid* grid, const bc_submatrix* subs, i
   try {
     SubStore low, pr;
     st = lower_subs(grid, subs, nsubs, low);
-    if (st != BC_OK) {
-      delete P;
-      return st;
+    if (st == BC_OK) {
+      if (has_cs_quadrature(subs, nsubs)) {
+        subs = low.subs.data();
+        nsubs = (int32_t)low.subs.size();
+      }
+      P->pruned = true;
+      st = prune_submatrices(grid, subs, nsubs, offsets, noffsets, pr);
+      if (st != BC_OK)
+        st = fail(st, "bad sub-matrix list");
+      else
+        st = plan_create_impl(grid, pr.subs.data(), (int32_t)pr.subs.size(), opts, P, offsets,
+                              noffsets);
     }
-    if (has_cs_quadrature(subs, nsubs)) {
-      subs = low.subs.data();
-      nsubs = (int32_t)low.subs.size();
-    }
-    P->pruned = true;
-    st = prune_submatrices(grid, subs, nsubs, offsets, noffsets, pr);
-    if (st != BC_OK)
-      st = fail(st, "bad sub-matrix list");
-    else
-      st = plan_create_impl(grid, pr.subs.data(), (int32_t)pr.subs.size(), opts, P, offsets,
-                            noffsets);
   } catch (const std::bad_alloc&) {
     st = fail(BC_ERR_NOMEM, "host allocation while building the plan");
   }
