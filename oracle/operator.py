@@ -61,7 +61,7 @@ class Operator:
         self.b = b
 
 
-def _validate(layout, rs):
+def _validate(layout, rs, ghost_columns=False):
     b = rs["b"]
     nr = len(rs["c"])
     bb = np.full(nr, b)
@@ -78,7 +78,10 @@ def _validate(layout, rs):
     if len(rs["e_b"]):
         if np.any((rs["e_b"] < 0) | (rs["e_b"] >= layout.nb)):
             raise OracleError("column block out of range")
-        if not np.all(layout.in_data(rs["e_b"], rs["e_ijk"])):
+        inside = layout.in_data(rs["e_b"], rs["e_ijk"])
+        if ghost_columns and not rs.get("data_rows"):
+            inside = layout.in_full(rs["e_b"], rs["e_ijk"])
+        if not np.all(inside):
             raise OracleError("a column is not a data cell")
         if np.any((rs["e_c"] < 0) | (rs["e_c"] >= layout.C[rs["e_b"]])):
             raise OracleError("column component out of range")
@@ -93,13 +96,21 @@ def build_operator(w, levels=None, diagnostics=None):
 
     ``levels`` restricts the rows to those levels (for sampled checks of
     large workloads); the columns always span the whole data region.
+
+    With ``w["ghost_sweeps"] = k > 0`` user CSR rows may also read covered
+    ghost values (the iterative form HOPE(I) of Sec. II-B): every ghost
+    starts at zero and all covered rows are evaluated together ``k`` times
+    (Jacobi sweeps), which is the single matrix of HOPE(M),
+    ``A = sum_{m<k} G^m D``, ``b = sum_{m<k} G^m b_0`` with ``D`` the entries
+    on data values and ``G`` those on ghost values.
     """
     layout = Layout(w["blocks"])
     sets = rowsets(w, diagnostics)
+    sweeps = int(w.get("ghost_sweeps") or 0)
     # merge per block, check disjointness at one level
     per_block = {}
     for rs in sets:
-        _validate(layout, rs)
+        _validate(layout, rs, ghost_columns=sweeps > 0)
         per_block.setdefault(rs["b"], []).append(rs)
     for b, lst in per_block.items():
         rs = concat_rowsets(lst) if len(lst) > 1 else lst[0]
@@ -117,7 +128,14 @@ def build_operator(w, levels=None, diagnostics=None):
             R.append(layout.row(np.full(nr, b), rs["c"], lev, rs["ijk"]))
             Bv.append(rs["rhs"])
             if len(rs["e_row"]):
-                Cc.append(layout.col(rs["e_b"], rs["e_c"], lev, rs["e_ijk"]))
+                ghost = ~layout.in_data(rs["e_b"], rs["e_ijk"])
+                # data values by column id; ghost values (sweeps only) by
+                # -1 - their full-region id, resolved below
+                col = np.where(ghost, 0, layout.col(rs["e_b"], rs["e_c"], lev,
+                                                    np.where(ghost[:, None], 0, rs["e_ijk"])))
+                col = np.where(ghost, -1 - layout.row(rs["e_b"], rs["e_c"], lev, rs["e_ijk"]),
+                               col)
+                Cc.append(col)
                 V.append(rs["e_w"])
                 Er.append(rs["e_row"] + row_off)
             row_off += nr
@@ -129,15 +147,39 @@ def build_operator(w, levels=None, diagnostics=None):
     order = np.argsort(rows, kind="stable")
     inv = np.empty_like(order)
     inv[order] = np.arange(len(order))
+    rows = rows[order]
+    bvec = bvec[order]
     if Cc:
         er = inv[np.concatenate(Er)]
-        A = sp.csr_matrix((np.concatenate(V), (er, np.concatenate(Cc))),
-                          shape=(len(rows), layout.n_data))
+        cc = np.concatenate(Cc)
+        vv = np.concatenate(V)
+        d = cc >= 0
+        A = sp.csr_matrix((vv[d], (er[d], cc[d])), shape=(len(rows), layout.n_data))
+        if not np.all(d):
+            gid = -1 - cc[~d]
+            pos = np.searchsorted(rows, gid)
+            pos = np.minimum(pos, len(rows) - 1)
+            if not np.all(rows[pos] == gid):
+                raise OracleError("a column is a ghost value no sub-matrix covers")
+            G = sp.csr_matrix((vv[~d], (er[~d], pos)), shape=(len(rows), len(rows)))
+            A, bvec = _jacobi_sweeps(A, G, bvec, sweeps)
     else:
         A = sp.csr_matrix((len(rows), layout.n_data))
     A.sum_duplicates()
     A.sort_indices()
-    return Operator(layout, rows[order], A, bvec[order])
+    return Operator(layout, rows, A, bvec)
+
+
+def _jacobi_sweeps(D, G, b0, k):
+    """``k`` Jacobi sweeps from zero ghosts, ``g <- D x + G g + b0``, as one
+    affine map of the data: ``(A, b)`` with ``A_0 = 0, b_0 = 0``,
+    ``A_{m+1} = D + G A_m``, ``b_{m+1} = b0 + G b_m``."""
+    A = sp.csr_matrix(D.shape)
+    b = np.zeros(len(b0))
+    for _ in range(k):
+        A = (D + G @ A).tocsr()
+        b = b0 + G @ b
+    return A, b
 
 
 def apply(op, fields):

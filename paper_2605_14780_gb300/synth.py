@@ -129,6 +129,79 @@ def dirichlet_block(nx=20, ny=14, h=2, nlevels=3, ncomp=2, dtype="f64", t=0.0, s
             "bcs": bcs, "fields": fields}
 
 
+def ghost_on_ghost(sizes=((12, 9), (7, 10)), h=3, nlevels=2, ncomp=2, dtype="f64",
+                   seed=22, scheme="extrapolate", sweeps=3):
+    """2-D blocks whose faces are user CSR rows that read other ghost values
+    (the iterative form of Sec. II-B, resolved by ``sweeps`` Jacobi sweeps
+    from zero ghosts); corners zero.
+
+    ``scheme``: ``"extrapolate"`` -- the ghost at depth r is
+    ``2 v(r-1) - v(r-2)``, v(-1), v(-2) the first two data layers behind the
+    face and v(r >= 0) the ghosts (exact linear extrapolation after h
+    sweeps); ``"smooth"`` -- ``0.5 data(layer r) + 0.2 (g(r, s-1) + g(r, s+1))
+    + 0.1 g(r-1, s)`` (the neighbours along the face wrap round; g(-1) is
+    data layer 0) plus b = 0.05, a contraction with ghost cycles."""
+    blocks = [block2d(nx, ny, h, nlevels, ncomp) for nx, ny in sizes]
+    fields = uniform_fields(blocks, dtype, -1.0, 1.0, seed)
+    comps = list(range(ncomp))
+    bcs = []
+    for b, blk in enumerate(blocks):
+        n = blk["n"]
+        for d in (0, 1):
+            for side in (0, 1):
+                ln = n[1 - d]
+
+                def cell(q, s_, d=d, side=side, n=n):
+                    # q < 0: data layer -1 - q behind the face; q >= 0: ghost depth q
+                    ijk = [0, 0, 0]
+                    if q < 0:
+                        L = -1 - q
+                        ijk[d] = L if side == 0 else n[d] - 1 - L
+                    else:
+                        ijk[d] = -1 - q if side == 0 else n[d] + q
+                    ijk[1 - d] = s_
+                    return ijk
+                lo, hi = [0, 0, 0], [n[0], n[1], 1]
+                lo[d], hi[d] = (-h, 0) if side == 0 else (n[d], n[d] + h)
+                # box cells in box order (axis 0 fastest)
+                box = [(i, j) for j in range(lo[1], hi[1]) for i in range(lo[0], hi[0])]
+                ents = []
+                for (i, j) in box:
+                    g = (i, j)
+                    r = (-1 - g[d]) if side == 0 else (g[d] - n[d])
+                    s_ = g[1 - d]
+                    if scheme == "extrapolate":
+                        ents.append([(cell(r - 1, s_), 2.0), (cell(r - 2, s_), -1.0)])
+                    elif scheme == "smooth":
+                        e = [(cell(-1 - r, s_) if r < n[d] else cell(-1, s_), 0.5),
+                             (cell(r, (s_ - 1) % ln), 0.2), (cell(r, (s_ + 1) % ln), 0.2),
+                             (cell(r - 1, s_), 0.1)]
+                        ents.append(e)
+                    else:
+                        raise ValueError(scheme)
+                nnz = np.array([len(e) for e in ents] * len(comps), np.int64)
+                rp = np.concatenate([[0], np.cumsum(nnz)])
+                col_ijk = np.array([c for _ in comps for e in ents for c, _w in e], np.int32)
+                val = np.array([w_ for _ in comps for e in ents for _c, w_ in e], np.float64)
+                col_comp = np.array([c for c in comps for e in ents for _ in e], np.int32)
+                rhs = None
+                if scheme == "smooth":
+                    rhs = np.full(len(box) * len(comps), 0.05)
+                bcs.append({"kind": "csr", "block": b, "lo": tuple(lo), "hi": tuple(hi),
+                            "comps": comps, "row_ptr": rp.astype(np.int64),
+                            "col_block": np.full(len(val), b, np.int32), "col_comp": col_comp,
+                            "col_ijk": col_ijk.reshape(-1, 3), "val": val, "rhs": rhs})
+        # corners zero
+        for a in (-1, 1):
+            for c in (-1, 1):
+                lo = [-h if a < 0 else n[0], -h if c < 0 else n[1], 0]
+                hi = [0 if a < 0 else n[0] + h, 0 if c < 0 else n[1] + h, 1]
+                bcs.append({"kind": "zero", "block": b, "lo": tuple(lo), "hi": tuple(hi),
+                            "comps": comps})
+    return {"name": f"ghost_on_ghost_{scheme}_k{sweeps}", "dtype": dtype, "blocks": blocks,
+            "bcs": bcs, "fields": fields, "ghost_sweeps": int(sweeps)}
+
+
 def total_full_values(w):
     return sum(int(np.prod(full_shape(b))) for b in w["blocks"])
 
