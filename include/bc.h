@@ -248,6 +248,19 @@ typedef struct bc_plan_opts {
                               geometry (generated on the GPU) is
                               BC_ERR_UNSUPPORTED, the host-built
                               BC_GEOM_CUBED_SPHERE_QUAD rows are not      */
+  int32_t ghost_sweeps;    /* 0 (default): every BC_CSR column must be a
+                              data value.  k in 1..64: BC_CSR rows may also
+                              read ghost values that a sub-matrix covers
+                              (the iterative form HOPE(I) of Sec. II-B);
+                              the plan folds k Jacobi sweeps, every ghost
+                              starting at zero and all covered rows
+                              evaluated together each sweep, into rows on
+                              data values only (HOPE(M)) at creation, on
+                              the host in FP64.  A column on an uncovered
+                              ghost is BC_ERR_COLUMN_NOT_DATA; folded rows
+                              over 4096 entries, or cubed-sphere rows
+                              generated on the GPU in the same plan,
+                              BC_ERR_UNSUPPORTED                             */
 } bc_plan_opts;
 
 typedef struct bc_plan bc_plan;

@@ -58,7 +58,7 @@ class BcPlanOpts(ctypes.Structure):
     _fields_ = [("units_per_lane", c_i32), ("unit_order", c_i32),
                 ("threads", c_i32), ("ctas_per_sm", c_i32),
                 ("strict_cover", c_i32), ("no_adjoint", c_i32),
-                ("no_runs", c_i32), ("host_only", c_i32)]
+                ("no_runs", c_i32), ("host_only", c_i32), ("ghost_sweeps", c_i32)]
 
 
 class BcStats(ctypes.Structure):
@@ -375,6 +375,8 @@ def plan_for_workload(w, tensors=None, opts=None, stencil=None):
         blocks = block_descriptors(tensors, w["blocks"])
     else:
         blocks = [specs.contiguous_block(b) for b in w["blocks"]]
+    if w.get("ghost_sweeps"):
+        opts = dict(opts or {}, ghost_sweeps=int(w["ghost_sweeps"]))
     return Plan(blocks, specs.submatrices(w), w["dtype"], opts, stencil)
 
 

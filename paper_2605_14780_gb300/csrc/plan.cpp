@@ -27,6 +27,9 @@
 
 #include <cuda_runtime.h>
 
+#include <unordered_map>
+#include <unordered_set>
+
 #include "../../include/bc.h"
 #include "bc_internal.h"
 #include "prune.h"
@@ -129,6 +132,11 @@ struct bc_plan {
   // or none); meaningless for pruned plans
   std::vector<int> sub_of_input;
   bool pruned = false;
+  // user CSR rows that read ghost values (bc_plan_opts.ghost_sweeps) are
+  // accepted only in the host-only plan that folds them; the ghost columns
+  // met are recorded by (slot, offset) key
+  bool allow_ghost_cols = false;
+  std::unordered_set<int64_t> ghost_cols;
   ExplicitRows rows;  // level 0, in sub-matrix order
   // host tables (FP64 copies)
   std::vector<int4> itp_idx;
@@ -209,6 +217,13 @@ int64_t cell_offset(const bc_block& b, int i, int j, int k) {
 bool in_data(const bc_block& b, int i, int j, int k) {
   return i >= 0 && i < b.n[0] && j >= 0 && j < b.n[1] && k >= 0 && k < b.n[2];
 }
+
+bool in_full(const bc_block& b, int i, int j, int k) {
+  return i >= -b.h[0] && i < b.n[0] + b.h[0] && j >= -b.h[1] && j < b.n[1] + b.h[1] &&
+         k >= -b.h[2] && k < b.n[2] + b.h[2];
+}
+
+int64_t col_key(int slot, int64_t off) { return ((int64_t)slot << 32) | (uint32_t)off; }
 
 bc_status validate_grid(const bc_grid* g, bc_plan* P) {
   if (!g) return fail(BC_ERR_INVALID_ARG, "grid is NULL");
@@ -443,7 +458,8 @@ bc_status add_csr(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
           return;
         }
         const bc_block& C = P->blocks[cb];
-        if (!in_data(C, ci, cj, ck)) {
+        const bool ghost_col = !in_data(C, ci, cj, ck);
+        if (ghost_col && !(P->allow_ghost_cols && in_full(C, ci, cj, ck))) {
           st = fail(BC_ERR_COLUMN_NOT_DATA, "sub-matrix %d: column (%d,%d,%d) of block %d is not data",
                     idx, ci, cj, ck, cb);
           return;
@@ -458,6 +474,7 @@ bc_status add_csr(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
         }
         const int cs = P->slot_base[cb] + cc;
         const int64_t co = cell_offset(C, ci, cj, ck);
+        if (ghost_col) P->ghost_cols.insert(col_key(cs, co));
         P->rows.entry(cs, co, m.val[e]);
         const int64_t pos = s.ell_base + r * w + (e - m.row_ptr[r]);
         P->csr_slot[pos] = cs;
@@ -1497,6 +1514,8 @@ void compute_stats(bc_plan* P) {
   st.launches_adj = P->has_adjoint ? ys + !P->adj_items.empty() + !P->adj_zero.empty() : 0;
 }
 
+constexpr int kMaxGhostSweeps = 64;
+
 bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
   std::memset(&o, 0, sizeof(o));
   if (in) o = *in;
@@ -1508,6 +1527,8 @@ bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
   if (o.units_per_lane < 1 || o.ctas_per_sm < 0 || o.unit_order < 0 || o.unit_order > 2 ||
       o.host_only < 0 || o.host_only > 1)
     return fail(BC_ERR_INVALID_ARG, "bad work-item options");
+  if (o.ghost_sweeps < 0 || o.ghost_sweeps > kMaxGhostSweeps)
+    return fail(BC_ERR_INVALID_ARG, "ghost_sweeps must be in 0..%d", kMaxGhostSweeps);
   return BC_OK;
 }
 
@@ -1750,6 +1771,168 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
 // ============================================================================
 // C ABI
 // ============================================================================
+// Cell (i, j, k) of block B at element offset `off` from its slot pointer:
+// the axes taken from the largest stride down, then checked by re-encoding
+// (false for a layout whose strides do not nest).
+bool decode_cell(const bc_block& B, int64_t off, int& i, int& j, int& k) {
+  int ax[3] = {0, 1, 2};
+  std::sort(ax, ax + 3, [&](int a, int b) { return B.stride[a] > B.stride[b]; });
+  int64_t rem = off;
+  int64_t c[3] = {0, 0, 0};
+  for (int t = 0; t < 3; ++t) {
+    c[ax[t]] = rem / B.stride[ax[t]];
+    rem -= c[ax[t]] * B.stride[ax[t]];
+  }
+  i = (int)c[0] - B.h[0];
+  j = (int)c[1] - B.h[1];
+  k = (int)c[2] - B.h[2];
+  return rem == 0 && in_full(B, i, j, k) && cell_offset(B, i, j, k) == off;
+}
+
+constexpr size_t kMaxFoldedRow = 4096;
+
+// Rows that read ghost values (the iterative form HOPE(I) of Sec. II-B)
+// become rows on data values only (HOPE(M)): every ghost starts at zero and
+// all covered rows are evaluated together `ghost_sweeps` times, Jacobi
+// style, which is one affine map of the data.  The rows of every kind come
+// from a host-only plan that accepts ghost columns; each user CSR
+// sub-matrix is then replaced by its folded rows (same box and components),
+// all other sub-matrices pass unchanged.
+bc_status fold_ghost_sweeps(const bc_grid* grid, const bc_submatrix* subs, int32_t nsubs,
+                            const bc_plan_opts& opts, SubStore& out) {
+  for (int32_t si = 0; si < nsubs; ++si)
+    if (subs[si].kind == BC_INTERP && subs[si].geometry == BC_GEOM_CUBED_SPHERE)
+      return fail(BC_ERR_UNSUPPORTED,
+                  "ghost_sweeps: the cubed-sphere rows generated on the GPU cannot be folded");
+  bc_plan T;
+  T.allow_ghost_cols = true;
+  bc_plan_opts o1 = opts;
+  o1.host_only = 1;
+  o1.no_adjoint = 1;
+  o1.ghost_sweeps = 0;
+  o1.strict_cover = 0;
+  bc_status st = plan_create_impl(grid, subs, nsubs, &o1, &T);
+  if (st != BC_OK) return st;
+  const ExplicitRows& R = T.rows;
+  const size_t nr = R.slot.size();
+  std::unordered_map<int64_t, size_t> row_of;
+  row_of.reserve(2 * nr);
+  for (size_t r = 0; r < nr; ++r) row_of[col_key(R.slot[r], R.off[r])] = r;
+  using Entries = std::vector<std::pair<int64_t, double>>;
+  struct Row {
+    Entries e;
+    double b = 0.0;
+  };
+  // data entries and rhs of every row, and the ghost rows each row reads
+  std::vector<Row> base(nr);
+  std::vector<std::vector<std::pair<size_t, double>>> reads(nr);
+  for (size_t r = 0; r < nr; ++r) {
+    base[r].b = R.rhs[r];
+    for (int64_t e = R.ptr[r]; e < R.ptr[r + 1]; ++e) {
+      const int64_t key = col_key(R.cslot[e], R.coff[e]);
+      if (T.ghost_cols.count(key)) {
+        const auto it = row_of.find(key);
+        if (it == row_of.end())
+          return fail(BC_ERR_COLUMN_NOT_DATA,
+                      "ghost_sweeps: a column is a ghost value no sub-matrix covers "
+                      "(slot %d, offset %lld)", R.cslot[e], (long long)R.coff[e]);
+        reads[r].push_back({it->second, R.val[e]});
+      } else {
+        base[r].e.push_back({key, R.val[e]});
+      }
+    }
+  }
+  // sweep 1 reads zero ghosts: every row is its data part; sweep m > 1 adds
+  // the weighted rows of sweep m - 1
+  std::vector<size_t> active;
+  for (size_t r = 0; r < nr; ++r)
+    if (!reads[r].empty()) active.push_back(r);
+  std::vector<Row> cur(nr), next(nr);
+  for (size_t r : active) cur[r] = base[r];
+  std::unordered_map<int64_t, double> acc;
+  for (int m = 2; m <= opts.ghost_sweeps; ++m) {
+    for (size_t r : active) {
+      acc.clear();
+      double b = base[r].b;
+      for (const auto& e : base[r].e) acc[e.first] += e.second;
+      for (const auto& g : reads[r]) {
+        const Row& src = reads[g.first].empty() ? base[g.first] : cur[g.first];
+        b += g.second * src.b;
+        for (const auto& e : src.e) acc[e.first] += g.second * e.second;
+      }
+      if (acc.size() > kMaxFoldedRow)
+        return fail(BC_ERR_UNSUPPORTED, "ghost_sweeps: a folded row has more than %d entries",
+                    (int)kMaxFoldedRow);
+      Row& o = next[r];
+      o.e.assign(acc.begin(), acc.end());
+      std::sort(o.e.begin(), o.e.end());
+      o.b = b;
+    }
+    for (size_t r : active) std::swap(cur[r], next[r]);
+  }
+  // the user CSR sub-matrices, refilled with their folded rows
+  out.subs.clear();
+  out.origin.clear();
+  for (int32_t si = 0; si < nsubs; ++si) {
+    const bc_submatrix& m = subs[si];
+    out.origin.push_back(si);
+    if (m.kind != BC_CSR) {
+      out.subs.push_back(m);
+      continue;
+    }
+    const Sub& s = T.subs[(size_t)T.sub_of_input[(size_t)si]];
+    const bc_block& B = T.blocks[(size_t)s.block];
+    auto& rp = out.i64.emplace_back();
+    auto& cb = out.i32.emplace_back();
+    auto& cc = out.i32.emplace_back();
+    auto& ck = out.i32.emplace_back();
+    auto& cv = out.dbl.emplace_back();
+    auto& rh = out.dbl.emplace_back();
+    rp.push_back(0);
+    for (int comp : s.comps) {
+      const int slot = T.slot_base[(size_t)s.block] + comp;
+      bc_status e2 = BC_OK;
+      for_box(s, [&](int, int i, int j, int k) {
+        if (e2 != BC_OK) return;
+        const size_t r = row_of.at(col_key(slot, cell_offset(B, i, j, k)));
+        const Row& row = reads[r].empty() ? base[r] : cur[r];
+        for (const auto& e : row.e) {
+          const int cs = (int)(e.first >> 32);
+          const int64_t co = (int64_t)(uint32_t)(e.first & 0xffffffff);
+          const int blk = T.slot_block[(size_t)cs];
+          int ci, cj, ckk;
+          if (!decode_cell(T.blocks[(size_t)blk], co, ci, cj, ckk)) {
+            e2 = fail(BC_ERR_UNSUPPORTED, "ghost_sweeps: block %d's strides do not nest", blk);
+            return;
+          }
+          cb.push_back(blk);
+          cc.push_back(cs - T.slot_base[(size_t)blk]);
+          ck.insert(ck.end(), {ci, cj, ckk});
+          cv.push_back(e.second);
+        }
+        rh.push_back(row.b);
+        rp.push_back((int64_t)cv.size());
+      });
+      if (e2 != BC_OK) return e2;
+    }
+    if (cv.empty()) {  // keep the arrays non-NULL
+      cb.push_back(0);
+      cc.push_back(0);
+      ck.insert(ck.end(), {0, 0, 0});
+      cv.push_back(0.0);
+    }
+    bc_submatrix s2 = m;
+    s2.row_ptr = rp.data();
+    s2.col_block = cb.data();
+    s2.col_comp = cc.data();
+    s2.col_ijk = ck.data();
+    s2.val = cv.data();
+    s2.rhs = rh.data();
+    out.subs.push_back(s2);
+  }
+  return BC_OK;
+}
+
 // Reconstruction-and-quadrature cubed-sphere sub-matrices become user CSR
 // sub-matrices before anything else sees the list.
 bc_status lower_subs(const bc_grid* grid, const bc_submatrix* subs, int32_t nsubs,
@@ -1758,6 +1941,26 @@ bc_status lower_subs(const bc_grid* grid, const bc_submatrix* subs, int32_t nsub
   std::string msg;
   const bc_status st = lower_cs_quadrature(grid, subs, nsubs, low, msg);
   return st == BC_OK ? st : fail(st, "%s", msg.c_str());
+}
+
+// The list plan creation works on: quadrature rows lowered to CSR, then rows
+// that read ghost values folded (both one-to-one or one-to-two in order).
+bc_status prepare_subs(const bc_grid* grid, const bc_plan_opts* opts, const bc_submatrix*& list,
+                       int32_t& n, SubStore& low, SubStore& fold) {
+  bc_status st = lower_subs(grid, list, n, low);
+  if (st != BC_OK) return st;
+  if (has_cs_quadrature(list, n)) {
+    list = low.subs.data();
+    n = (int32_t)low.subs.size();
+  }
+  if (opts && opts->ghost_sweeps != 0) {
+    bc_plan_opts o;
+    if ((st = normalise_opts(opts, o)) != BC_OK) return st;
+    if ((st = fold_ghost_sweeps(grid, list, n, o, fold)) != BC_OK) return st;
+    list = fold.subs.data();
+    n = (int32_t)fold.subs.size();
+  }
+  return BC_OK;
 }
 
 extern "C" {
@@ -1772,12 +1975,13 @@ bc_status bc_plan_create(const bc_grid* grid, const bc_submatrix* subs, int32_t 
   if (!P) return fail(BC_ERR_NOMEM, "host allocation of the plan");
   bc_status st;
   try {
-    SubStore low;
-    st = lower_subs(grid, subs, nsubs, low);
+    SubStore low, fold;
+    const bc_submatrix* list = subs;
+    int32_t n = nsubs;
+    st = prepare_subs(grid, opts, list, n, low, fold);
     if (st == BC_OK) {
       const bool lowered = has_cs_quadrature(subs, nsubs);
-      st = plan_create_impl(grid, lowered ? low.subs.data() : subs,
-                            lowered ? (int32_t)low.subs.size() : nsubs, opts, P);
+      st = plan_create_impl(grid, list, n, opts, P);
       if (st == BC_OK && lowered) {
         // back to the caller's numbering (a lowered sub-matrix maps to the
         // first of its CSR pieces)
@@ -1812,13 +2016,9 @@ bc_status bc_plan_create_pruned(const bc_grid* grid, const bc_submatrix* subs, i
   if (!P) return fail(BC_ERR_NOMEM, "host allocation of the plan");
   bc_status st;
   try {
-    SubStore low, pr;
-    st = lower_subs(grid, subs, nsubs, low);
+    SubStore low, fold, pr;
+    st = prepare_subs(grid, opts, subs, nsubs, low, fold);
     if (st == BC_OK) {
-      if (has_cs_quadrature(subs, nsubs)) {
-        subs = low.subs.data();
-        nsubs = (int32_t)low.subs.size();
-      }
       P->pruned = true;
       st = prune_submatrices(grid, subs, nsubs, offsets, noffsets, pr);
       if (st != BC_OK)

@@ -179,6 +179,20 @@ def test_pure_function_boundary_evaluated_on_the_device(dtype, layout):
         compare(synth.dirichlet_block(dtype=dtype, t=t), [x.cpu().numpy() for x in ts])
 
 
+@pytest.mark.parametrize("scheme,k", [("extrapolate", 3), ("extrapolate", 1), ("smooth", 6)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("layout", ["outermost", "innermost"])
+def test_ghost_reading_rows_folded(scheme, k, dtype, layout):
+    """User CSR rows that read other ghosts, folded by k Jacobi sweeps at
+    plan creation, against the oracle's folded matrix."""
+    import torch
+    w = synth.ghost_on_ghost(scheme=scheme, sweeps=k, dtype=dtype, nlevels=3)
+    ts = to_device_innermost(w["fields"]) if layout == "innermost" else to_device(w["fields"])
+    run(w, tensors=ts)
+    torch.cuda.synchronize()
+    compare(w, [t.cpu().numpy() for t in ts])
+
+
 def test_const_table_view():
     """The constant table as a torch view (CUDA array interface): a write
     through it is the b of the next apply."""

@@ -268,3 +268,44 @@ def test_host_plan_has_no_constant_tables():
     with pytest.raises(bc.BCError) as e:
         plan.const_values(0)
     assert e.value.status == "BC_ERR_UNSUPPORTED"
+
+
+# -- rows that read ghost values, folded by Jacobi sweeps ----------------------
+@pytest.mark.parametrize("scheme", ["extrapolate", "smooth"])
+@pytest.mark.parametrize("k", [1, 2, 3, 7])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_host_ghost_sweeps_equal_the_oracle(scheme, k, dtype):
+    w = synth.ghost_on_ghost(scheme=scheme, sweeps=k, dtype=dtype)
+    _close(*_plan_matrix(w, bc.plan_for_workload(w, opts=HOST)), atol=1e-14)
+
+
+@pytest.mark.parametrize("stencil", [bc.star_stencil(2, 1), bc.box_stencil(2, 2)])
+def test_host_ghost_sweeps_pruned(stencil):
+    """Folding sees every row; pruning then keeps the live ones."""
+    w = synth.ghost_on_ghost(scheme="smooth", sweeps=4)
+    rows, A, b, op = _plan_matrix(w, bc.plan_for_workload(w, opts=HOST, stencil=stencil))
+    keep = live_mask(w, stencil)[op.rows]
+    _close(rows, A, b, Operator(op.layout, op.rows[keep], op.A[keep], op.b[keep]), atol=1e-14)
+
+
+def test_host_ghost_sweeps_rejects():
+    w = synth.ghost_on_ghost(scheme="extrapolate", sweeps=2)
+    for k, status in ((-1, "BC_ERR_INVALID_ARG"), (65, "BC_ERR_INVALID_ARG"),
+                      (0, "BC_ERR_COLUMN_NOT_DATA")):
+        with pytest.raises(bc.BCError) as e:
+            bc.plan_for_workload(dict(w, ghost_sweeps=None), opts=dict(HOST, ghost_sweeps=k))
+        assert e.value.status == status, (k, e.value)
+    # a column on a ghost that no sub-matrix covers
+    w2 = synth.ghost_on_ghost(scheme="extrapolate", sweeps=2)
+    w2["bcs"][0]["col_ijk"] = w2["bcs"][0]["col_ijk"].copy()
+    w2["bcs"][0]["col_ijk"][1] = (-1, -1, 0)
+    w2["bcs"] = [d for d in w2["bcs"] if not (d["kind"] == "zero" and d["block"] == 0
+                                               and tuple(d["hi"][:2]) == (0, 0))]
+    with pytest.raises(bc.BCError) as e:
+        bc.plan_for_workload(w2, opts=HOST)
+    assert e.value.status == "BC_ERR_COLUMN_NOT_DATA"
+    # GPU-generated cubed-sphere rows cannot be folded on the host
+    t = synth.tiny_cubed_sphere()
+    with pytest.raises(bc.BCError) as e:
+        bc.plan_for_workload(dict(t, ghost_sweeps=2), opts=HOST)
+    assert e.value.status == "BC_ERR_UNSUPPORTED" and "fold" in str(e.value)
