@@ -174,7 +174,10 @@ typedef struct bc_grid {
  *              entries row_ptr[r] .. row_ptr[r+1]-1 with columns
  *              (col_block, col_comp, col_ijk[3]) and values val; rhs[r] (or
  *              NULL for zero) is added.  Rows repeat per level and read the
- *              same level of their column blocks.
+ *              same level of their column blocks.  Columns are data values;
+ *              with bc_plan_opts.ghost_sweeps > 0 they may also be ghost
+ *              values other sub-matrices (or this one) cover, folded at
+ *              creation (see there).
  * BC_SYNC   -- block-edge averaging (Sync of Sec. III-B): the fields of
  *              BC_CSR, but the box lies in the *data* region and its rows
  *              overwrite those data cells (cells several blocks store for
