@@ -420,7 +420,8 @@ def family_plans(w, tensors):
 
     def family_kind(s):
         # reconstruction-and-quadrature rows are executed as user CSR rows
-        if s["kind"] == specs.BC_INTERP and s.get("geometry") == specs.BC_GEOM_CUBED_SPHERE_QUAD:
+        if s["kind"] == specs.BC_INTERP and s.get("geometry") in (
+                specs.BC_GEOM_CUBED_SPHERE_QUAD, specs.BC_GEOM_CUBED_SPHERE_QUAD_CENTRED):
             return specs.BC_CSR
         return s["kind"]
     for name, kinds in FAMILY_KINDS.items():

@@ -90,8 +90,11 @@ typedef enum bc_kind {
 typedef enum bc_geometry {
   BC_GEOM_USER = 0,              /* interpolation tables given by the caller */
   BC_GEOM_CUBED_SPHERE = 1,      /* generated on the GPU for gnomonic panels */
-  BC_GEOM_CUBED_SPHERE_QUAD = 2  /* cell averages by reconstruction and
+  BC_GEOM_CUBED_SPHERE_QUAD = 2, /* cell averages by reconstruction and
                                     Gauss quadrature, generated on the host */
+  BC_GEOM_CUBED_SPHERE_QUAD_CENTRED = 3 /* the same with patches centred on
+                                    the ghost, which may read ghost values
+                                    (needs bc_plan_opts.ghost_sweeps)     */
 } bc_geometry;
 
 /* Execution forms of the forward apply. */
@@ -164,6 +167,14 @@ typedef struct bc_grid {
  *              bad p or nquad BC_ERR_UNSUPPORTED (p > N: INVALID_ARG), a
  *              box beyond the panel's full region BC_ERR_OUT_OF_RANGE, a box
  *              cell that is not an edge ghost BC_ERR_GEOMETRY.
+ *              geometry = BC_GEOM_CUBED_SPHERE_QUAD_CENTRED: the same rows
+ *              with both clamps dropped, so that every patch stays centred
+ *              on its ghost; near the panel corners and across the shared
+ *              edge it then takes ghost values of the neighbour panel (the
+ *              iterative form HOPE(I) of Sec. II-B), which the plan folds
+ *              with bc_plan_opts.ghost_sweeps (0 sweeps:
+ *              BC_ERR_COLUMN_NOT_DATA).  Patches must stay inside the
+ *              neighbour's full region (h >= p/2), else BC_ERR_GEOMETRY.
  *              rot_comp = {cu, cv} (or {-1, -1}) names two listed components
  *              that form a covariant vector: for them the interpolated pair
  *              is multiplied by the 2x2 matrix M (user: itp_rot[vol*4],

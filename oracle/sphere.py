@@ -36,7 +36,10 @@ throughout the project:
   the data values.  The patch is chosen once per ghost from its centre:
   normal cells from ``clamp(r' - (p/2 - 1), 0, N - p)``, along cells from
   ``clamp(floor(t + 1e-9) - (p/2 - 1), 0, N - p)``.  Vector pairs are
-  rotated by ``M`` at every point before the average.
+  rotated by ``M`` at every point before the average.  With ``centred`` the
+  two clamps are dropped: near the panel corners and across the shared
+  edge the patch then takes ghost cells of ``Q`` (HOPE(I) of Sec. II-B),
+  which the operator resolves by Jacobi sweeps (``ghost_sweeps``).
 """
 from __future__ import annotations
 
@@ -269,12 +272,16 @@ def cubed_sphere_rows(bc, blocks, diagnostics=None):
 # Reconstruction at quadrature points (Sec. II-B, the HOPE example; Sec. III-B,
 # Itp = Agg . Recons)
 # ----------------------------------------------------------------------------
-def patch_starts(rq, t, N, p):
+def patch_starts(rq, t, N, p, centred=False):
     """First node of the ``p x p`` reconstruction patch on the neighbour panel
     along its normal axis (from the depth row ``rq``) and along the edge (from
-    the along position ``t`` of the ghost centre)."""
-    sn = np.clip(np.asarray(rq, np.int64) - (p // 2 - 1), 0, N - p)
-    st = np.clip(np.floor(np.asarray(t) + SNAP_TOL).astype(np.int64) - (p // 2 - 1), 0, N - p)
+    the along position ``t`` of the ghost centre).  Clamped into the data
+    cells, or, ``centred``, left centred on the ghost (the patch may then
+    take ghost cells of the neighbour, the HOPE(I) case of Sec. II-B)."""
+    sn = np.asarray(rq, np.int64) - (p // 2 - 1)
+    st = np.floor(np.asarray(t) + SNAP_TOL).astype(np.int64) - (p // 2 - 1)
+    if not centred:
+        sn, st = np.clip(sn, 0, N - p), np.clip(st, 0, N - p)
     return sn, st
 
 
@@ -306,7 +313,7 @@ def average_reconstruction_weights(x, p):
     return c
 
 
-def quad_strip(P, N, h, p, nq, d, side, vector):
+def quad_strip(P, N, h, p, nq, d, side, vector, centred=False):
     """Weights of the ghost cells of one edge strip.
 
     Each ghost cell is averaged over its ``nq x nq`` Gauss-Legendre points in
@@ -320,7 +327,9 @@ def quad_strip(P, N, h, p, nq, d, side, vector):
     every point)."""
     g = strip_geometry(P, N, h, d, side)
     Q, dq = g["Q"], g["dq"]
-    sn, st = patch_starts(g["rq"], g["t"], N, p)
+    sn, st = patch_starts(g["rq"], g["t"], N, p, centred)
+    if np.any(sn < -h) or np.any(sn + p > N + h) or np.any(st < -h) or np.any(st + p > N + h):
+        raise OracleError("a centred patch leaves the neighbour's full region")
     xg, wg = np.polynomial.legendre.leggauss(nq)
     delta = math.pi / (2 * N)
     R = len(g["cells"])
@@ -353,6 +362,7 @@ def cubed_sphere_quad_rows(bc, blocks):
     (entries normal node major, along node minor)."""
     panels = list(bc["panels"])
     N, h, p, nq = int(bc["N"]), int(bc["h"]), int(bc["p"]), int(bc["quad"])
+    centred = bool(bc.get("centred"))
     if p < 2 or p > N:
         raise OracleError("reconstruction order must be in 2..N")
     if nq < 1:
@@ -370,7 +380,7 @@ def cubed_sphere_quad_rows(bc, blocks):
         sets = []
         for d in (0, 1):
             for side in (0, 1):
-                g, sn, st, W, V = quad_strip(P, N, h, p, nq, d, side, bool(vpair))
+                g, sn, st, W, V = quad_strip(P, N, h, p, nq, d, side, bool(vpair), centred)
                 R = len(g["cells"])
                 src = np.zeros((R, p * p, 3), np.int64)
                 src[:, :, g["dq"]] = sn[:, None] + kn[None, :]

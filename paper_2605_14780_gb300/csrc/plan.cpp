@@ -1864,7 +1864,9 @@ bc_status fold_ghost_sweeps(const bc_grid* grid, const bc_submatrix* subs, int32
         return fail(BC_ERR_UNSUPPORTED, "ghost_sweeps: a folded row has more than %d entries",
                     (int)kMaxFoldedRow);
       Row& o = next[r];
-      o.e.assign(acc.begin(), acc.end());
+      o.e.clear();
+      for (const auto& e : acc)
+        if (e.second != 0.0) o.e.push_back(e);  // terms that cancel exactly
       std::sort(o.e.begin(), o.e.end());
       o.b = b;
     }

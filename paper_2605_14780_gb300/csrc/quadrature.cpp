@@ -10,7 +10,10 @@
 //   * Recons: each point is carried to the neighbour panel Q across the edge
 //     and evaluated by the tensor-product polynomial of degree p - 1 per axis
 //     whose averages over a p x p patch of Q's data cells are the data (cell
-//     averages in Q's angles); the patch is fixed per ghost from its centre;
+//     averages in Q's angles); the patch is fixed per ghost from its centre,
+//     clamped into Q's data cells or (the centred variant) left centred, in
+//     which case it may take Q's ghost cells and the plan folds the rows
+//     that read ghosts by Jacobi sweeps;
 //   * Agg: the tensor Gauss weights w_a w_b / 4 (the cell average in angle
 //     coordinates);
 //   * covariant vector pairs are rotated by M = e_P . e_Q^dual at every point
@@ -176,7 +179,9 @@ void average_reconstruction(double x, int p, double* c) {
 bool has_cs_quadrature(const bc_submatrix* subs, int nsubs) {
   if (!subs) return false;
   for (int i = 0; i < nsubs; ++i)
-    if (subs[i].kind == BC_INTERP && subs[i].geometry == BC_GEOM_CUBED_SPHERE_QUAD) return true;
+    if (subs[i].kind == BC_INTERP && (subs[i].geometry == BC_GEOM_CUBED_SPHERE_QUAD ||
+                                      subs[i].geometry == BC_GEOM_CUBED_SPHERE_QUAD_CENTRED))
+      return true;
   return false;
 }
 
@@ -197,8 +202,9 @@ struct GhostRow {
   double V[2][2][kQuadPMax][kQuadPMax];
 };
 
-bc_status ghost_row(int P, int N, int p, int nq, bool vec, int i, int j, const double* xg,
-                    const double* wg, GhostRow& g, std::string& msg, int idx) {
+bc_status ghost_row(int P, int N, int h, int p, int nq, bool vec, bool centred, int i, int j,
+                    const double* xg, const double* wg, GhostRow& g, std::string& msg,
+                    int idx) {
   const double delta = kPi / (2.0 * N);
   const bool io = i < 0 || i >= N, jo = j < 0 || j >= N;
   if (io == jo) return bad(msg, BC_ERR_GEOMETRY, idx, "a box cell is not an edge ghost");
@@ -224,8 +230,14 @@ bc_status ghost_row(int P, int N, int p, int nq, bool vec, int i, int j, const d
     return bad(msg, BC_ERR_GEOMETRY, idx, "ghost centre is off the neighbour rows");
   g.Q = Q;
   g.dq = dq;
-  g.sn = std::min(std::max((int)rq - (p / 2 - 1), 0), N - p);
-  g.st = std::min(std::max((int)std::floor(fc[1 - dq] + kSnap) - (p / 2 - 1), 0), N - p);
+  g.sn = (int)rq - (p / 2 - 1);
+  g.st = (int)std::floor(fc[1 - dq] + kSnap) - (p / 2 - 1);
+  if (!centred) {
+    g.sn = std::min(std::max(g.sn, 0), N - p);
+    g.st = std::min(std::max(g.st, 0), N - p);
+  } else if (g.sn < -h || g.sn + p > N + h || g.st < -h || g.st + p > N + h) {
+    return bad(msg, BC_ERR_GEOMETRY, idx, "a centred patch leaves the neighbour's full region");
+  }
   for (int a = 0; a < p; ++a)
     for (int b = 0; b < p; ++b) {
       g.W[a][b] = 0.0;
@@ -271,7 +283,8 @@ bc_status lower_cs_quadrature(const bc_grid* grid, const bc_submatrix* subs, int
   }
   for (int si = 0; si < nsubs; ++si) {
     const bc_submatrix& m = subs[si];
-    if (!(m.kind == BC_INTERP && m.geometry == BC_GEOM_CUBED_SPHERE_QUAD)) {
+    const bool centred = m.geometry == BC_GEOM_CUBED_SPHERE_QUAD_CENTRED;
+    if (!(m.kind == BC_INTERP && (m.geometry == BC_GEOM_CUBED_SPHERE_QUAD || centred))) {
       out.subs.push_back(m);
       out.origin.push_back(si);
       continue;
@@ -331,7 +344,8 @@ bc_status lower_cs_quadrature(const bc_grid* grid, const bc_submatrix* subs, int
     std::vector<GhostRow> rows((size_t)vol);
     for (int j = m.lo[1], q = 0; j < m.hi[1]; ++j)
       for (int i = m.lo[0]; i < m.hi[0]; ++i, ++q) {
-        bc_status st = ghost_row(panel, N, p, m.nquad, vec, i, j, xg, wg, rows[q], msg, si);
+        bc_status st = ghost_row(panel, N, hh, p, m.nquad, vec, centred, i, j, xg, wg, rows[q],
+                                 msg, si);
         if (st != BC_OK) return st;
       }
     // one CSR sub-matrix per group of components: the scalar ones, then the pair

@@ -27,6 +27,7 @@ import numpy as np
 
 BC_ZERO, BC_CONST, BC_MAP, BC_INTERP, BC_CSR, BC_SYNC = range(6)
 BC_GEOM_USER, BC_GEOM_CUBED_SPHERE, BC_GEOM_CUBED_SPHERE_QUAD = 0, 1, 2
+BC_GEOM_CUBED_SPHERE_QUAD_CENTRED = 3
 
 
 def contiguous_block(blk):
@@ -187,7 +188,9 @@ def cubed_sphere_submatrices(bc, blocks):
                 hi = [N, N, 1]
                 lo[d], hi[d] = (-h, 0) if side == 0 else (N, N + h)
                 if bc.get("quad"):
-                    geom = {"geometry": BC_GEOM_CUBED_SPHERE_QUAD, "nquad": int(bc["quad"])}
+                    geom = {"geometry": (BC_GEOM_CUBED_SPHERE_QUAD_CENTRED if bc.get("centred")
+                                         else BC_GEOM_CUBED_SPHERE_QUAD),
+                            "nquad": int(bc["quad"])}
                 else:
                     geom = {"geometry": BC_GEOM_CUBED_SPHERE}
                 out.append(_sub(BC_INTERP, panels[P], lo, hi, comps, p=p, rot_comp=rot,

@@ -481,13 +481,16 @@ def _corner_csr(N, h, panel, corner, ncomp, scalar_comps, vector_pair):
 
 
 def cubed_sphere(N=32, h=2, p=4, nlevels=1, fields=("scalar",), dtype="f64",
-                 seed=1, quad=None):
+                 seed=1, quad=None, centred=False, sweeps=10):
     """Six equiangular gnomonic panels of N x N cells with halo h.
 
     ``quad = nq`` asks for reconstruction-and-quadrature edge rows (each
     edge ghost the average of nq x nq Gauss points, each point reconstructed
     from a p x p patch of the neighbour panel, Sec. II-B) instead of the 1-D
-    Lagrange rows along the neighbour row.
+    Lagrange rows along the neighbour row.  ``centred`` (with ``quad``)
+    keeps every patch centred on its ghost, so that patches take ghost cells
+    of the neighbour panel (HOPE's iterative form, Sec. II-B), resolved by
+    ``sweeps`` Jacobi sweeps (the workload's ``ghost_sweeps``).
 
     ``fields`` is ``("scalar",)`` (one component uniform in [-1, 1]) or
     ``("h", "u", "v")`` (a smooth height field of 1e4 +- 100 m built from a
@@ -533,14 +536,19 @@ def cubed_sphere(N=32, h=2, p=4, nlevels=1, fields=("scalar",), dtype="f64",
             "vector_pair": vpair}]
     if quad:
         bcs[0]["quad"] = int(quad)
+        if centred:
+            bcs[0]["centred"] = True
     for pnl in range(6):
         for corner in range(4):
             bcs.append(_corner_csr(N, h, pnl, corner, ncomp, scalar_comps,
                                    vpair))
-    qtag = f"_q{int(quad)}" if quad else ""
-    return {"name": f"cubed_sphere{N}_h{h}_p{p}{qtag}_L{nlevels}", "dtype": dtype,
-            "blocks": blocks, "bcs": bcs, "fields": arrs,
-            "sphere": {"N": N, "h": h, "p": p, "quad": quad, "fields": tuple(fields)}}
+    qtag = (f"_q{int(quad)}" + (f"c{int(sweeps)}" if centred else "")) if quad else ""
+    w = {"name": f"cubed_sphere{N}_h{h}_p{p}{qtag}_L{nlevels}", "dtype": dtype,
+         "blocks": blocks, "bcs": bcs, "fields": arrs,
+         "sphere": {"N": N, "h": h, "p": p, "quad": quad, "fields": tuple(fields)}}
+    if quad and centred:
+        w["ghost_sweeps"] = int(sweeps)
+    return w
 
 
 # ----------------------------------------------------------------------------

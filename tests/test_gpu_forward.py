@@ -136,6 +136,20 @@ def test_cubed_sphere_quadrature(N, h, p, nq, fields, dtype, layout):
     compare(w, out)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("layout", ["outermost", "innermost"])
+def test_cubed_sphere_centred_quadrature_folded(dtype, layout):
+    """Centred reconstruction patches that read the neighbour's ghosts,
+    folded by 10 Jacobi sweeps at plan creation (rows of a few hundred
+    entries), against the oracle."""
+    from gpu_util import to_device_innermost
+    w = synth.cubed_sphere(10, 3, 4, 4, ("h", "u", "v"), dtype, seed=7, quad=2, centred=True,
+                           sweeps=10)
+    ts = to_device_innermost(w["fields"]) if layout == "innermost" else None
+    _, out = run(w, tensors=ts)
+    compare(w, out)
+
+
 def test_hope_cubed_sphere_sampled():
     """6 x 384^2, h = 3, (h, u, v) x 32 levels FP32, 4 x 4 reconstruction at
     2 x 2 Gauss points: levels 0, 17 and 31 compared with the oracle."""

@@ -309,3 +309,32 @@ def test_host_ghost_sweeps_rejects():
     with pytest.raises(bc.BCError) as e:
         bc.plan_for_workload(dict(t, ghost_sweeps=2), opts=HOST)
     assert e.value.status == "BC_ERR_UNSUPPORTED" and "fold" in str(e.value)
+
+
+def _close_values(rows, A, b, op, atol=1e-13):
+    """Same rows, entries equal within FP64 rounding (an entry that cancels
+    to zero on one side may be stored or dropped on the other)."""
+    assert np.array_equal(rows, op.rows)
+    assert abs(A - op.A).max() <= atol if A.nnz + op.A.nnz else True
+    assert np.allclose(b, op.b, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("N,h,p,nq,k,fields,dtype", [
+    (12, 3, 4, 2, 10, ("h", "u", "v"), "f64"), (9, 2, 4, 1, 3, ("scalar",), "f32"),
+    (10, 3, 6, 3, 2, ("h", "u", "v"), "f64"), (8, 1, 2, 2, 5, ("scalar",), "f64")])
+def test_host_centred_quadrature_folded(N, h, p, nq, k, fields, dtype):
+    """Centred patches read the neighbour's ghost cells (HOPE(I)); folded
+    by k sweeps, the library's rows equal the oracle's."""
+    w = synth.cubed_sphere(N, h, p, 2, fields, dtype, seed=5, quad=nq, centred=True, sweeps=k)
+    _close_values(*_plan_matrix(w, bc.plan_for_workload(w, opts=HOST)))
+
+
+def test_host_centred_quadrature_needs_sweeps():
+    w = synth.cubed_sphere(8, 2, 4, 1, ("scalar",), "f64", seed=5, quad=2, centred=True)
+    with pytest.raises(bc.BCError) as e:
+        bc.plan_for_workload(dict(w, ghost_sweeps=None), opts=HOST)
+    assert e.value.status == "BC_ERR_COLUMN_NOT_DATA"
+    w = synth.cubed_sphere(8, 1, 6, 1, ("scalar",), "f64", seed=5, quad=2, centred=True)
+    with pytest.raises(bc.BCError) as e:                     # h < p/2: patch leaves the region
+        bc.plan_for_workload(w, opts=HOST)
+    assert e.value.status == "BC_ERR_GEOMETRY"

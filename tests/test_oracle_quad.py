@@ -171,3 +171,42 @@ def test_pin_catches_transposed_rotation(monkeypatch):
     real = sphere.rotation
     monkeypatch.setattr(sphere, "rotation", lambda *a: np.transpose(real(*a), (0, 2, 1)))
     assert _quad_error(16, 4, 2, True) > 100 * good
+
+
+def _mid_edge_error(N, p, nq, centred, sweeps):
+    """Largest error over the middle half of every edge strip (away from the
+    panel corners, whose CSR rows are only first-order)."""
+    h = 3
+    w = synth.cubed_sphere(N, h, p, 1, ("scalar",), "f64", seed=1, quad=nq, centred=centred,
+                           sweeps=sweeps)
+    idx = np.arange(-h, N + h)
+    I, J = np.meshgrid(idx, idx, indexing="xy")
+    exact = []
+    for P in range(6):
+        avg = _cell_averages(P, N, I, J, _smooth)[0]
+        exact.append(avg)
+        synth.data_view(w["fields"][P], w["blocks"][P])[0, 0, 0] = avg[h:h + N, h:h + N]
+    y = apply(build_operator(w), w["fields"])
+    q = N // 4
+    m = np.zeros((N + 2 * h,) * 2, bool)
+    m[h + q:h + N - q, :h] = m[h + q:h + N - q, N + h:] = True
+    m[:h, h + q:h + N - q] = m[N + h:, h + q:h + N - q] = True
+    return max(float(np.max(np.abs(y[P][0, 0, 0][m] - exact[P][m]))) for P in range(6))
+
+
+def test_centred_patches_fold_to_a_converged_fixed_point():
+    """Centred patches read the neighbour's ghost cells (HOPE(I)); the
+    Jacobi sweeps have converged by ten (twenty change nothing), and one
+    sweep (ghost columns dropped) is a different, worse answer."""
+    ops = {}
+    w = synth.cubed_sphere(12, 3, 4, 1, ("h", "u", "v"), "f64", seed=2, quad=2, centred=True)
+    for k in (1, 10, 20):
+        ops[k] = apply(build_operator(dict(w, ghost_sweeps=k)), w["fields"])
+    diff = max(float(np.max(np.abs(a - b))) for a, b in zip(ops[10], ops[20]))
+    first = max(float(np.max(np.abs(a - b))) for a, b in zip(ops[1], ops[10]))
+    assert diff < 1e-9 * 1e4 and first > 1e-3
+
+
+def test_centred_patches_converge_away_from_corners():
+    e = [_mid_edge_error(N, 4, 2, True, 10) for N in (16, 32)]
+    assert math.log2(e[0] / e[1]) >= 4 - 0.7, e
