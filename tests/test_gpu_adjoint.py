@@ -71,6 +71,8 @@ def _level_mask(w, levels):
     lambda: synth.ghost_on_ghost(scheme="smooth", sweeps=5, dtype="f64"),
     lambda: synth.ghost_on_ghost(scheme="extrapolate", sweeps=3, dtype="f32", nlevels=4),
     lambda: synth.cubed_sphere(9, 3, 4, 3, ("h", "u", "v"), "f64", seed=4, quad=2),
+    lambda: synth.cubed_sphere(8, 3, 4, 3, ("h", "u", "v"), "f64", seed=4, quad=2,
+                               centred=True, sweeps=10),
     lambda: synth.cubed_sphere(14, 2, 6, 6, ("h", "u", "v"), "f32", seed=4, quad=3),
 ])
 def test_adjoint_vs_oracle(make):
