@@ -162,12 +162,85 @@ static int quadrature_sphere(void) {
   return 0;
 }
 
+/* one 2-D block whose low x face extrapolates linearly, g_r = 2 v_{r-1} -
+   v_{r-2}, reading the ghosts nearer the data: folded by h sweeps, every
+   row holds two data entries (x0, x1) with weights (r + 2, -(r + 1)) */
+static int folded_extrapolation(void) {
+  const int n = 6, h = 3;
+  const int F = n + 2 * h;
+  bc_block blk = {{n, n, 1}, {h, h, 0}, 1, 1, {1, F, (int64_t)F * F}, 1};
+  bc_grid grid = {BC_F64, 1, &blk};
+  int32_t comp0 = 0;
+  int64_t rp[3 * 6 + 1];
+  int32_t cb[2 * 3 * 6], cc[2 * 3 * 6], ck[3 * 2 * 3 * 6];
+  double v[2 * 3 * 6];
+  int e = 0, r = 0;
+  rp[0] = 0;
+  for (int j = 0; j < n; ++j)
+    for (int i = -h; i < 0; ++i) {       /* box order: axis 0 fastest */
+      const int a = i + 1, b = i + 2;    /* v_{r-1}, v_{r-2} of depth r = -1 - i */
+      cb[e] = 0; cc[e] = 0; ck[3 * e] = a; ck[3 * e + 1] = j; ck[3 * e + 2] = 0; v[e++] = 2.0;
+      cb[e] = 0; cc[e] = 0; ck[3 * e] = b; ck[3 * e + 1] = j; ck[3 * e + 2] = 0; v[e++] = -1.0;
+      rp[++r] = e;
+    }
+  bc_submatrix m = {0};
+  m.kind = BC_CSR;
+  m.block = 0;
+  m.lo[0] = -h; m.hi[0] = 0;
+  m.lo[1] = 0; m.hi[1] = n;
+  m.lo[2] = 0; m.hi[2] = 1;
+  m.ncomps = 1;
+  m.comps = &comp0;
+  m.row_ptr = rp;
+  m.col_block = cb;
+  m.col_comp = cc;
+  m.col_ijk = ck;
+  m.val = v;
+  bc_plan_opts opts = {0};
+  opts.host_only = 1;
+  bc_plan* plan = NULL;
+  const bc_status st0 = bc_plan_create(&grid, &m, 1, &opts, &plan);
+  printf("unfolded %s\n", bc_status_string(st0));
+  opts.ghost_sweeps = h;
+  if (check(bc_plan_create(&grid, &m, 1, &opts, &plan), "folded plan")) return 1;
+  int64_t nrows = 0, nnz = 0;
+  if (check(bc_plan_export_csr(plan, &nrows, &nnz, NULL, NULL, NULL, NULL, NULL, NULL, NULL),
+            "export sizes")) return 1;
+  int32_t* rs = malloc(sizeof(int32_t) * nrows);
+  int64_t* ro = malloc(sizeof(int64_t) * nrows);
+  int64_t* p = malloc(sizeof(int64_t) * (nrows + 1));
+  int32_t* cs = malloc(sizeof(int32_t) * nnz);
+  int64_t* co = malloc(sizeof(int64_t) * nnz);
+  double* w = malloc(sizeof(double) * nnz);
+  double* rhs = malloc(sizeof(double) * nrows);
+  if (check(bc_plan_export_csr(plan, &nrows, &nnz, rs, ro, p, cs, co, w, rhs), "export"))
+    return 1;
+  int bad = 0;
+  for (int64_t q = 0; q < nrows; ++q) {
+    const int i = (int)(ro[q] % F) - h;
+    const int depth = -1 - i;
+    const int64_t x0 = ro[q] - i, x1 = x0 + 1;      /* offsets of data cells (0, j), (1, j) */
+    double w0 = 0.0, w1 = 0.0;
+    for (int64_t t = p[q]; t < p[q + 1]; ++t) {
+      if (co[t] == x0) w0 += w[t];
+      else if (co[t] == x1) w1 += w[t];
+      else ++bad;
+    }
+    if (w0 != depth + 2.0 || w1 != -(depth + 1.0)) ++bad;
+  }
+  printf("folded %lld %lld %d\n", (long long)nrows, (long long)nnz, bad);
+  free(rs); free(ro); free(p); free(cs); free(co); free(w); free(rhs);
+  bc_plan_destroy(plan);
+  return 0;
+}
+
 int main(void) {
   printf("sizes %zu %zu %zu %zu %zu %zu\n", sizeof(bc_block), sizeof(bc_grid),
          sizeof(bc_submatrix), sizeof(bc_plan_opts), sizeof(bc_stats),
          offsetof(bc_submatrix, nquad));
   if (periodic_block()) return 1;
   if (quadrature_sphere()) return 1;
+  if (folded_extrapolation()) return 1;
   return 0;
 }
 """
@@ -217,3 +290,9 @@ def test_quadrature_rows_from_c(program):
     assert int(nrows) == 6 * 4 * h * N
     assert int(nnz) == int(nrows) * p * p
     assert float(worst) < 1e-12
+
+
+def test_folded_ghost_rows_from_c(program):
+    assert program["unfolded"] == ["BC_ERR_COLUMN_NOT_DATA"]
+    nrows, nnz, bad = (int(x) for x in program["folded"])
+    assert nrows == 3 * 6 and nnz == 2 * nrows and bad == 0
