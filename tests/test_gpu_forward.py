@@ -74,6 +74,35 @@ def test_persistent_and_item_shapes(opts):
     compare(w, out)
 
 
+@pytest.mark.parametrize("make", [
+    lambda: synth.hpcg_block((1, 1, 1), "P", seed=3),
+    lambda: synth.hpcg_block((1, 1, 1), "S", seed=3, dtype="f32"),
+    lambda: synth.hpcg_block((2, 1, 3), "P", seed=3),
+    lambda: synth.batching(nblocks=6, side_lo=1, side_hi=3, lev_lo=1, lev_hi=3, h=1, seed=5,
+                           dtype="f32"),
+])
+def test_degenerate_block_sizes(make):
+    """One-cell extents (h = N = 1 reflections, one-cell blocks): forward
+    bit-exact against the oracle, and the adjoint."""
+    import torch
+    from oracle.operator import apply_adjoint
+    w = make()
+    plan, out = run(w)
+    compare(w, out)
+    cot = synth.cotangent_like(w, 9)
+    cs = to_device(cot)
+    plan.adjoint(bc.slot_table(cs))
+    torch.cuda.synchronize()
+    got = flat([c.cpu().numpy() for c in cs]).astype(np.float64)
+    op = build_operator(w)
+    ref = flat(apply_adjoint(op, cot))
+    y = flat(cot).astype(np.float64)
+    scale = np.abs(y).copy()
+    scale[op.layout.data_rows()] += abs(op.A).T @ np.abs(y[op.rows])
+    tol = 1e-12 if w["dtype"] == "f64" else 2e-6
+    assert np.all(np.abs(got - ref) <= tol * scale)
+
+
 def test_batching_full_512():
     """The 512-block batching workload in full."""
     w = synth.batching()

@@ -338,3 +338,19 @@ def test_host_centred_quadrature_needs_sweeps():
     with pytest.raises(bc.BCError) as e:                     # h < p/2: patch leaves the region
         bc.plan_for_workload(w, opts=HOST)
     assert e.value.status == "BC_ERR_GEOMETRY"
+
+
+@pytest.mark.parametrize("n,variant", [((1, 1, 1), "P"), ((1, 1, 1), "S"), ((1, 2, 1), "Z"),
+                                       ((2, 1, 3), "P")])
+def test_host_degenerate_block_sizes(n, variant):
+    """One-cell extents: circular and symmetric maps of a single data layer
+    (h = N = 1), and blocks of one cell along some axes."""
+    w = synth.hpcg_block(n, variant, seed=3)
+    _same(*_plan_matrix(w, bc.plan_for_workload(w, opts=HOST)))
+
+
+def test_host_tiny_uneven_blocks():
+    w = synth.batching(nblocks=6, side_lo=1, side_hi=3, lev_lo=1, lev_hi=3, h=1, seed=5,
+                       dtype="f64")
+    assert min(min(b["n"][:2]) for b in w["blocks"]) == 1
+    _same(*_plan_matrix(w, bc.plan_for_workload(w, opts=HOST)))
