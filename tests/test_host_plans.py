@@ -354,3 +354,22 @@ def test_host_tiny_uneven_blocks():
                        dtype="f64")
     assert min(min(b["n"][:2]) for b in w["blocks"]) == 1
     _same(*_plan_matrix(w, bc.plan_for_workload(w, opts=HOST)))
+
+
+def test_host_largest_component_span():
+    """Element offsets are 32-bit: the largest element offset of a component
+    must stay below 2^31 - 1 (here set through a padded axis-2 stride: the
+    last cell sits at 15 + 3 s2)."""
+    from paper_2605_14780_gb300 import specs
+    s_max = (2 ** 31 - 2 - 15) // 3
+    for s2, ok in ((s_max, True), (s_max + 1, False)):
+        blk = {"n": (2, 2, 2), "h": (1, 1, 1), "nlevels": 1, "ncomp": 1,
+               "stride": (1, 4, s2), "level_stride": 1}
+        subs = [specs._sub(specs.BC_ZERO, 0, (-1, 0, 0), (0, 2, 2), [0])]
+        if ok:
+            plan = bc.Plan([blk], subs, "f64", opts=HOST)
+            assert plan.stats()["ghost_values"] == 4
+        else:
+            with pytest.raises(bc.BCError) as e:
+                bc.Plan([blk], subs, "f64", opts=HOST)
+            assert e.value.status == "BC_ERR_UNSUPPORTED"
