@@ -5,7 +5,7 @@ second."""
 import numpy as np
 import pytest
 
-from gpu_util import TOL, bits, compare, flat, run, to_device, to_device_innermost
+from gpu_util import TOL, compare, flat, run, to_device, to_device_innermost
 from oracle.operator import apply_adjoint, build_operator
 from paper_2605_14780_gb300 import bc, synth
 
