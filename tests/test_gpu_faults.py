@@ -2,10 +2,9 @@
 device allocation of a plan creation fail (no GPU fault is made).  Creation
 must report BC_ERR_NOMEM, leak no device memory, and leave the library
 usable."""
-import numpy as np
 import pytest
 
-from gpu_util import compare, flat, to_device
+from gpu_util import compare, to_device
 from paper_2605_14780_gb300 import bc, synth
 
 pytestmark = pytest.mark.gpu

@@ -5,7 +5,6 @@ apply (a separate code path from the transpose), the dot-product identity is
 evaluated with compensated sums, and explicit CSR rows must equal the user's
 matrix entry for entry.
 """
-import math
 
 import numpy as np
 import pytest

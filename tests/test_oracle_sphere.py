@@ -11,7 +11,6 @@
   differences;
 * adjacency is symmetric.
 """
-import math
 
 import numpy as np
 import pytest

@@ -3,7 +3,7 @@ closed-form counts for star and box stencils."""
 import numpy as np
 import pytest
 
-from paper_2605_14780_gb300 import bc, synth
+from paper_2605_14780_gb300 import bc
 from pruning import live_cells
 
 
