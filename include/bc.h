@@ -411,6 +411,19 @@ bc_status bc_plan_const_values(bc_plan* plan, int32_t sub, void** values,
 bc_status bc_plan_set_const(bc_plan* plan, int32_t sub, const void* values,
                             void* stream);
 
+/*
+ * Test and debugging aid: replay on the host the values every forward work
+ * item (the per-kind list and the batched per-family lists) and every
+ * adjoint item (gather, add-runs of unit copies, zero pass) would write,
+ * with the kernels' unit decompositions, and compare them with the plan's
+ * rows: each covered value written exactly once, copies reading their row's
+ * column, zero and constant values equal to the row's b, each data value
+ * gathering exactly the terms of A^T in ascending ghost order.  *values =
+ * values checked, *problems = mismatches (the first is described by
+ * bc_last_error).  Works on host-only plans; no device work.
+ */
+bc_status bc_plan_check_work(const bc_plan* plan, int64_t* values, int64_t* problems);
+
 /* Fill *out with the plan's counters. */
 bc_status bc_plan_stats(const bc_plan* plan, bc_stats* out);
 

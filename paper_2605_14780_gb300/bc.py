@@ -90,6 +90,7 @@ SIGNATURES = {
     "bc_plan_autotune": (c_i32, [c_vp, c_vp, c_vp]),
     "bc_plan_const_values": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), P_i64]),
     "bc_plan_set_const": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
+    "bc_plan_check_work": (c_i32, [c_vp, P_i64, P_i64]),
     "bc_plan_stats": (c_i32, [c_vp, ctypes.POINTER(BcStats)]),
     "bc_plan_export_csr": (c_i32, [c_vp, P_i64, P_i64, P_i32, P_i64, P_i64,
                                    P_i32, P_i64, P_dbl, P_dbl]),
@@ -252,6 +253,14 @@ class Plan:
             v = getattr(s, name)
             out[name] = list(v) if hasattr(v, "__len__") else int(v)
         return out
+
+    def check_work(self):
+        """Host replay of the work lists against the plan's rows:
+        ``(values checked, problems, first problem)``."""
+        n, bad = c_i64(), c_i64()
+        _check(self._lib.bc_plan_check_work(self._h, ctypes.byref(n), ctypes.byref(bad)))
+        msg = self._lib.bc_last_error().decode() if bad.value else ""
+        return n.value, bad.value, msg
 
     def export_csr(self):
         nr, nz = c_i64(), c_i64()

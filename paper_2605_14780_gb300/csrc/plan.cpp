@@ -1935,6 +1935,177 @@ bc_status fold_ghost_sweeps(const bc_grid* grid, const bc_submatrix* subs, int32
   return BC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Host emulation of the work lists (test and debugging aid): replays, item by
+// item, the values each forward and adjoint kernel writes, with the unit
+// decompositions of the kernels (flat cell- or level-fastest units, chunks of
+// levels, runs), and compares them with the plan's explicit rows.
+// ---------------------------------------------------------------------------
+struct WorkCheck {
+  const bc_plan* P;
+  int64_t problems = 0;
+  std::string first;
+  void problem(const char* what, int slot, int64_t off) {
+    if (problems++ == 0) {
+      char buf[200];
+      snprintf(buf, sizeof(buf), "%s (slot %d, element %lld)", what, slot, (long long)off);
+      first = buf;
+    }
+  }
+  int64_t ls_of_slot(int slot) const {
+    const bc_block& B = P->blocks[(size_t)P->slot_block[(size_t)slot]];
+    return B.nlevels > 1 ? B.level_stride : 0;
+  }
+  int levels_of_slot(int slot) const {
+    return P->blocks[(size_t)P->slot_block[(size_t)slot]].nlevels;
+  }
+  // every (q, l) unit of a non-run item
+  template <typename F>
+  void units(const Item& it, F f) const {
+    const int vol = (int)it.vol.d, L = (int)it.lev.d;
+    for (int u = it.u0; u < it.u0 + it.nunits; ++u) {
+      if (it.mode == MODE_FLAT_LEVEL) {
+        f(u / L, u % L);
+      } else if (it.mode == MODE_FLAT_CELL) {
+        f(u % vol, u / vol);
+      } else {
+        const int c = u / vol, q = u % vol;
+        for (int l = c * it.mode; l < std::min(c * it.mode + it.mode, L); ++l) f(q, l);
+      }
+    }
+  }
+};
+
+int64_t check_forward_list(WorkCheck& W, const std::vector<Item>& items, bool values = true) {
+  const bc_plan* P = W.P;
+  const ExplicitRows& R = P->rows;
+  struct Want {
+    size_t r;
+    int l;
+    int hits;
+  };
+  std::unordered_map<int64_t, Want> want;
+  for (size_t r = 0; r < R.slot.size(); ++r)
+    for (int l = 0; l < W.levels_of_slot(R.slot[r]); ++l)
+      want[col_key(R.slot[r], R.off[r] + l * W.ls_of_slot(R.slot[r]))] = {r, l, 0};
+  auto write = [&](int slot, int64_t E) -> Want* {
+    const auto it = want.find(col_key(slot, E));
+    if (it == want.end()) {
+      W.problem("a forward item writes a value no row covers", slot, E);
+      return nullptr;
+    }
+    if (++it->second.hits > 1) W.problem("a value is written twice", slot, E);
+    return &it->second;
+  };
+  auto check_copy = [&](const Want* w, int src_slot, int64_t src_E, int slot, int64_t E) {
+    const size_t r = w->r;
+    const int64_t e = R.ptr[r];
+    if (R.ptr[r + 1] - e != 1 || R.val[e] != 1.0 || R.rhs[r] != 0.0 || R.cslot[e] != src_slot ||
+        R.coff[e] + w->l * W.ls_of_slot(R.cslot[e]) != src_E)
+      W.problem("a copy reads another value than its row", slot, E);
+  };
+  auto check_const = [&](const Want* w, double v, int slot, int64_t E) {
+    if (R.ptr[w->r + 1] != R.ptr[w->r] || R.rhs[w->r] != v)
+      W.problem("a zero or constant value differs from its row", slot, E);
+  };
+  for (const Item& it : items) {
+    if (it.mode == MODE_RUNS) {
+      for (int k = it.u0; k < it.u0 + it.nunits; ++k) {
+        const int4 run = P->runs[(size_t)k];
+        for (int t = 0; t < run.z; ++t) {
+          const Want* w = write(it.dst_slot, (int64_t)run.x + t);
+          if (!w || !values) continue;
+          if (it.kind == IK_MAP) check_copy(w, it.src_slot, (int64_t)run.y + t, it.dst_slot, run.x + t);
+          else if (it.kind == IK_ZERO) check_const(w, 0.0, it.dst_slot, run.x + t);
+          else W.problem("a run item of another kind than zero or map", it.dst_slot, run.x);
+        }
+      }
+      continue;
+    }
+    W.units(it, [&](int q, int l) {
+      const int64_t E = (int64_t)P->ctab_d[(size_t)(it.ctab + q)] + (int64_t)l * it.dst_ls;
+      const Want* w = write(it.dst_slot, E);
+      if (it.kind == IK_INTERP_PAIR) write(it.dst_slot2, E);
+      if (!w || !values) return;
+      if (it.kind == IK_MAP)
+        check_copy(w, it.src_slot, (int64_t)P->ctab_s[(size_t)(it.ctab + q)] + (int64_t)l * it.src_ls,
+                   it.dst_slot, E);
+      else if (it.kind == IK_ZERO)
+        check_const(w, 0.0, it.dst_slot, E);
+      else if (it.kind == IK_CONST)
+        check_const(w, P->const_val[(size_t)(it.table + q)], it.dst_slot, E);
+    });
+  }
+  for (const auto& kv : want)
+    if (kv.second.hits != 1)
+      W.problem("a covered value is not written", (int)(kv.first >> 32),
+                (int64_t)(uint32_t)(kv.first & 0xffffffff));
+  return (int64_t)want.size();
+}
+
+int64_t check_adjoint_lists(WorkCheck& W, const std::vector<Item>& adj_items) {
+  const bc_plan* P = W.P;
+  const ExplicitRows& R = P->rows;
+  using Terms = std::vector<std::pair<int64_t, double>>;
+  // A^T by data value: the ghost values (and weights) that read it
+  std::unordered_map<int64_t, Terms> want;
+  for (size_t r = 0; r < R.slot.size(); ++r)
+    for (int l = 0; l < W.levels_of_slot(R.slot[r]); ++l) {
+      const int64_t g = col_key(R.slot[r], R.off[r] + l * W.ls_of_slot(R.slot[r]));
+      for (int64_t e = R.ptr[r]; e < R.ptr[r + 1]; ++e)
+        want[col_key(R.cslot[e], R.coff[e] + l * W.ls_of_slot(R.cslot[e]))].push_back({g, R.val[e]});
+    }
+  std::unordered_map<int64_t, Terms> got;
+  std::unordered_map<int64_t, int> hits;
+  for (const Item& it : adj_items) {
+    if (it.kind == IK_ADD) {
+      for (int k = it.u0; k < it.u0 + it.nunits; ++k) {
+        const int4 run = P->runs[(size_t)k];
+        for (int t = 0; t < run.z; ++t) {
+          const int64_t d = col_key(it.dst_slot, (int64_t)run.x + t);
+          ++hits[d];
+          got[d].push_back({col_key(it.src_slot, (int64_t)run.y + t), 1.0});
+        }
+      }
+      continue;
+    }
+    W.units(it, [&](int q, int l) {
+      const size_t tr = (size_t)(it.table + q);
+      const int64_t d = col_key(it.dst_slot, (int64_t)P->arow_off[tr] + (int64_t)l * it.dst_ls);
+      ++hits[d];
+      int64_t prev = INT64_MIN;
+      for (int64_t e = P->adj_ptr[tr]; e < P->adj_ptr[tr + 1]; ++e) {
+        const int gs = P->aent_slot[(size_t)e];
+        const int64_t order = col_key(gs, P->aent_off[(size_t)e]);
+        if (order < prev)
+          W.problem("transpose entries out of ghost order", it.dst_slot, P->arow_off[tr]);
+        prev = order;
+        got[d].push_back({col_key(gs, (int64_t)P->aent_off[(size_t)e] + l * W.ls_of_slot(gs)),
+                          P->aent_w[(size_t)e]});
+      }
+    });
+  }
+  for (auto& kv : want) {
+    const int slot = (int)(kv.first >> 32);
+    const int64_t off = (int64_t)(uint32_t)(kv.first & 0xffffffff);
+    const auto h = hits.find(kv.first);
+    if (h == hits.end() || h->second != 1) {
+      W.problem("a data value is not gathered exactly once", slot, off);
+      continue;
+    }
+    Terms a = kv.second, b = got[kv.first];
+    std::sort(a.begin(), a.end());
+    std::sort(b.begin(), b.end());
+    if (a != b) W.problem("a data value gathers other terms than A^T holds", slot, off);
+  }
+  for (const auto& kv : hits)
+    if (!want.count(kv.first))
+      W.problem("the adjoint writes a data value no row reads", (int)(kv.first >> 32),
+                (int64_t)(uint32_t)(kv.first & 0xffffffff));
+  // the zero pass clears every covered ghost value once (coverage only)
+  return (int64_t)want.size() + check_forward_list(W, P->adj_zero, false);
+}
+
 // Reconstruction-and-quadrature cubed-sphere sub-matrices become user CSR
 // sub-matrices before anything else sees the list.
 bc_status lower_subs(const bc_grid* grid, const bc_submatrix* subs, int32_t nsubs,
@@ -2186,6 +2357,28 @@ bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) 
   cudaEventDestroy(e1);
   cudaFree(flush);
   return st;
+}
+
+bc_status bc_plan_check_work(const bc_plan* plan, int64_t* values, int64_t* problems) {
+  if (!plan || !values || !problems) return fail(BC_ERR_INVALID_ARG, "NULL argument");
+  WorkCheck W{plan};
+  std::vector<Item> items = plan->items, fam, adj = plan->adj_items;
+  for (const auto& f : plan->fam_items) fam.insert(fam.end(), f.begin(), f.end());
+  // the checker's own test: BC_CHECK_PLANT=drop|dup|adjdrop alters the
+  // copies replayed here (never the plan), which must then fail
+  if (const char* plant = std::getenv("BC_CHECK_PLANT")) {
+    const std::string w = plant;
+    if (w == "drop" && !items.empty()) items.erase(items.begin());
+    if (w == "dup" && !fam.empty()) fam.push_back(fam.front());
+    if (w == "adjdrop" && !adj.empty()) adj.pop_back();
+  }
+  int64_t n = check_forward_list(W, items);
+  n += check_forward_list(W, fam);
+  if (plan->has_adjoint) n += check_adjoint_lists(W, adj);
+  *values = n;
+  *problems = W.problems;
+  if (W.problems) return fail(BC_OK, "%s", W.first.c_str());
+  return BC_OK;
 }
 
 bc_status bc_plan_stats(const bc_plan* plan, bc_stats* out) {

@@ -160,6 +160,8 @@ def test_host_plan_random_sweep(seed):
     rng = np.random.default_rng(100 + seed)
     plan = bc.plan_for_workload(w, opts=HOST)
     _same(*_plan_matrix(w, plan))
+    n, bad, msg = plan.check_work()
+    assert bad == 0, msg
     ndim = 3 if w["blocks"][0]["n"][2] > 1 else 2
     offs = rng.integers(-2, 3, size=(int(rng.integers(1, 6)), 3))
     if ndim == 2:
@@ -373,3 +375,72 @@ def test_host_largest_component_span():
             with pytest.raises(bc.BCError) as e:
                 bc.Plan([blk], subs, "f64", opts=HOST)
             assert e.value.status == "BC_ERR_UNSUPPORTED"
+
+
+# -- host replay of the work lists ---------------------------------------------
+def _innermost_blocks(w):
+    """Block descriptors with the levels of every cell contiguous."""
+    out = []
+    for b in w["blocks"]:
+        n, h, L = b["n"], b["h"], b["nlevels"]
+        F = [n[d] + 2 * h[d] for d in range(3)]
+        out.append({"n": tuple(n), "h": tuple(h), "nlevels": L, "ncomp": b["ncomp"],
+                    "stride": (L, L * F[0], L * F[0] * F[1]), "level_stride": 1})
+    return out
+
+
+WORK_CASES = [
+    ("alg1", lambda: synth.alg1_example()),
+    ("hpcg_P", lambda: synth.hpcg_block((7, 5, 6), "P", seed=1)),
+    ("batching", lambda: synth.batching(nblocks=16, side_lo=2, side_hi=40, lev_lo=1, lev_hi=20,
+                                        h=2, seed=3, dtype="f32")),
+    ("sync", lambda: synth.sync_grid(3, 2, 6, 2, 3, 2, "f64", seed=3)),
+    ("two_level", lambda: synth.two_level(14, 10, 2, 3, 2, "f64", seed=4)),
+    ("quadrature", lambda: synth.cubed_sphere(8, 2, 4, 5, ("h", "u", "v"), "f32", seed=5, quad=2)),
+    ("ghost", lambda: synth.ghost_on_ghost(scheme="smooth", sweeps=4, nlevels=3)),
+    ("dirichlet", lambda: synth.dirichlet_block(nlevels=9)),
+]
+WORK_OPTS = [{}, {"no_runs": 1}, {"units_per_lane": 1}, {"units_per_lane": 8, "unit_order": 1},
+             {"unit_order": 2}, {"threads": 512, "units_per_lane": 2}]
+
+
+@pytest.mark.parametrize("name,make", WORK_CASES, ids=[c[0] for c in WORK_CASES])
+@pytest.mark.parametrize("opts", WORK_OPTS, ids=lambda o: "-".join(f"{k}{v}" for k, v in o.items())
+                         or "default")
+@pytest.mark.parametrize("layout", ["outermost", "innermost"])
+def test_work_lists_replay_against_rows(name, make, opts, layout):
+    """Every forward item (per-kind and batched lists) and adjoint item,
+    replayed on the host with the kernels' unit decompositions, writes each
+    covered value once with its row's source or value, and each data value
+    gathers exactly its A^T terms."""
+    from paper_2605_14780_gb300 import specs
+    w = make()
+    o = dict(HOST, **opts)
+    if w.get("ghost_sweeps"):
+        o["ghost_sweeps"] = w["ghost_sweeps"]
+    blocks = (_innermost_blocks(w) if layout == "innermost"
+              else [specs.contiguous_block(b) for b in w["blocks"]])
+    plan = bc.Plan(blocks, specs.submatrices(w), w["dtype"], o)
+    n, bad, msg = plan.check_work()
+    assert n > 0 and bad == 0, msg
+
+
+@pytest.mark.parametrize("stencil", [bc.star_stencil(2, 1), bc.box_stencil(2, 2)])
+def test_work_lists_of_pruned_plans(stencil):
+    w = synth.batching(nblocks=12, side_lo=2, side_hi=30, lev_lo=1, lev_hi=9, h=2, seed=6,
+                       dtype="f32")
+    n, bad, msg = bc.plan_for_workload(w, opts=HOST, stencil=stencil).check_work()
+    assert n > 0 and bad == 0, msg
+
+
+@pytest.mark.parametrize("plant", ["drop", "dup", "adjdrop"])
+def test_work_replay_catches_planted_mistakes(monkeypatch, plant):
+    """The replay alters its own copies of the lists (never the plan): a
+    dropped item, a duplicated item and a dropped adjoint item are found."""
+    w = synth.batching(nblocks=8, side_lo=2, side_hi=20, lev_lo=1, lev_hi=6, h=2, seed=3,
+                       dtype="f32")
+    plan = bc.plan_for_workload(w, opts=HOST)
+    assert plan.check_work()[1] == 0
+    monkeypatch.setenv("BC_CHECK_PLANT", plant)
+    n, bad, msg = plan.check_work()
+    assert bad > 0 and msg
