@@ -2034,6 +2034,25 @@ int64_t check_forward_list(WorkCheck& W, const std::vector<Item>& items, bool va
         check_const(w, 0.0, it.dst_slot, E);
       else if (it.kind == IK_CONST)
         check_const(w, P->const_val[(size_t)(it.table + q)], it.dst_slot, E);
+      else if (it.kind == IK_CSR) {
+        // the ELL row as the CSR kernels read it (common source slot or one
+        // slot per entry) against the row's own entries at this level
+        const size_t row = (size_t)(it.table + q);
+        const int nnz = P->csr_nnz[row];
+        std::vector<std::pair<int64_t, double>> a, b;
+        for (int k = 0; k < nnz; ++k) {
+          const size_t e = (size_t)it.src_org + (size_t)q * (size_t)it.p + (size_t)k;
+          const int slot = it.src_slot >= 0 ? it.src_slot : P->csr_slot[e];
+          const int64_t ls = it.src_slot >= 0 ? it.src_ls : W.ls_of_slot(slot);
+          a.push_back({col_key(slot, (int64_t)P->csr_off[e] + l * ls), P->csr_val[e]});
+        }
+        for (int64_t e = R.ptr[w->r]; e < R.ptr[w->r + 1]; ++e)
+          b.push_back({col_key(R.cslot[e], R.coff[e] + w->l * W.ls_of_slot(R.cslot[e])), R.val[e]});
+        std::sort(a.begin(), a.end());
+        std::sort(b.begin(), b.end());
+        if (a != b || P->csr_rhs[row] != R.rhs[w->r] || nnz > it.p)
+          W.problem("a CSR row reads other entries than its row", it.dst_slot, E);
+      }
     });
   }
   for (const auto& kv : want)
