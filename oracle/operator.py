@@ -18,7 +18,7 @@ import scipy.sparse as sp
 
 from .regions import Layout
 from .rows import (OracleError, concat_rowsets, const_rows, csr_rows,
-                   faces_rows, map_rows, sync_rows, zero_rows)
+                   faces_rows, interp_rows, map_rows, sync_rows, zero_rows)
 from .sphere import cubed_sphere_rows
 
 __all__ = ["OracleError", "Operator", "rowsets", "build_operator", "apply",
@@ -39,6 +39,8 @@ def rowsets(w, diagnostics=None):
             out.append(map_rows(bc))
         elif k == "csr":
             out.append(csr_rows(bc))
+        elif k == "interp":
+            out.append(interp_rows(bc))
         elif k == "faces":
             out.append(faces_rows(bc, blocks))
         elif k == "cubed_sphere_edges":

@@ -129,6 +129,43 @@ def const_rows(bc):
     return rs
 
 
+def interp_rows(bc):
+    """User-defined interpolation rows ``A_ij = Itp_ij`` (Sec. III-B) given as
+    tables: box cell ``q`` reads the ``p`` data cells ``start[q] + n e_axis``
+    (``n < p``) of ``src_block`` with weights ``w[q, n]``.  A covariant pair
+    ``rot_comp = (cu, cv)`` is interpolated, then multiplied by the 2x2
+    ``rot[q]`` (row-major); other listed components use the plain row."""
+    cells = box_cells(bc["lo"], bc["hi"])
+    R = len(cells)
+    p = int(bc["p"])
+    start = np.asarray(bc["start"], np.int64).reshape(R, 3)
+    axis = np.asarray(bc["axis"], np.int64).reshape(R)
+    w = np.asarray(bc["w"], np.float64).reshape(R, p)
+    src = np.repeat(start[:, None, :], p, axis=1)               # (R, p, 3)
+    src[np.arange(R)[:, None], np.arange(p)[None, :], axis[:, None]] += np.arange(p)[None, :]
+    pair = tuple(bc.get("rot_comp") or (-1, -1))
+    rot = np.asarray(bc["rot"], np.float64).reshape(R, 2, 2) if pair[0] >= 0 else None
+    sets = []
+    e_row = np.repeat(np.arange(R), p)
+    for c in bc["comps"]:
+        rs = empty_rowset(bc["block"], np.full(R, c), cells)
+        if c in pair:
+            i = pair.index(c)
+            rs["e_row"] = np.concatenate([e_row, e_row])
+            rs["e_c"] = np.concatenate([np.full(R * p, pair[0]), np.full(R * p, pair[1])])
+            rs["e_ijk"] = np.concatenate([src.reshape(-1, 3), src.reshape(-1, 3)])
+            rs["e_w"] = np.concatenate([(rot[:, i, 0][:, None] * w).reshape(-1),
+                                        (rot[:, i, 1][:, None] * w).reshape(-1)])
+        else:
+            rs["e_row"] = e_row.copy()
+            rs["e_c"] = np.full(R * p, c)
+            rs["e_ijk"] = src.reshape(-1, 3).copy()
+            rs["e_w"] = w.reshape(-1).copy()
+        rs["e_b"] = np.full(len(rs["e_row"]), bc["src_block"], np.int64)
+        sets.append(rs)
+    return concat_rowsets(sets)
+
+
 def map_rows(bc):
     """A static single-entry row list (Table III, F_LIST), e.g. the rotated
     map of Alg. 1: the column of ghost ``g`` is

@@ -213,6 +213,16 @@ def submatrices(w):
             out.append(_sub(BC_MAP, bc["block"], bc["lo"], bc["hi"], bc["comps"],
                             src_block=bc["src_block"], perm=tuple(bc["perm"]),
                             sign=tuple(bc["sign"]), offset=tuple(bc["offset"])))
+        elif k == "interp":
+            out.append(_sub(BC_INTERP, bc["block"], bc["lo"], bc["hi"], bc["comps"],
+                            p=int(bc["p"]), geometry=BC_GEOM_USER,
+                            rot_comp=tuple(bc.get("rot_comp") or (-1, -1)),
+                            itp_src_block=np.full(len(bc["axis"]), bc["src_block"], np.int32),
+                            itp_start=np.asarray(bc["start"], np.int32).reshape(-1),
+                            itp_axis=np.asarray(bc["axis"], np.int32),
+                            itp_w=np.asarray(bc["w"], np.float64).reshape(-1),
+                            itp_rot=(np.asarray(bc["rot"], np.float64).reshape(-1)
+                                     if bc.get("rot_comp") else None)))
         elif k == "csr":
             out.append(_sub(BC_CSR, bc["block"], bc["lo"], bc["hi"], bc["comps"],
                             row_ptr=bc["row_ptr"], col_block=bc["col_block"],

@@ -202,6 +202,73 @@ def ghost_on_ghost(sizes=((12, 9), (7, 10)), h=3, nlevels=2, ncomp=2, dtype="f64
             "bcs": bcs, "fields": fields, "ghost_sweeps": int(sweeps)}
 
 
+def _lagrange(tau, p):
+    w = np.ones(p)
+    for k in range(p):
+        for m in range(p):
+            if m != k:
+                w[k] *= (tau - m) / (k - m)
+    return w
+
+
+def staggered_interp(nx=16, ny=12, h=2, nlevels=3, p=4, dtype="f64", seed=23, rotate=True):
+    """Two 2-D blocks side by side along x whose rows are staggered by half a
+    cell: each block's ghost columns facing the other are user interpolation
+    tables (Sec. III-B ``Itp`` given by the user): the ghost at depth r and
+    row s reads the other block's data column at depth r, interpolated along
+    y at s +- 1/2 with ``p``-point Lagrange weights (stencil clamped into the
+    data).  Components (h, u, v); with ``rotate`` the pair (u, v) is turned
+    by a per-cell angle after interpolation.  The y faces are circular, the
+    outer x faces and the corners zero."""
+    blocks = [block2d(nx, ny, h, nlevels, 3) for _ in range(2)]
+    fields = uniform_fields(blocks, dtype, -1.0, 1.0, seed)
+    comps = [0, 1, 2]
+    bcs = []
+    for b in range(2):
+        other = 1 - b
+        side = 1 if b == 0 else 0          # the face towards the other block
+        shift = 0.5 if b == 0 else -0.5
+        lo = [nx, 0, 0] if side else [-h, 0, 0]
+        hi = [nx + h, ny, 1] if side else [0, ny, 1]
+        starts, axes, ws, rots = [], [], [], []
+        for j in range(lo[1], hi[1]):
+            for i in range(lo[0], hi[0]):
+                r = i - nx if side else -1 - i
+                t = j + shift
+                st = int(np.clip(np.floor(t) - (p // 2 - 1), 0, ny - p))
+                src_i = r if side else nx - 1 - r
+                starts.append((src_i, st, 0))
+                axes.append(1)
+                ws.append(_lagrange(t - st, p))
+                th = 0.05 * (j + 1) * (r + 1) if rotate else 0.0
+                rots.append((np.cos(th), -np.sin(th), np.sin(th), np.cos(th)))
+        bcs.append({"kind": "interp", "block": b, "lo": tuple(lo), "hi": tuple(hi),
+                    "comps": comps, "src_block": other, "p": p,
+                    "start": np.array(starts, np.int32), "axis": np.array(axes, np.int32),
+                    "w": np.array(ws, np.float64), "rot_comp": (1, 2),
+                    "rot": np.array(rots, np.float64)})
+        # outer x face zero, y faces circular, corners zero
+        olo = [-h, 0, 0] if side else [nx, 0, 0]
+        ohi = [0, ny, 1] if side else [nx + h, ny, 1]
+        bcs.append({"kind": "zero", "block": b, "lo": tuple(olo), "hi": tuple(ohi),
+                    "comps": comps})
+        for yside in (0, 1):
+            ylo = [0, -h, 0] if yside == 0 else [0, ny, 0]
+            yhi = [nx, 0, 1] if yside == 0 else [nx, ny + h, 1]
+            off = ny if yside == 0 else -ny
+            bcs.append({"kind": "map", "block": b, "lo": tuple(ylo), "hi": tuple(yhi),
+                        "comps": comps, "src_block": b, "perm": (0, 1, 2), "sign": (1, 1, 1),
+                        "offset": (0, off, 0)})
+        for a in (-1, 1):
+            for c in (-1, 1):
+                clo = [-h if a < 0 else nx, -h if c < 0 else ny, 0]
+                chi = [0 if a < 0 else nx + h, 0 if c < 0 else ny + h, 1]
+                bcs.append({"kind": "zero", "block": b, "lo": tuple(clo), "hi": tuple(chi),
+                            "comps": comps})
+    return {"name": f"staggered_interp{nx}x{ny}_p{p}", "dtype": dtype, "blocks": blocks,
+            "bcs": bcs, "fields": fields}
+
+
 def total_full_values(w):
     return sum(int(np.prod(full_shape(b))) for b in w["blocks"])
 
