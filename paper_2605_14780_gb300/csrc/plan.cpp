@@ -2025,7 +2025,7 @@ int64_t check_forward_list(WorkCheck& W, const std::vector<Item>& items, bool va
     W.units(it, [&](int q, int l) {
       const int64_t E = (int64_t)P->ctab_d[(size_t)(it.ctab + q)] + (int64_t)l * it.dst_ls;
       const Want* w = write(it.dst_slot, E);
-      if (it.kind == IK_INTERP_PAIR) write(it.dst_slot2, E);
+      const Want* w2 = it.kind == IK_INTERP_PAIR ? write(it.dst_slot2, E) : nullptr;
       if (!w || !values) return;
       if (it.kind == IK_MAP)
         check_copy(w, it.src_slot, (int64_t)P->ctab_s[(size_t)(it.ctab + q)] + (int64_t)l * it.src_ls,
@@ -2052,6 +2052,42 @@ int64_t check_forward_list(WorkCheck& W, const std::vector<Item>& items, bool va
         std::sort(b.begin(), b.end());
         if (a != b || P->csr_rhs[row] != R.rhs[w->r] || nnz > it.p)
           W.problem("a CSR row reads other entries than its row", it.dst_slot, E);
+      } else if (it.kind == IK_INTERP || it.kind == IK_INTERP_PAIR) {
+        // the nodes and weights the interpolation kernels read (a snapped
+        // row reads node 0 only), rotated for a pair, against the rows
+        const size_t cell = (size_t)(it.table + q);
+        const int4 ix = P->itp_idx[cell];
+        const int np_ = (ix.w & kFlagSnap) ? 1 : it.p;
+        const int cu = it.comp & 0xffff, cv = it.comp >> 16;
+        auto node = [&](int comp, int n) {
+          const int slot = ix.x + comp;
+          return col_key(slot, (int64_t)ix.y + (int64_t)n * ix.z + l * W.ls_of_slot(slot));
+        };
+        auto same = [&](const Want* ww, const std::vector<std::pair<int64_t, double>>& a0) {
+          std::vector<std::pair<int64_t, double>> a = a0, b;
+          for (int64_t e = R.ptr[ww->r]; e < R.ptr[ww->r + 1]; ++e)
+            b.push_back({col_key(R.cslot[e], R.coff[e] + ww->l * W.ls_of_slot(R.cslot[e])),
+                         R.val[e]});
+          std::sort(a.begin(), a.end());
+          std::sort(b.begin(), b.end());
+          return a == b && R.rhs[ww->r] == 0.0;
+        };
+        const double* wt = &P->itp_w[cell * kPMax];
+        if (it.kind == IK_INTERP) {
+          std::vector<std::pair<int64_t, double>> a;
+          for (int n = 0; n < np_; ++n) a.push_back({node(cu, n), wt[n]});
+          if (!same(w, a)) W.problem("an interpolation row reads other nodes than its row",
+                                     it.dst_slot, E);
+        } else if (w2) {
+          const double* M = &P->itp_m[cell * 4];
+          for (int rr = 0; rr < 2; ++rr) {
+            std::vector<std::pair<int64_t, double>> a;
+            for (int n = 0; n < np_; ++n) a.push_back({node(cu, n), M[2 * rr] * wt[n]});
+            for (int n = 0; n < np_; ++n) a.push_back({node(cv, n), M[2 * rr + 1] * wt[n]});
+            if (!same(rr == 0 ? w : w2, a))
+              W.problem("a rotated pair reads other nodes than its rows", it.dst_slot, E);
+          }
+        }
       }
     });
   }

@@ -68,6 +68,8 @@ def _level_mask(w, levels):
     lambda: synth.cubed_sphere(9, 3, 6, 3, ("h", "u", "v"), "f64", seed=4),
     lambda: synth.cubed_sphere(16, 3, 6, 10, ("h", "u", "v"), "f32", seed=4),
     lambda: synth.two_level(20, 14, 2, nlevels=3, ncomp=2, dtype="f64", seed=5),
+    lambda: synth.staggered_interp(nlevels=4, p=4, dtype="f64"),
+    lambda: synth.staggered_interp(nlevels=9, p=6, dtype="f32"),
     lambda: synth.ghost_on_ghost(scheme="smooth", sweeps=5, dtype="f64"),
     lambda: synth.ghost_on_ghost(scheme="extrapolate", sweeps=3, dtype="f32", nlevels=4),
     lambda: synth.cubed_sphere(9, 3, 4, 3, ("h", "u", "v"), "f64", seed=4, quad=2),

@@ -179,6 +179,19 @@ def test_cubed_sphere_centred_quadrature_folded(dtype, layout):
     compare(w, out)
 
 
+@pytest.mark.parametrize("p,rotate", [(4, True), (2, False), (6, True), (8, False)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("layout", ["outermost", "innermost"])
+def test_user_interpolation_tables(p, rotate, dtype, layout):
+    """Interpolation rows given as user tables (staggered neighbours, a
+    per-cell rotation of the (u, v) pair) through the interpolation kernels."""
+    from gpu_util import to_device_innermost
+    w = synth.staggered_interp(nx=18, ny=13, h=2, nlevels=6, p=p, dtype=dtype, rotate=rotate)
+    ts = to_device_innermost(w["fields"]) if layout == "innermost" else None
+    _, out = run(w, tensors=ts)
+    compare(w, out)
+
+
 def test_hope_cubed_sphere_sampled():
     """6 x 384^2, h = 3, (h, u, v) x 32 levels FP32, 4 x 4 reconstruction at
     2 x 2 Gauss points: levels 0, 17 and 31 compared with the oracle."""

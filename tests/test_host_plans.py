@@ -399,6 +399,7 @@ WORK_CASES = [
     ("quadrature", lambda: synth.cubed_sphere(8, 2, 4, 5, ("h", "u", "v"), "f32", seed=5, quad=2)),
     ("ghost", lambda: synth.ghost_on_ghost(scheme="smooth", sweeps=4, nlevels=3)),
     ("dirichlet", lambda: synth.dirichlet_block(nlevels=9)),
+    ("user_interp", lambda: synth.staggered_interp(nlevels=5)),
 ]
 WORK_OPTS = [{}, {"no_runs": 1}, {"units_per_lane": 1}, {"units_per_lane": 8, "unit_order": 1},
              {"unit_order": 2}, {"threads": 512, "units_per_lane": 2}]
@@ -444,3 +445,35 @@ def test_work_replay_catches_planted_mistakes(monkeypatch, plant):
     monkeypatch.setenv("BC_CHECK_PLANT", plant)
     n, bad, msg = plan.check_work()
     assert bad > 0 and msg
+
+
+@pytest.mark.parametrize("p", [2, 4, 6])
+@pytest.mark.parametrize("rotate", [True, False])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_host_user_interpolation_tables(p, rotate, dtype):
+    """Interpolation rows given as user tables (geometry BC_GEOM_USER)."""
+    w = synth.staggered_interp(p=p, rotate=rotate, dtype=dtype)
+    _same(*_plan_matrix(w, bc.plan_for_workload(w, opts=HOST)))
+
+
+def test_host_user_interpolation_rejects():
+    from paper_2605_14780_gb300 import specs
+    w = synth.staggered_interp()
+    blocks = [specs.contiguous_block(b) for b in w["blocks"]]
+    for change, status in (
+            ({"itp_w": None}, "BC_ERR_INVALID_ARG"),                 # tables missing
+            ({"itp_axis": np.full(24, 3, np.int32)}, "BC_ERR_INVALID_ARG"),
+            ({"p": 9}, "BC_ERR_UNSUPPORTED")):
+        subs = specs.submatrices(w)
+        subs[0] = dict(subs[0], **change)
+        with pytest.raises(bc.BCError) as e:
+            bc.Plan(blocks, subs, w["dtype"], opts=HOST)
+        assert e.value.status == status, (change, e.value)
+    # a stencil that leaves the source data
+    subs = specs.submatrices(w)
+    st = np.asarray(subs[0]["itp_start"]).reshape(-1, 3).copy()
+    st[0, 1] = 12 - 2                                            # rows 10..13 of 12
+    subs[0] = dict(subs[0], itp_start=st.reshape(-1))
+    with pytest.raises(bc.BCError) as e:
+        bc.Plan(blocks, subs, w["dtype"], opts=HOST)
+    assert e.value.status == "BC_ERR_COLUMN_NOT_DATA"
