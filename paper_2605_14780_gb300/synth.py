@@ -211,6 +211,39 @@ def _lagrange(tau, p):
     return w
 
 
+def swap_xy(w):
+    """The same workload with axes 0 and 1 exchanged (blocks, boxes, maps,
+    tables and fields), so that every stencil steps along the other axis."""
+    def sw(t):
+        t = list(t)
+        return (t[1], t[0]) + tuple(t[2:])
+    out = dict(w, name=w["name"] + "_yx")
+    out["blocks"] = [dict(b, n=sw(b["n"]), h=sw(b["h"])) for b in w["blocks"]]
+    out["fields"] = [np.ascontiguousarray(a.swapaxes(3, 4)) for a in w["fields"]]
+    bcs = []
+    for bc in w["bcs"]:
+        d = dict(bc, lo=sw(bc["lo"]), hi=sw(bc["hi"]))
+        if bc["kind"] == "interp":
+            # box order is axis 0 fastest: reorder the per-cell tables too
+            nx_, ny_ = bc["hi"][0] - bc["lo"][0], bc["hi"][1] - bc["lo"][1]
+            order = np.arange(nx_ * ny_).reshape(ny_, nx_).T.reshape(-1)
+            st = np.asarray(bc["start"]).reshape(-1, 3)[order]
+            d["start"] = st[:, [1, 0, 2]].astype(np.int32)
+            d["axis"] = np.asarray(1 - np.asarray(bc["axis"])[order], np.int32)
+            d["w"] = np.asarray(bc["w"])[order]
+            d["rot"] = np.asarray(bc["rot"])[order]
+        elif bc["kind"] == "map":
+            perm = list(bc["perm"])
+            perm[0], perm[1] = perm[1], perm[0]
+            perm = [1 - q if q < 2 else q for q in perm]
+            d["perm"], d["sign"], d["offset"] = tuple(perm), sw(bc["sign"]), sw(bc["offset"])
+        elif bc["kind"] not in ("zero",):
+            raise ValueError(bc["kind"])
+        bcs.append(d)
+    out["bcs"] = bcs
+    return out
+
+
 def staggered_interp(nx=16, ny=12, h=2, nlevels=3, p=4, dtype="f64", seed=23, rotate=True):
     """Two 2-D blocks side by side along x whose rows are staggered by half a
     cell: each block's ghost columns facing the other are user interpolation

@@ -456,6 +456,13 @@ def test_host_user_interpolation_tables(p, rotate, dtype):
     _same(*_plan_matrix(w, bc.plan_for_workload(w, opts=HOST)))
 
 
+def test_host_user_interpolation_along_axis_0():
+    w = synth.swap_xy(synth.staggered_interp(nx=11, ny=9, p=4))
+    plan = bc.plan_for_workload(w, opts=HOST)
+    _same(*_plan_matrix(w, plan))
+    assert plan.check_work()[1] == 0
+
+
 def test_host_user_interpolation_rejects():
     from paper_2605_14780_gb300 import specs
     w = synth.staggered_interp()

@@ -77,3 +77,14 @@ def test_pin_catches_transposed_rotation(monkeypatch):
     import oracle.operator as op_mod
     monkeypatch.setattr(op_mod, "interp_rows", transposed)
     assert _turned_constant_error(synth.staggered_interp()) > 1e-3
+
+
+def test_axis_swap_transposes_the_result():
+    """The workload with axes 0 and 1 exchanged (stencils stepping along
+    axis 0) gives the transposed ghost values."""
+    w = synth.staggered_interp(nx=10, ny=7, h=2, nlevels=2, p=4)
+    v = synth.swap_xy(w)
+    y = apply(build_operator(w), w["fields"])
+    z = apply(build_operator(v), v["fields"])
+    for a, b in zip(y, z):
+        assert np.allclose(a.swapaxes(3, 4), b, rtol=0, atol=1e-13, equal_nan=True)
