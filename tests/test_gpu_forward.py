@@ -103,6 +103,42 @@ def test_degenerate_block_sizes(make):
     assert np.all(np.abs(got - ref) <= tol * scale)
 
 
+@pytest.mark.parametrize("unit_order", [1, 2])
+@pytest.mark.parametrize("layout", ["outermost", "innermost"])
+def test_forced_unit_orders(unit_order, layout):
+    """bc_plan_opts.unit_order forces cells-fastest or levels-fastest units
+    whatever the layout (the other order than the automatic one for one of
+    the two layouts): forward bit-exact, adjoint within tolerance."""
+    import torch
+    from oracle.operator import apply_adjoint
+    w = synth.batching(nblocks=24, side_lo=2, side_hi=30, lev_lo=1, lev_hi=17, h=2, seed=29,
+                       dtype="f32")
+    dev = to_device_innermost if layout == "innermost" else to_device
+    ts = dev(w["fields"])
+    plan, _ = run(w, opts={"unit_order": unit_order}, tensors=ts)
+    compare(w, [t.cpu().numpy() for t in ts])
+    cot = synth.cotangent_like(w, 30)
+    cs = dev(cot)
+    plan.adjoint(bc.slot_table(cs))
+    torch.cuda.synchronize()
+    got = flat([c.cpu().numpy() for c in cs]).astype(np.float64)
+    op = build_operator(w)
+    ref = flat(apply_adjoint(op, cot))
+    y = flat(cot).astype(np.float64)
+    scale = np.abs(y).copy()
+    scale[op.layout.data_rows()] += abs(op.A).T @ np.abs(y[op.rows])
+    assert np.all(np.abs(got - ref) <= 2e-6 * scale)
+
+
+def test_no_adjoint_plans_refuse_the_adjoint():
+    w = synth.alg1_example()
+    ts = to_device(w["fields"])
+    plan = bc.plan_for_workload(w, ts, {"no_adjoint": 1})
+    with pytest.raises(bc.BCError) as e:
+        plan.adjoint(bc.slot_table(ts))
+    assert e.value.status == "BC_ERR_UNSUPPORTED"
+
+
 def test_batching_full_512():
     """The 512-block batching workload in full."""
     w = synth.batching()
