@@ -418,7 +418,9 @@ bc_status bc_plan_set_const(bc_plan* plan, int32_t sub, const void* values,
  * with the kernels' unit decompositions, and compare them with the plan's
  * rows: each covered value written exactly once, copies reading their row's
  * column, zero and constant values equal to the row's b, CSR rows read from
- * the ELL tables equal to their rows, each data value
+ * the ELL tables and interpolation items read from their node and weight
+ * tables equal to their rows, Sync rows staged and committed once with
+ * column lists that are their transpose, each data value
  * gathering exactly the terms of A^T in ascending ghost order.  *values =
  * values checked, *problems = mismatches (the first is described by
  * bc_last_error).  Works on host-only plans; no device work.

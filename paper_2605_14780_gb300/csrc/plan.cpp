@@ -27,6 +27,7 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
 #include <unordered_map>
 #include <unordered_set>
 
@@ -2414,6 +2415,46 @@ bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) 
   return st;
 }
 
+// Sync rows (block-edge averaging): every row's staging range is its own,
+// every Sync value is committed once, and the column lists of the adjoint
+// hold exactly the rows' entries (the transpose) with the rows' staging
+// offsets.
+int64_t check_sync(WorkCheck& W) {
+  const auto& Y = W.P->sync;
+  std::vector<int> stage_hits((size_t)Y.stage, 0);
+  std::unordered_set<int64_t> committed;
+  std::map<int64_t, std::vector<std::pair<int, double>>> want, got;
+  int64_t n = 0;
+  for (size_t u = 0; u < Y.row.size(); ++u) {
+    const int4 r = Y.row[u];
+    if (r.w != W.levels_of_slot(r.x)) W.problem("a Sync row has another level count", r.x, r.y);
+    for (int l = 0; l < r.w; ++l, ++n) {
+      const int64_t idx = (int64_t)r.z + l;
+      if (idx < 0 || idx >= Y.stage) {
+        W.problem("a Sync row stages outside the buffer", r.x, r.y);
+        continue;
+      }
+      ++stage_hits[(size_t)idx];
+      if (!committed.insert(col_key(r.x, r.y + l * W.ls_of_slot(r.x))).second)
+        W.problem("a Sync value is committed twice", r.x, r.y);
+    }
+    for (int32_t e = Y.ptr[u]; e < Y.ptr[u + 1]; ++e)
+      want[col_key(Y.ent[(size_t)e].x, Y.ent[(size_t)e].y)].push_back({r.z, Y.w[(size_t)e]});
+  }
+  for (size_t i = 0; i < stage_hits.size(); ++i)
+    if (stage_hits[i] != 1) W.problem("a staging value is not used exactly once", -1, (int64_t)i);
+  for (size_t u = 0; u < Y.col.size(); ++u) {
+    const int4 c = Y.col[u];
+    if (c.z != W.levels_of_slot(c.x)) W.problem("a Sync column has another level count", c.x, c.y);
+    for (int32_t e = Y.cptr[u]; e < Y.cptr[u + 1]; ++e)
+      got[col_key(c.x, c.y)].push_back({Y.cstage[(size_t)e], Y.cw[(size_t)e]});
+  }
+  for (auto& kv : want) std::sort(kv.second.begin(), kv.second.end());
+  for (auto& kv : got) std::sort(kv.second.begin(), kv.second.end());
+  if (want != got) W.problem("the Sync column lists are not the transpose of the rows", -1, 0);
+  return n;
+}
+
 bc_status bc_plan_check_work(const bc_plan* plan, int64_t* values, int64_t* problems) {
   if (!plan || !values || !problems) return fail(BC_ERR_INVALID_ARG, "NULL argument");
   WorkCheck W{plan};
@@ -2430,6 +2471,7 @@ bc_status bc_plan_check_work(const bc_plan* plan, int64_t* values, int64_t* prob
   int64_t n = check_forward_list(W, items);
   n += check_forward_list(W, fam);
   if (plan->has_adjoint) n += check_adjoint_lists(W, adj);
+  n += check_sync(W);
   *values = n;
   *problems = W.problems;
   if (W.problems) return fail(BC_OK, "%s", W.first.c_str());
