@@ -130,6 +130,21 @@ def test_forced_unit_orders(unit_order, layout):
     assert np.all(np.abs(got - ref) <= 2e-6 * scale)
 
 
+@pytest.mark.parametrize("make", [
+    lambda: synth.tiny_cubed_sphere(),
+    lambda: synth.cubed_sphere(9, 3, 6, 5, ("h", "u", "v"), "f32", seed=4),
+    lambda: synth.batching(nblocks=20, side_lo=2, side_hi=30, lev_lo=1, lev_hi=9, h=2, seed=8,
+                           dtype="f32"),
+])
+def test_work_replay_of_device_plans(make):
+    """The host replay of the work lists on plans built with the GPU
+    geometry (interpolation tables generated on the device)."""
+    w = make()
+    plan = bc.plan_for_workload(w, to_device(w["fields"]))
+    n, bad, msg = plan.check_work()
+    assert n > 0 and bad == 0, msg
+
+
 def test_no_adjoint_plans_refuse_the_adjoint():
     w = synth.alg1_example()
     ts = to_device(w["fields"])
