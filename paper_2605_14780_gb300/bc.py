@@ -105,7 +105,9 @@ _LIB = None
 
 
 def library_path():
-    return os.path.join(LIB_DIR, LIB_NAME)
+    """The in-tree library, or the one ``BC_LIBRARY`` names (e.g. the
+    sanitized host build)."""
+    return os.environ.get("BC_LIBRARY") or os.path.join(LIB_DIR, LIB_NAME)
 
 
 def load_library():

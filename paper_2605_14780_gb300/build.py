@@ -35,10 +35,21 @@ def _compile(src, obj, extra):
     return r.stderr
 
 
-def build_library(force=False, extra_flags=()):
-    """Compile and link the library; returns its path."""
-    os.makedirs(OUT_DIR, exist_ok=True)
-    lib = os.path.join(OUT_DIR, "libbcgb300.so")
+SANITIZE = ["-O1", "-g", "-Xcompiler",
+            "-fsanitize=address,-fsanitize=undefined,-fno-omit-frame-pointer"]
+HOST_SOURCES = ("plan.cpp", "prune.cpp", "quadrature.cpp")
+
+
+def build_library(force=False, extra_flags=(), sanitize=False):
+    """Compile and link the library; returns its path.
+
+    ``sanitize`` builds a separate copy (``_lib/sanitize/``) whose host
+    translation units (plan builder, pruning, quadrature rows) carry the
+    address and undefined-behaviour sanitizers, for host-only checks with
+    the sanitizer runtimes preloaded; its kernels are the regular ones."""
+    out_dir = os.path.join(OUT_DIR, "sanitize") if sanitize else OUT_DIR
+    os.makedirs(out_dir, exist_ok=True)
+    lib = os.path.join(out_dir, "libbcgb300.so")
     srcs = [os.path.join(CSRC, s) for s in SOURCES] + [
         os.path.join(CSRC, "bc_internal.h"), os.path.join(CSRC, "prune.h"),
         os.path.join(CSRC, "quadrature.h"),
@@ -47,12 +58,16 @@ def build_library(force=False, extra_flags=()):
         newest = max(os.path.getmtime(s) for s in srcs)
         if os.path.getmtime(lib) >= newest and not extra_flags:
             return lib
-    objs = [os.path.join(OUT_DIR, s.replace(".", "_") + ".o") for s in SOURCES]
+    objs = [os.path.join(out_dir, s.replace(".", "_") + ".o") for s in SOURCES]
+
+    def flags(src):
+        return list(extra_flags) + (SANITIZE if sanitize and src in HOST_SOURCES else [])
     with ThreadPoolExecutor(len(SOURCES)) as ex:
-        list(ex.map(lambda a: _compile(a[0], a[1], list(extra_flags)),
-                    zip(SOURCES, objs)))
+        list(ex.map(lambda a: _compile(a[0], a[1], flags(a[0])), zip(SOURCES, objs)))
     cmd = [nvcc(), *ARCH, "-shared", "-o", lib + ".tmp", *objs,
            "-cudart", "static"]
+    if sanitize:
+        cmd += ["-Xcompiler", "-fsanitize=address,-fsanitize=undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
