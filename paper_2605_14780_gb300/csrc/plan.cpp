@@ -31,6 +31,8 @@
 #include <unordered_map>
 #include <unordered_set>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/bc.h"
 #include "bc_internal.h"
 #include "prune.h"
@@ -225,6 +227,15 @@ bool in_full(const bc_block& b, int i, int j, int k) {
 }
 
 int64_t col_key(int slot, int64_t off) { return ((int64_t)slot << 32) | (uint32_t)off; }
+
+// A named NVTX range over one entry point (visible to Nsight tools, which
+// can also filter kernels by it; without a tool attached it costs a branch).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 bc_status validate_grid(const bc_grid* g, bc_plan* P) {
   if (!g) return fail(BC_ERR_INVALID_ARG, "grid is NULL");
@@ -2196,6 +2207,7 @@ extern "C" {
 
 bc_status bc_plan_create(const bc_grid* grid, const bc_submatrix* subs, int32_t nsubs,
                          const bc_plan_opts* opts, bc_plan** out) {
+  TraceRange trace("bc_plan_create");
   if (!out) return fail(BC_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   g_last_error.clear();
@@ -2234,6 +2246,7 @@ bc_status bc_plan_create(const bc_grid* grid, const bc_submatrix* subs, int32_t 
 bc_status bc_plan_create_pruned(const bc_grid* grid, const bc_submatrix* subs, int32_t nsubs,
                                 const bc_plan_opts* opts, const int32_t* offsets,
                                 int32_t noffsets, bc_plan** out) {
+  TraceRange trace("bc_plan_create_pruned");
   if (!out) return fail(BC_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   g_last_error.clear();
@@ -2270,6 +2283,7 @@ bc_status bc_plan_create_pruned(const bc_grid* grid, const bc_submatrix* subs, i
 int32_t bc_plan_nslots(const bc_plan* plan) { return plan ? plan->nslots : 0; }
 
 bc_status bc_apply_form(bc_plan* plan, void* const* slot_ptrs, int32_t form, void* stream) {
+  TraceRange trace("bc_apply");
   if (!plan) return fail(BC_ERR_INVALID_ARG, "plan is NULL");
   if (plan->opts.host_only) return fail(BC_ERR_UNSUPPORTED, "host_only plan");
   if (!slot_ptrs && plan->nslots > 0) return fail(BC_ERR_INVALID_ARG, "slot_ptrs is NULL");
@@ -2281,6 +2295,7 @@ bc_status bc_apply(bc_plan* plan, void* const* slot_ptrs, void* stream) {
 }
 
 bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs, void* stream) {
+  TraceRange trace("bc_apply_adjoint");
   if (!plan) return fail(BC_ERR_INVALID_ARG, "plan is NULL");
   if (plan->opts.host_only) return fail(BC_ERR_UNSUPPORTED, "host_only plan");
   if (!plan->has_adjoint) return fail(BC_ERR_UNSUPPORTED, "plan was built without the transpose");
@@ -2309,6 +2324,7 @@ bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs, void* stream) 
 
 bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs, void* const* dev_ptrs,
                         void* const* slot_ptrs, void* stream) {
+  TraceRange trace("bc_apply_host");
   if (!plan || !host_ptrs || !dev_ptrs || !slot_ptrs)
     return fail(BC_ERR_INVALID_ARG, "NULL argument");
   if (plan->opts.host_only) return fail(BC_ERR_UNSUPPORTED, "host_only plan");
@@ -2345,6 +2361,7 @@ bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs, void* const* dev_
 }
 
 bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) {
+  TraceRange trace("bc_plan_autotune");
   if (plan && plan->opts.host_only) return fail(BC_ERR_UNSUPPORTED, "host_only plan");
   if (!plan || !slot_ptrs) return fail(BC_ERR_INVALID_ARG, "NULL argument");
   arm_fault_injection();
