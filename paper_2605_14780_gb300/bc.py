@@ -233,6 +233,50 @@ class Plan:
         _check(st)
         self._h = handle
         self.nslots = lib.bc_plan_nslots(handle)
+        # the layouts the plan's element offsets were computed for
+        self.layout = [dict(b) for b in blocks]
+
+    # -- layout checks -------------------------------------------------------
+    def check_tensors(self, tensors):
+        """Raise ``ValueError`` unless ``tensors`` (one per block, shaped
+        ``(C, L, F2, F1, F0)``) have the dtype and the element strides the
+        plan was built for and live on a CUDA device.  The plan's offsets
+        are fixed at creation, so a tensor laid out differently would be
+        read and written at the wrong elements."""
+        want = "torch.float32" if self.dtype == "f32" else "torch.float64"
+        if len(tensors) != len(self.layout):
+            raise ValueError(f"plan has {len(self.layout)} blocks, got {len(tensors)} tensors")
+        for k, (t, b) in enumerate(zip(tensors, self.layout)):
+            n, h = b["n"], b["h"]
+            shape = (b["ncomp"], b["nlevels"], n[2] + 2 * h[2], n[1] + 2 * h[1],
+                     n[0] + 2 * h[0])
+            if tuple(t.shape) != shape:
+                raise ValueError(f"block {k}: shape {tuple(t.shape)}, plan expects {shape}")
+            if str(t.dtype) != want:
+                raise ValueError(f"block {k}: dtype {t.dtype}, plan expects {want}")
+            # strides matter only along axes with more than one element
+            pairs = [(4, b["stride"][0]), (3, b["stride"][1]), (2, b["stride"][2]),
+                     (1, b["level_stride"])]
+            for dim, s in pairs:
+                if shape[dim] > 1 and t.stride(dim) != s:
+                    raise ValueError(
+                        f"block {k}: stride {t.stride(dim)} along dim {dim}, the plan was "
+                        f"built for {s} (strides {tuple(t.stride())})")
+            if t.device.type != "cuda":
+                raise ValueError(f"block {k}: tensor on {t.device}, the plan runs on CUDA")
+
+    def apply_(self, tensors, form=BC_FORM_BATCHED, stream=None):
+        """In-place forward on per-block tensors, after :meth:`check_tensors`."""
+        self.check_tensors(tensors)
+        self.apply(slot_table(tensors), form, stream)
+        return tensors
+
+    def adjoint_(self, tensors, stream=None):
+        """In-place adjoint on per-block cotangent tensors laid out as the
+        plan's fields, after :meth:`check_tensors`."""
+        self.check_tensors(tensors)
+        self.adjoint(slot_table(tensors), stream)
+        return tensors
 
     # -- lifecycle -----------------------------------------------------------
     def close(self):
@@ -413,9 +457,12 @@ def box_stencil(ndim, radius=1):
 class BCFill:
     """``torch.autograd.Function`` of the in-place ghost fill of one plan.
 
-    Forward: ghosts <- A x_D + b in place (the inputs are marked dirty).
+    Forward: ghosts <- A x_D + b in place (the inputs are marked dirty);
+    the fields must have the plan's layout (:meth:`Plan.check_tensors`).
     Backward: x_D_bar = y_D_bar + A^T y_G_bar and x_G_bar = 0 on covered
-    ghosts, computed in place on a copy of the incoming cotangents.
+    ghosts, computed in place on copies of the incoming cotangents that are
+    laid out with the forward fields' strides, since the plan's element
+    offsets were built for those strides.
     """
 
     _fn = None
@@ -428,17 +475,24 @@ class BCFill:
             class _Fill(torch.autograd.Function):
                 @staticmethod
                 def forward(ctx, plan, *fields):
-                    table = slot_table(fields)
-                    plan.apply(table)
+                    plan.check_tensors(fields)
+                    plan.apply(slot_table(fields))
                     ctx.plan = plan
+                    ctx.layouts = [(f.size(), f.stride(), f.dtype, f.device) for f in fields]
                     ctx.mark_dirty(*fields)
                     return fields
 
                 @staticmethod
                 def backward(ctx, *grads):
-                    gs = [g.contiguous().clone() for g in grads]
-                    table = slot_table(gs)
-                    ctx.plan.adjoint(table)
+                    gs = []
+                    for g, (size, stride, dt, dev) in zip(grads, ctx.layouts):
+                        out = torch.empty_strided(size, stride, dtype=dt, device=dev)
+                        if g is None:
+                            out.zero_()
+                        else:
+                            out.copy_(g)
+                        gs.append(out)
+                    ctx.plan.adjoint_(gs)
                     return (None, *gs)
 
             cls._fn = _Fill

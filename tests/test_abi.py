@@ -214,3 +214,30 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         bc.load_library()
     with pytest.raises(RuntimeError):
         bc.plan_for_workload(synth.alg1_example())
+
+
+def test_tensor_layout_checks_on_the_host(lib):
+    """The tensor API compares shape, dtype and strides with the layout the
+    plan was built for before any device work (host-only plan, CPU
+    tensors: the layout is right, so only the device is refused)."""
+    import torch
+    w = synth.batching(nblocks=6, side_lo=4, side_hi=12, lev_lo=2, lev_hi=6, h=2,
+                       seed=5, dtype="f32")
+    outer = [torch.from_numpy(a.copy()) for a in w["fields"]]
+    inner = [torch.from_numpy(np.ascontiguousarray(a.transpose(0, 2, 3, 4, 1)))
+             .permute(0, 4, 1, 2, 3) for a in w["fields"]]
+    plan = bc.plan_for_workload(w, outer, {"host_only": 1})
+    with pytest.raises(ValueError, match="stride"):
+        plan.check_tensors(inner)
+    with pytest.raises(ValueError, match="dtype"):
+        plan.check_tensors([t.double() for t in outer])
+    with pytest.raises(ValueError, match="shape"):
+        plan.check_tensors([t[:, :1] for t in outer])
+    with pytest.raises(ValueError, match="cuda|CUDA"):
+        plan.check_tensors(outer)
+    # a plan built on the level-innermost strides accepts those
+    plan2 = bc.plan_for_workload(w, inner, {"host_only": 1})
+    with pytest.raises(ValueError, match="CUDA"):
+        plan2.check_tensors(inner)
+    with pytest.raises(ValueError, match="stride"):
+        plan2.check_tensors(outer)
