@@ -275,7 +275,35 @@ typedef struct bc_plan_opts {
                               over 4096 entries, or cubed-sphere rows
                               generated on the GPU in the same plan,
                               BC_ERR_UNSUPPORTED                             */
+  int32_t batch_mode;      /* how BC_FORM_BATCHED runs: 0 default
+                              (BC_BATCH_PERSISTENT), BC_BATCH_PERSISTENT or
+                              BC_BATCH_FAMILIES                             */
+  int32_t scalar_runs;     /* 1: contiguous runs move one 4- or 8-byte value
+                              per lane and load; 0 (default): 16-byte vectors,
+                              whatever the runs' alignment                   */
+  int32_t level_chunk;     /* levels one lane carries through a table row
+                              when levels are far apart in memory
+                              (interpolation, CSR and transpose rows): 0
+                              default (4), or 1, 2, 4, 8; the persistent
+                              launch takes at most 4                        */
 } bc_plan_opts;
+
+/* Execution of BC_FORM_BATCHED (bc_plan_opts.batch_mode). */
+typedef enum bc_batch_mode {
+  BC_BATCH_PERSISTENT = 1, /* one resident grid whose warps claim the work
+                              items of every kind from a device counter, the
+                              longest first; the adjoint's gather and zero
+                              pass run the same way.  The counter lives in
+                              the plan, one per stream: applies of one plan
+                              may run concurrently on different streams
+                              (up to 64 streams), and a captured graph uses
+                              the counter of the stream it was captured on,
+                              so it must not be replayed while an apply of
+                              the same plan runs on that stream             */
+  BC_BATCH_FAMILIES = 2    /* one plain-grid kernel per kernel family
+                              (structured, interpolation, CSR), forked onto
+                              plan-owned streams and joined                 */
+} bc_batch_mode;
 
 typedef struct bc_plan bc_plan;
 

@@ -17,6 +17,7 @@ LIB_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib")
 
 BC_F32, BC_F64 = 0, 1
 BC_FORM_BATCHED, BC_FORM_TYPEWIDE, BC_FORM_PER_BC = 0, 1, 2
+BC_BATCH_PERSISTENT, BC_BATCH_FAMILIES = 1, 2
 STATUS = {0: "BC_OK", 1: "BC_ERR_INVALID_ARG", 2: "BC_ERR_OVERLAP",
           3: "BC_ERR_COLUMN_NOT_DATA", 4: "BC_ERR_UNCOVERED",
           5: "BC_ERR_HALO_TOO_WIDE", 6: "BC_ERR_OUT_OF_RANGE",
@@ -58,7 +59,8 @@ class BcPlanOpts(ctypes.Structure):
     _fields_ = [("units_per_lane", c_i32), ("unit_order", c_i32),
                 ("threads", c_i32), ("ctas_per_sm", c_i32),
                 ("strict_cover", c_i32), ("no_adjoint", c_i32),
-                ("no_runs", c_i32), ("host_only", c_i32), ("ghost_sweeps", c_i32)]
+                ("no_runs", c_i32), ("host_only", c_i32), ("ghost_sweeps", c_i32),
+                ("batch_mode", c_i32), ("scalar_runs", c_i32), ("level_chunk", c_i32)]
 
 
 class BcStats(ctypes.Structure):

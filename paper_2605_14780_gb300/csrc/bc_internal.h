@@ -77,6 +77,7 @@ static_assert(sizeof(Item) % 16 == 0, "Item must be a multiple of 16 bytes");
 // Device-side view of a plan (passed by value to every kernel).
 struct Ctx {
   void* const* slots;       // caller's device array of slot pointers
+  int32_t vec_runs;         // 1: runs move 16-byte vectors (runs_vec)
   const int32_t* slot_ls;   // level stride of every slot (elements)
   // cell tables, one row per cell of every sub-matrix box: the element
   // offset of the ghost cell (level 0) and, for maps, of its source cell
@@ -113,6 +114,8 @@ struct Ctx {
 // rotated pairs FAM_INTERP; CSR rows FAM_CSR; the transpose gather FAM_ADJ.
 enum Family : int32_t { FAM_STRUCT = 0, FAM_INTERP = 1, FAM_CSR = 2, FAM_ADJ = 3 };
 constexpr int kFamilies = 4;
+// the persistent work-list kernel that runs every forward kind
+constexpr int FAM_ALL = 4;
 
 // Launcher (kernels.cu).  dtype: 0 = float, 1 = double.  One warp per item,
 // `threads` per CTA (32..512).  grid <= 0: a plain grid with one warp per
@@ -123,6 +126,13 @@ cudaError_t launch_family(int dtype, int family, const Ctx& ctx,
                           cudaStream_t s);
 // CTAs of one family kernel that fit on an SM at once.
 int resident_ctas(int dtype, int family, int threads);
+// Persistent work-list launch: ctas_per_sm resident CTAs per SM (0: as many
+// as fit) on `sms` SMs, whose warps claim the items through `counter`
+// (two words, zero before the launch and zero again after it).  family:
+// FAM_ALL (every forward kind), FAM_ADJ or FAM_STRUCT.
+cudaError_t launch_persistent(int dtype, int family, const Ctx& ctx, const Item* items,
+                              int nitems, int threads, int ctas_per_sm, int sms,
+                              unsigned* counter, cudaStream_t s);
 
 // Cubed-sphere geometry (geometry.cu).
 struct CsPanels {

@@ -14,6 +14,7 @@
 // lane keeps several independent values in flight; copies move integer bit
 // patterns so they are exact; table rows (stencils, CSR entries) are loaded
 // once per cell and level chunk.
+#include <climits>
 #include <cstddef>
 #include <cstdint>
 
@@ -217,10 +218,161 @@ __device__ void structured_runs(const Item& it, const Ptrs& P, const Ctx& c, int
   }
 }
 
+// ---------------------------------------------------------------------------
+// 16-byte vector runs.  The runs of an item (at most 32, one descriptor per
+// lane) are cut into destination-aligned 16-byte chunks -- E = 16 / S
+// elements, the first and last chunk of a run partly outside it -- and the
+// chunks of all runs form one sequence that the lanes take in order, lane t
+// chunk t, t + 32, ..., U chunks in flight per lane.  So a warp instruction
+// moves 512 contiguous bytes whatever the run lengths, and short runs do not
+// leave lanes idle.  The alignment of a run depends on the caller's slot
+// pointers, so it is worked out here: a chunk whose source is aligned the
+// same way loads one 16-byte vector, otherwise the two aligned vectors that
+// hold its elements and shifts them into place.  Every vector loaded holds
+// at least one element of its run (so no load leaves the field's
+// allocation); full chunks are stored as one vector, the chunks at the ends
+// of a run element by element, so no value outside a run is written.
+// ---------------------------------------------------------------------------
+constexpr int kVecUnroll = 4;
+constexpr int kNoChunk = INT_MIN;  // a lane's chunk slot past the item's last chunk
+
+enum RunOp : int { RUN_ZERO = 0, RUN_COPY = 1, RUN_ADD = 2 };
+
+// words [ws, ws + 4) of the 8 words (a, b), ws in 1..3
+__device__ __forceinline__ uint4 shift_words(const uint4& a, const uint4& b, int ws) {
+  uint4 r;
+  r.x = ws == 1 ? a.y : (ws == 2 ? a.z : a.w);
+  r.y = ws == 1 ? a.z : (ws == 2 ? a.w : b.x);
+  r.z = ws == 1 ? a.w : (ws == 2 ? b.x : b.y);
+  r.w = ws == 1 ? b.x : (ws == 2 ? b.y : b.z);
+  return r;
+}
+
+// bit pattern of element j (a constant after unrolling) of a 16-byte vector
+template <typename T>
+__device__ __forceinline__ typename BitsOf<T>::type vec_elem(const uint4& v, int j) {
+  if constexpr (sizeof(T) == 4) {
+    return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+  } else {
+    return j == 0 ? ((uint64_t)v.y << 32 | v.x) : ((uint64_t)v.w << 32 | v.z);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ uint4 add_vec(const uint4& a, const uint4& b) {
+  uint4 r;
+  if constexpr (sizeof(T) == 4) {
+    r.x = __float_as_uint(__uint_as_float(a.x) + __uint_as_float(b.x));
+    r.y = __float_as_uint(__uint_as_float(a.y) + __uint_as_float(b.y));
+    r.z = __float_as_uint(__uint_as_float(a.z) + __uint_as_float(b.z));
+    r.w = __float_as_uint(__uint_as_float(a.w) + __uint_as_float(b.w));
+  } else {
+    const double a0 = __hiloint2double((int)a.y, (int)a.x), a1 = __hiloint2double((int)a.w, (int)a.z);
+    const double b0 = __hiloint2double((int)b.y, (int)b.x), b1 = __hiloint2double((int)b.w, (int)b.z);
+    const double r0 = a0 + b0, r1 = a1 + b1;
+    r.x = (unsigned)__double2loint(r0);
+    r.y = (unsigned)__double2hiint(r0);
+    r.z = (unsigned)__double2loint(r1);
+    r.w = (unsigned)__double2hiint(r1);
+  }
+  return r;
+}
+
+// OP: RUN_ZERO (d = 0), RUN_COPY (d = s, bit patterns), RUN_ADD (d = d + s
+// in T; the adjoint of unit copies).  Runs {dst offset, src offset, length}.
+template <typename T, int OP>
+__device__ void runs_vec(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
+  using B = typename BitsOf<T>::type;
+  constexpr int E = 16 / (int)sizeof(T);
+  constexpr int LS = sizeof(T) == 4 ? 2 : 3;  // log2 of the element size
+  constexpr int WPE = (int)sizeof(T) / 4;     // 32-bit words per element
+  constexpr int U = kVecUnroll;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int nr = it.nunits;
+  int4 mine = make_int4(0, 0, 0, 0);
+  if (lane < nr) mine = __ldg(c.runs + it.u0 + lane);
+  B* dbase = static_cast<B*>(P.d);
+  const B* sbase = static_cast<const B*>(P.s);
+  const uint32_t dmis = (uint32_t)(reinterpret_cast<uintptr_t>(dbase) >> LS);
+  const uint32_t smis = (uint32_t)(reinterpret_cast<uintptr_t>(sbase) >> LS);
+  // chunks of this lane's run and their running count over the lanes
+  const int ad = (int)((dmis + (uint32_t)mine.x) & (E - 1));
+  const int nch = mine.z > 0 ? (mine.z + ad + E - 1) / E : 0;
+  int incl = nch;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int total = __shfl_sync(FULL, incl, 31);
+  const int excl = incl - nch;
+  for (int base = 0; base < total; base += 32 * U) {
+    uint4 v[U];
+    int dq[U], lo[U], hi[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int ch = base + lane + 32 * u;
+      // the run of chunk ch: the last lane whose first chunk is <= ch
+      int r = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int e = __shfl_sync(FULL, excl, r + step);
+        if (e <= ch) r += step;
+      }
+      const int rd = __shfl_sync(FULL, mine.x, r);
+      const int rs = __shfl_sync(FULL, mine.y, r);
+      const int rn = __shfl_sync(FULL, mine.z, r);
+      const int ra = __shfl_sync(FULL, ad, r);
+      const int re = __shfl_sync(FULL, excl, r);
+      const int e0 = (ch - re) * E - ra;  // run element in the chunk's first slot
+      lo[u] = max(0, -e0);
+      hi[u] = min(E, rn - e0);
+      dq[u] = ch < total ? rd + e0 : kNoChunk;  // may be negative: slots before the slot base
+      v[u] = make_uint4(0u, 0u, 0u, 0u);
+      if (OP != RUN_ZERO && ch < total) {
+        const int s0 = rs + e0;
+        const int sa = (int)((smis + (uint32_t)s0) & (E - 1));
+        const uint4* sp = reinterpret_cast<const uint4*>(sbase + (s0 - sa));
+        if (sa == 0) {
+          v[u] = __ldg(sp);
+        } else {
+          uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a;
+          if (sa + lo[u] < E) a = __ldg(sp);
+          if (sa + hi[u] > E) b = __ldg(sp + 1);
+          v[u] = shift_words(a, b, sa * WPE);
+        }
+      }
+    }
+    if (OP == RUN_ADD) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (dq[u] != kNoChunk) {
+          const uint4 x = *reinterpret_cast<const uint4*>(dbase + dq[u]);
+          v[u] = add_vec<T>(x, v[u]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (dq[u] == kNoChunk) continue;
+      B* d = dbase + dq[u];
+      if (lo[u] == 0 && hi[u] == E) {
+        *reinterpret_cast<uint4*>(d) = v[u];
+      } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j)
+          if (j >= lo[u] && j < hi[u]) d[j] = vec_elem<T>(v[u], j);
+      }
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void structured_flat(const Item& it, const Ptrs& P, const Ctx& c,
                                                 int lane) {
-  if (it.mode == MODE_RUNS)
+  if (it.mode == MODE_RUNS && c.vec_runs)
+    it.kind == IK_MAP ? runs_vec<T, RUN_COPY>(it, P, c, lane)
+                      : runs_vec<T, RUN_ZERO>(it, P, c, lane);
+  else if (it.mode == MODE_RUNS)
     structured_runs<T>(it, P, c, lane);
   else if (it.mode == MODE_FLAT_LEVEL)
     structured_flat_t<T, true>(it, P, c, lane);
@@ -232,7 +384,9 @@ __device__ __forceinline__ void structured_flat(const Item& it, const Ptrs& P, c
 // interpolation rows (user Itp, Sec. III-B) with optional 2x2 rotation of a
 // covariant component pair (Sec. V-A): y = M (sum_k w_k x_u, sum_k w_k x_v)
 // ---------------------------------------------------------------------------
-template <typename T>
+// CH: the most levels of one unit (the arrays of a lane); the item's mode
+// (its chunk length, <= CH) is the levels-per-lane split the plan chose.
+template <typename T, int CH>
 __device__ void interp_scalar_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
   using B = typename BitsOf<T>::type;
   const int end = it.u0 + it.nunits;
@@ -254,38 +408,38 @@ __device__ void interp_scalar_chunk(const Item& it, const Ptrs& P, const Ctx& c,
     if (ix.w & kFlagSnap) {  // unit row: exact copy of node 0
       const B* s = reinterpret_cast<const B*>(x);
       B* db = reinterpret_cast<B*>(d);
-      B v[kInterpChunk];
+      B v[CH];
 #pragma unroll
-      for (int l = 0; l < kInterpChunk; ++l)
+      for (int l = 0; l < CH; ++l)
         if (l < nl) v[l] = ldg(s + l * sls);
 #pragma unroll
-      for (int l = 0; l < kInterpChunk; ++l)
+      for (int l = 0; l < CH; ++l)
         if (l < nl) db[l * ls] = v[l];
       continue;
     }
     const T* wr = static_cast<const T*>(c.itp_w) + row * kPMax;
-    T acc[kInterpChunk];
+    T acc[CH];
 #pragma unroll
-    for (int l = 0; l < kInterpChunk; ++l) acc[l] = T(0);
+    for (int l = 0; l < CH; ++l) acc[l] = T(0);
 #pragma unroll
     for (int n = 0; n < kPMax; ++n) {
       if (n < p) {
         const T w = ldg(wr + n);
         const T* xn = x + n * ix.z;
 #pragma unroll
-        for (int l = 0; l < kInterpChunk; ++l)
+        for (int l = 0; l < CH; ++l)
           if (l < nl) acc[l] = fma(w, ldg(xn + l * sls), acc[l]);
       }
     }
 #pragma unroll
-    for (int l = 0; l < kInterpChunk; ++l)
+    for (int l = 0; l < CH; ++l)
       if (l < nl) d[l * ls] = acc[l];
   }
 }
 
-template <typename T>
+template <typename T, int CH>
 __device__ void interp_pair_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
-  constexpr int LU = kInterpChunk / 2;
+  constexpr int LU = CH / 2;
   const int end = it.u0 + it.nunits;
   const int ls = it.dst_ls;
   const int p = it.p;
@@ -446,9 +600,15 @@ __device__ __forceinline__ void load_ell(const Ctx& c, int e0, bool common, int 
 #pragma unroll
   for (int j = 0; j < W / N; ++j) {
     const V v = __ldg(a4 + j);
-    const T* t = reinterpret_cast<const T*>(&v);
-#pragma unroll
-    for (int k = 0; k < N; ++k) a[N * j + k] = t[k];
+    if constexpr (N == 4) {
+      a[4 * j] = v.x;
+      a[4 * j + 1] = v.y;
+      a[4 * j + 2] = v.z;
+      a[4 * j + 3] = v.w;
+    } else {
+      a[2 * j] = v.x;
+      a[2 * j + 1] = v.y;
+    }
   }
   if (!common) {
     const int4* s4 = reinterpret_cast<const int4*>(c.csr_slot + e0);
@@ -503,7 +663,7 @@ __device__ void csr_flat_w(const Item& it, const Ptrs& P, const Ctx& c, int lane
 }
 
 // A cell times a chunk of levels per lane, a whole ELL row of width W.
-template <typename T, int W>
+template <typename T, int W, int CH>
 __device__ void csr_chunk_w(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
   const int end = it.u0 + it.nunits;
   const int ls = it.dst_ls;
@@ -522,9 +682,9 @@ __device__ void csr_chunk_w(const Item& it, const Ptrs& P, const Ctx& c, int lan
     load_ell<T, W>(c, it.src_org + q * W, common, off, a, slot);
     T* d = static_cast<T*>(P.d) + (dst_cell(it, c, q) + l0 * ls);
     const T rhs = ldg(static_cast<const T*>(c.csr_rhs) + row);
-    T acc[kChunk];
+    T acc[CH];
 #pragma unroll
-    for (int l = 0; l < kChunk; ++l) acc[l] = T(0);
+    for (int l = 0; l < CH; ++l) acc[l] = T(0);
     if (common) {  // padding entries read offset 0 of the slot, dropped below
       const int sls = it.src_ls;
 #pragma unroll
@@ -532,7 +692,7 @@ __device__ void csr_chunk_w(const Item& it, const Ptrs& P, const Ctx& c, int lan
         const T* xs = sb + (off[j] + l0 * sls);
         const T aj = j < nnz ? a[j] : T(0);
 #pragma unroll
-        for (int l = 0; l < kChunk; ++l)
+        for (int l = 0; l < CH; ++l)
           if (l < nl) {
             const T xv = ldg(xs + l * sls);
             acc[l] = j < nnz ? fma(aj, xv, acc[l]) : acc[l];
@@ -545,12 +705,12 @@ __device__ void csr_chunk_w(const Item& it, const Ptrs& P, const Ctx& c, int lan
           const int sls = __ldg(c.slot_ls + slot[j]);
           const T* xs = static_cast<const T*>(c.slots[slot[j]]) + (off[j] + l0 * sls);
 #pragma unroll
-          for (int l = 0; l < kChunk; ++l)
+          for (int l = 0; l < CH; ++l)
             if (l < nl) acc[l] = fma(a[j], ldg(xs + l * sls), acc[l]);
         }
     }
 #pragma unroll
-    for (int l = 0; l < kChunk; ++l)
+    for (int l = 0; l < CH; ++l)
       if (l < nl) d[l * ls] = acc[l] + rhs;
   }
 }
@@ -560,7 +720,7 @@ __device__ void csr_chunk_w(const Item& it, const Ptrs& P, const Ctx& c, int lan
 // latencies per E entries instead of two per entry.
 constexpr int kCsrBatch = 8;
 
-template <typename T>
+template <typename T, int CH>
 __device__ void csr_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
   constexpr int E = kCsrBatch;
   const int end = it.u0 + it.nunits;
@@ -577,9 +737,9 @@ __device__ void csr_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane)
     const int nnz = __ldg(c.csr_nnz + row);
     const int e0 = it.src_org + q * W;
     T* d = static_cast<T*>(P.d) + (dst_cell(it, c, q) + l0 * ls);
-    T acc[kChunk];
+    T acc[CH];
 #pragma unroll
-    for (int l = 0; l < kChunk; ++l) acc[l] = T(0);
+    for (int l = 0; l < CH; ++l) acc[l] = T(0);
     for (int eb = 0; eb < nnz; eb += E) {
       const T* xs[E];
       int sl[E];
@@ -594,13 +754,13 @@ __device__ void csr_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane)
       for (int e = 0; e < E; ++e)
         if (eb + e < nnz) {
 #pragma unroll
-          for (int l = 0; l < kChunk; ++l)
+          for (int l = 0; l < CH; ++l)
             if (l < nl) acc[l] = fma(a[e], ldg(xs[e] + l * sl[e]), acc[l]);
         }
     }
     const T rhs = ldg(static_cast<const T*>(c.csr_rhs) + row);
 #pragma unroll
-    for (int l = 0; l < kChunk; ++l)
+    for (int l = 0; l < CH; ++l)
       if (l < nl) d[l * ls] = acc[l] + rhs;
   }
 }
@@ -642,7 +802,7 @@ __device__ void csr_flat(const Item& it, const Ptrs& P, const Ctx& c, int lane) 
 // ---------------------------------------------------------------------------
 constexpr int kAdjBatch = 4;
 
-template <typename T>
+template <typename T, int CH>
 __device__ void adj_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
   constexpr int E = kAdjBatch;
   const int end = it.u0 + it.nunits;
@@ -657,9 +817,9 @@ __device__ void adj_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane)
     const int ls = it.dst_ls;
     T* xb = static_cast<T*>(P.d) + (__ldg(c.arow_off + r) + l0 * ls);
     const int e0 = (int)__ldg(c.adj_ptr + r), e1 = (int)__ldg(c.adj_ptr + r + 1);
-    T acc[kChunk];
+    T acc[CH];
 #pragma unroll
-    for (int l = 0; l < kChunk; ++l) acc[l] = (l < nl) ? xb[l * ls] : T(0);
+    for (int l = 0; l < CH; ++l) acc[l] = (l < nl) ? xb[l * ls] : T(0);
     for (int eb = e0; eb < e1; eb += E) {
       const T* ys[E];
       int gl[E];
@@ -683,12 +843,12 @@ __device__ void adj_chunk(const Item& it, const Ptrs& P, const Ctx& c, int lane)
       for (int e = 0; e < E; ++e)
         if (eb + e < e1) {
 #pragma unroll
-          for (int l = 0; l < kChunk; ++l)
+          for (int l = 0; l < CH; ++l)
             if (l < nl) acc[l] = fma(a[e], ys[e][l * gl[e]], acc[l]);
         }
     }
 #pragma unroll
-    for (int l = 0; l < kChunk; ++l)
+    for (int l = 0; l < CH; ++l)
       if (l < nl) xb[l * ls] = acc[l];
   }
 }
@@ -731,46 +891,82 @@ __device__ void adj_flat(const Item& it, const Ptrs& P, const Ctx& c, int lane) 
 
 // Kernel families: one kernel per family keeps each family's register
 // budget (and so its occupancy) independent of the others.
-template <typename T, int FAM>
+template <typename T, int FAM, int MAXCH>
 __device__ __forceinline__ void run_item(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
   const bool flat = it.mode < 2;
+  const bool ch8 = MAXCH > 4 && it.mode > 4;  // level chunks of up to 8
   if constexpr (FAM == FAM_STRUCT) {
     structured_flat<T>(it, P, c, lane);
   } else if constexpr (FAM == FAM_INTERP) {
     if (it.kind == IK_INTERP_PAIR) {
       if (flat)
         interp_flat<T, true>(it, P, c, lane);
+      else if (ch8)
+        interp_pair_chunk<T, (MAXCH > 4 ? 8 : 4)>(it, P, c, lane);
       else
-        interp_pair_chunk<T>(it, P, c, lane);
+        interp_pair_chunk<T, 4>(it, P, c, lane);
     } else {
       if (flat)
         interp_flat<T, false>(it, P, c, lane);
+      else if (ch8)
+        interp_scalar_chunk<T, (MAXCH > 4 ? 8 : 4)>(it, P, c, lane);
       else
-        interp_scalar_chunk<T>(it, P, c, lane);
+        interp_scalar_chunk<T, 4>(it, P, c, lane);
     }
   } else if constexpr (FAM == FAM_CSR) {
     if (it.p == 8) {
       if (flat)
         csr_flat_w<T, 8>(it, P, c, lane);
+      else if (ch8)
+        csr_chunk_w<T, 8, (MAXCH > 4 ? 8 : 4)>(it, P, c, lane);
       else
-        csr_chunk_w<T, 8>(it, P, c, lane);
+        csr_chunk_w<T, 8, 4>(it, P, c, lane);
     } else if (it.p == 4) {
       if (flat)
         csr_flat_w<T, 4>(it, P, c, lane);
+      else if (ch8)
+        csr_chunk_w<T, 4, (MAXCH > 4 ? 8 : 4)>(it, P, c, lane);
       else
-        csr_chunk_w<T, 4>(it, P, c, lane);
+        csr_chunk_w<T, 4, 4>(it, P, c, lane);
     } else if (flat) {
       csr_flat<T>(it, P, c, lane);
+    } else if (ch8) {
+      csr_chunk<T, (MAXCH > 4 ? 8 : 4)>(it, P, c, lane);
     } else {
-      csr_chunk<T>(it, P, c, lane);
+      csr_chunk<T, 4>(it, P, c, lane);
     }
   } else {
-    if (it.kind == IK_ADD)
+    if (it.kind == IK_ADD && c.vec_runs)
+      runs_vec<T, RUN_ADD>(it, P, c, lane);
+    else if (it.kind == IK_ADD)
       add_runs<T>(it, P, c, lane);
     else if (flat)
       adj_flat<T>(it, P, c, lane);
+    else if (ch8)
+      adj_chunk<T, (MAXCH > 4 ? 8 : 4)>(it, P, c, lane);
     else
-      adj_chunk<T>(it, P, c, lane);
+      adj_chunk<T, 4>(it, P, c, lane);
+  }
+}
+
+// All forward item kinds in one kernel (the persistent work-list launch):
+// dispatch on the item's kind.  That kernel holds level chunks of at most 4
+// (the plan cuts its units so), which keeps its register budget; the family
+// kernels take chunks of up to 8.
+template <typename T, int FAM>
+__device__ __forceinline__ void run_work(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
+  if constexpr (FAM == FAM_ALL) {
+    switch (it.kind) {
+      case IK_ZERO:
+      case IK_CONST:
+      case IK_MAP: run_item<T, FAM_STRUCT, 4>(it, P, c, lane); break;
+      case IK_INTERP:
+      case IK_INTERP_PAIR: run_item<T, FAM_INTERP, 4>(it, P, c, lane); break;
+      case IK_CSR: run_item<T, FAM_CSR, 4>(it, P, c, lane); break;
+      default: run_item<T, FAM_ADJ, 4>(it, P, c, lane); break;
+    }
+  } else {
+    run_item<T, FAM, 8>(it, P, c, lane);
   }
 }
 
@@ -782,7 +978,14 @@ template <int FAM, int THREADS> struct Occ {
 #ifndef BC_STRUCT_WARPS
 #define BC_STRUCT_WARPS 40
 #endif
-  static constexpr int kWarps = FAM == FAM_STRUCT ? BC_STRUCT_WARPS : 32;
+#ifndef BC_ALL_WARPS
+#define BC_ALL_WARPS 16
+#endif
+  // the persistent kernel of every kind carries the union of the paths:
+  // 16 warps per SM (128 registers) keep its CSR and transpose rows in
+  // registers, and each warp moves 16-byte vectors with several in flight
+  static constexpr int kWarps =
+      FAM == FAM_STRUCT ? BC_STRUCT_WARPS : (FAM == FAM_ALL ? BC_ALL_WARPS : 32);
   // resident CTAs asked of the register allocator: the warp budget in CTAs,
   // at least 1 and at most 32 (the SM's CTA limit)
   static constexpr int kBlocksRaw = (kWarps * 32) / THREADS;
@@ -821,7 +1024,7 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
   reinterpret_cast<int*>(&sit[warp])[lane] = w;
   const Ptrs P = gather_ptrs(lookup_slot(c, w, lane));
   __syncwarp();
-  run_item<T, FAM>(sit[warp], P, c, lane);
+  run_work<T, FAM>(sit[warp], P, c, lane);
 }
 
 // Streaming form: a grid of resident warps walks the items with a fixed
@@ -848,13 +1051,78 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     const int w_nxt2 = nxt2 < nitems ? __ldg(iw + (int64_t)nxt2 * 32 + lane) : 0;
     const Ptrs P = gather_ptrs(p_cur);
     __syncwarp();
-    run_item<T, FAM>(sit[warp], P, c, lane);
+    run_work<T, FAM>(sit[warp], P, c, lane);
     __syncwarp();
     if (nxt >= nitems) break;
     w_cur = w_nxt;
     p_cur = p_nxt;
     nxt = nxt2;
     w_nxt = w_nxt2;
+  }
+}
+
+// Persistent work-list form: a resident grid whose warps claim items from a
+// device counter (one atomic per item, issued by lane 0 while the warp still
+// works on an earlier item; nothing ever waits on another warp).  Three items
+// are in the pipeline of a warp: the one it works on, the next one (its slot
+// pointers already loaded) and the one after (its descriptor in flight), plus
+// the claim of a fourth.  A warp stops claiming at its first claim past the
+// end of the list; it then counts itself done, and the last warp of the
+// launch to do so puts both counters back to zero, so the next launch on the
+// stream (or the next replay of a captured graph) starts from item 0.  Items
+// are ordered longest first, so the last items claimed are the short ones.
+template <typename T, int THREADS, int FAM>
+__global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
+    k_persist(Ctx c, const Item* __restrict__ items, int nitems, unsigned* __restrict__ ctr) {
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ Item sit[THREADS / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int* iw = reinterpret_cast<const int*>(items);
+  const unsigned n = (unsigned)nitems;
+  bool more = true;
+  auto finish = [&](unsigned raw) -> unsigned {
+    if (!more) return n;
+    const unsigned v = __shfl_sync(FULL, raw, 0);
+    if (v >= n) more = false;
+    return v < n ? v : n;
+  };
+  auto issue = [&]() -> unsigned { return (more && lane == 0) ? atomicAdd(ctr, 1u) : 0u; };
+  auto words = [&](unsigned i) -> int { return i < n ? __ldg(iw + (size_t)i * 32 + lane) : 0; };
+  // prologue: the first three items
+  unsigned a = finish(issue());
+  int wa = words(a);
+  unsigned b = finish(issue());
+  int wb = words(b);
+  void* pa = a < n ? lookup_slot(c, wa, lane) : nullptr;
+  unsigned cn = finish(issue());
+  int wc = words(cn);
+  void* pb = b < n ? lookup_slot(c, wb, lane) : nullptr;
+  while (a < n) {
+    const unsigned raw = issue();  // claim of the fourth item, in flight
+    reinterpret_cast<int*>(&sit[warp])[lane] = wa;
+    const Ptrs P = gather_ptrs(pa);
+    __syncwarp();
+    run_work<T, FAM>(sit[warp], P, c, lane);
+    __syncwarp();
+    const unsigned d = finish(raw);
+    const int wd = words(d);
+    void* pc = cn < n ? lookup_slot(c, wc, lane) : nullptr;
+    a = b;
+    wa = wb;
+    pa = pb;
+    b = cn;
+    wb = wc;
+    pb = pc;
+    cn = d;
+    wc = wd;
+  }
+  if (lane == 0) {
+    __threadfence();
+    const unsigned warps = gridDim.x * (THREADS / 32);
+    if (atomicAdd(ctr + 1, 1u) == warps - 1) {
+      atomicExch(ctr, 0u);
+      atomicExch(ctr + 1, 0u);
+    }
   }
 }
 
@@ -868,6 +1136,45 @@ cudaError_t launch_t(const Ctx& c, const Item* items, int nitems, int grid,
   else
     k_stream<T, THREADS, FAM><<<grid < need ? grid : need, THREADS, 0, s>>>(c, items, nitems);
   return cudaGetLastError();
+}
+
+template <typename T, int THREADS, int FAM>
+cudaError_t persist_t(const Ctx& c, const Item* items, int nitems, int ctas_per_sm, int sms,
+                      unsigned* ctr, cudaStream_t s) {
+  int fit = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_persist<T, THREADS, FAM>, THREADS,
+                                                    0) != cudaSuccess || fit < 1)
+    fit = 1;
+  const int per_sm = ctas_per_sm > 0 ? (ctas_per_sm < fit ? ctas_per_sm : fit) : fit;
+  const int wpb = THREADS / 32;
+  const int need = (nitems + wpb - 1) / wpb;
+  const int grid = per_sm * sms < need ? per_sm * sms : need;
+  k_persist<T, THREADS, FAM><<<grid, THREADS, 0, s>>>(c, items, nitems, ctr);
+  return cudaGetLastError();
+}
+
+template <typename T, int FAM>
+cudaError_t persist_fam(const Ctx& c, const Item* items, int nitems, int threads,
+                        int ctas_per_sm, int sms, unsigned* ctr, cudaStream_t s) {
+  switch (threads) {
+    case 64: return persist_t<T, 64, FAM>(c, items, nitems, ctas_per_sm, sms, ctr, s);
+    case 128: return persist_t<T, 128, FAM>(c, items, nitems, ctas_per_sm, sms, ctr, s);
+    case 512: return persist_t<T, 512, FAM>(c, items, nitems, ctas_per_sm, sms, ctr, s);
+    default: return persist_t<T, 256, FAM>(c, items, nitems, ctas_per_sm, sms, ctr, s);
+  }
+}
+
+template <typename T>
+cudaError_t persist_any(int fam, const Ctx& c, const Item* items, int nitems, int threads,
+                        int ctas_per_sm, int sms, unsigned* ctr, cudaStream_t s) {
+  switch (fam) {
+    case FAM_STRUCT:
+      return persist_fam<T, FAM_STRUCT>(c, items, nitems, threads, ctas_per_sm, sms, ctr, s);
+    case FAM_ADJ:
+      return persist_fam<T, FAM_ADJ>(c, items, nitems, threads, ctas_per_sm, sms, ctr, s);
+    default:
+      return persist_fam<T, FAM_ALL>(c, items, nitems, threads, ctas_per_sm, sms, ctr, s);
+  }
 }
 
 template <typename T, int THREADS, int FAM>
@@ -931,6 +1238,15 @@ cudaError_t launch_family(int dtype, int family, const Ctx& ctx,
   if (nitems <= 0) return cudaSuccess;
   return dtype == 1 ? launch_any<double>(family, ctx, items, nitems, threads, grid, s)
                     : launch_any<float>(family, ctx, items, nitems, threads, grid, s);
+}
+
+cudaError_t launch_persistent(int dtype, int family, const Ctx& ctx, const Item* items,
+                              int nitems, int threads, int ctas_per_sm, int sms,
+                              unsigned* counter, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  return dtype == 1
+             ? persist_any<double>(family, ctx, items, nitems, threads, ctas_per_sm, sms, counter, s)
+             : persist_any<float>(family, ctx, items, nitems, threads, ctas_per_sm, sms, counter, s);
 }
 
 int resident_ctas(int dtype, int family, int threads) {

@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <string>
@@ -185,6 +186,7 @@ struct bc_plan {
   // work lists
   std::vector<Item> items, adj_items, adj_zero, adj_add;
   std::vector<Item> fam_items[kFamilies];  // batched form: per family, sub-matrix order
+  std::vector<Item> all_items;  // persistent form: every forward item, longest first
   std::vector<int> sub_begin, sub_end;
   int type_begin[5] = {0, 0, 0, 0, 0}, type_end[5] = {0, 0, 0, 0, 0};
   // device
@@ -205,6 +207,12 @@ struct bc_plan {
   }
   Item* d_adj = nullptr;
   Item* d_adj_zero = nullptr;
+  Item* d_all = nullptr;
+  // work counters of the persistent launches: one pair per stream that
+  // applies the plan (zero between launches)
+  unsigned* d_ctr = nullptr;
+  std::mutex ctr_mu;
+  std::vector<void*> ctr_streams;
   int num_sms = 1;
   bc_plan_opts opts{};
   bc_stats stats{};
@@ -833,10 +841,17 @@ int structured_mode(const bc_block& B, int order) {
   return levels_fastest(B, order) ? MODE_FLAT_LEVEL : MODE_FLAT_CELL;
 }
 
-int table_mode(const bc_block& B, int order) {
+int table_mode(const bc_block& B, int order, int chunk) {
   if (levels_fastest(B, order)) return MODE_FLAT_LEVEL;
-  if (B.nlevels == 1) return MODE_FLAT_CELL;
-  return std::min(B.nlevels, kChunk);
+  if (B.nlevels == 1 || chunk <= 1) return MODE_FLAT_CELL;
+  return std::min(B.nlevels, chunk);
+}
+
+// levels per unit of the chunked unit order (bc_plan_opts.level_chunk); the
+// persistent launch's kernel holds at most 4
+int level_chunk(const bc_plan* P) {
+  const int ch = P->opts.level_chunk;
+  return P->opts.batch_mode == BC_BATCH_PERSISTENT ? std::min(ch, 4) : ch;
 }
 
 // split the unit space into warp-sized items: vol * L single values (flat
@@ -985,12 +1000,9 @@ void build_items(bc_plan* P) {
       run_n[si] = nr;
     }
   }
+  const int chunk = level_chunk(P);
   auto table_emit = [&](std::vector<Item>& out, const Item& it, const bc_block& B, int vol) {
-    int mode = table_mode(B, P->opts.unit_order);
-    // interpolation units hold kInterpChunk levels (smaller per-lane arrays
-    // in the interpolation kernels)
-    if (mode >= 2 && (it.kind == IK_INTERP || it.kind == IK_INTERP_PAIR))
-      mode = std::min(mode, kInterpChunk);
+    const int mode = table_mode(B, P->opts.unit_order, chunk);
     emit_units(out, it, vol, B.nlevels, mode, mode < 2 ? per_table_flat_item : per_table_item);
   };
   std::vector<std::pair<int, std::vector<Item>>> per_sub(P->subs.size());
@@ -1087,6 +1099,29 @@ void build_items(bc_plan* P) {
     std::vector<Item> sorted(v.size());
     for (size_t t = 0; t < v.size(); ++t) sorted[t] = v[key[t].second];
     v.swap(sorted);
+  }
+  // persistent launch: every forward item, the most bytes first (values
+  // times the bytes a value moves: one store, plus the loads of its row)
+  {
+    auto bytes = [&](const Item& it) -> int64_t {
+      int64_t vals = work(it);
+      if (it.mode >= 2) vals *= it.mode;
+      switch (it.kind) {
+        case IK_ZERO:
+        case IK_CONST: return vals;
+        case IK_MAP: return 2 * vals;
+        case IK_INTERP: return vals * (2 + it.p / 2);
+        case IK_INTERP_PAIR: return vals * 2 * (2 + it.p / 2);
+        default: return vals * (1 + it.p);
+      }
+    };
+    std::vector<Item> all;
+    for (const auto& v : P->fam_items) all.insert(all.end(), v.begin(), v.end());
+    std::vector<std::pair<int64_t, size_t>> key(all.size());
+    for (size_t t = 0; t < all.size(); ++t) key[t] = {-bytes(all[t]), t};
+    std::stable_sort(key.begin(), key.end());
+    P->all_items.resize(all.size());
+    for (size_t t = 0; t < all.size(); ++t) P->all_items[t] = all[key[t].second];
   }
   // adjoint: the zero pass over every covered ghost value
   P->adj_zero.clear();
@@ -1280,6 +1315,9 @@ void build_transpose(bc_plan* P) {
 }
 
 // -- device upload -------------------------------------------------------------
+// streams one plan's persistent launches can run on at the same time
+constexpr int kCounterStreams = 64;
+
 struct Layout {
   size_t off = 0;
   size_t take(size_t bytes) {
@@ -1331,6 +1369,7 @@ bc_status upload_tables(bc_plan* P) {
   const size_t o_ycs = L.take(Y.cstage.size() * 4);
   const size_t o_ycw = L.take(Y.cw.size() * S);
   const size_t o_yst = L.take((size_t)Y.stage * S);
+  const size_t o_ctr = L.take(2 * kCounterStreams * sizeof(unsigned));  // zero
   std::vector<char> host(L.off + 256, 0);
   put_raw(host, o_yr, Y.row);
   put_raw(host, o_yp, Y.ptr);
@@ -1415,6 +1454,7 @@ bc_status upload_tables(bc_plan* P) {
   y.cstage = reinterpret_cast<const int32_t*>(b + o_ycs);
   y.cw = b + o_ycw;
   y.stage = b + o_yst;
+  P->d_ctr = reinterpret_cast<unsigned*>(b + o_ctr);
   return BC_OK;
 }
 
@@ -1430,8 +1470,10 @@ bc_status upload_work(bc_plan* P) {
   const size_t o_r = L.take(P->runs.size() * sizeof(int4));
   const size_t o_a = L.take(P->adj_items.size() * sizeof(Item));
   const size_t o_z = L.take(P->adj_zero.size() * sizeof(Item));
+  const size_t o_all = L.take(P->all_items.size() * sizeof(Item));
   std::vector<char> host(L.off + 256, 0);
   put_raw(host, o_i, P->items);
+  put_raw(host, o_all, P->all_items);
   for (int f = 0; f < kFamilies; ++f) put_raw(host, o_f[f], P->fam_items[f]);
   put_raw(host, o_r, P->runs);
   put_raw(host, o_a, P->adj_items);
@@ -1450,6 +1492,7 @@ bc_status upload_work(bc_plan* P) {
   P->ctx.runs = reinterpret_cast<const int4*>(b + o_r);
   P->d_adj = reinterpret_cast<Item*>(b + o_a);
   P->d_adj_zero = reinterpret_cast<Item*>(b + o_z);
+  P->d_all = reinterpret_cast<Item*>(b + o_all);
   return BC_OK;
 }
 
@@ -1522,7 +1565,10 @@ void compute_stats(bc_plan* P) {
   st.units_per_lane = P->opts.units_per_lane;
   const int ys = P->sync_ctx.nrows > 0 ? 2 : 0;
   st.launches_fwd = ys;
-  for (const auto& v : P->fam_items) st.launches_fwd += v.empty() ? 0 : 1;
+  if (P->opts.batch_mode == BC_BATCH_PERSISTENT)
+    st.launches_fwd += P->all_items.empty() ? 0 : 1;
+  else
+    for (const auto& v : P->fam_items) st.launches_fwd += v.empty() ? 0 : 1;
   st.launches_adj = P->has_adjoint ? ys + !P->adj_items.empty() + !P->adj_zero.empty() : 0;
 }
 
@@ -1541,6 +1587,14 @@ bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
     return fail(BC_ERR_INVALID_ARG, "bad work-item options");
   if (o.ghost_sweeps < 0 || o.ghost_sweeps > kMaxGhostSweeps)
     return fail(BC_ERR_INVALID_ARG, "ghost_sweeps must be in 0..%d", kMaxGhostSweeps);
+  if (o.batch_mode == 0) o.batch_mode = BC_BATCH_PERSISTENT;
+  if (o.batch_mode != BC_BATCH_PERSISTENT && o.batch_mode != BC_BATCH_FAMILIES)
+    return fail(BC_ERR_INVALID_ARG, "batch_mode must be 0, BC_BATCH_PERSISTENT or BC_BATCH_FAMILIES");
+  if (o.scalar_runs < 0 || o.scalar_runs > 1)
+    return fail(BC_ERR_INVALID_ARG, "scalar_runs must be 0 or 1");
+  if (o.level_chunk == 0) o.level_chunk = 4;
+  if (o.level_chunk != 1 && o.level_chunk != 2 && o.level_chunk != 4 && o.level_chunk != 8)
+    return fail(BC_ERR_INVALID_ARG, "level_chunk must be 0, 1, 2, 4 or 8");
   return BC_OK;
 }
 
@@ -1723,11 +1777,27 @@ int stream_grid(const bc_plan* P, int fam) {
   return std::min(P->opts.ctas_per_sm, fit) * P->num_sms;
 }
 
+// The persistent launches' counter pair of `stream`, or nullptr when every
+// pair is already bound to another stream.
+unsigned* counter_for(bc_plan* P, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lock(P->ctr_mu);
+  void* key = static_cast<void*>(stream);
+  for (size_t i = 0; i < P->ctr_streams.size(); ++i)
+    if (P->ctr_streams[i] == key) return P->d_ctr + 2 * i;
+  if ((int)P->ctr_streams.size() >= kCounterStreams) return nullptr;
+  P->ctr_streams.push_back(key);
+  return P->d_ctr + 2 * (P->ctr_streams.size() - 1);
+}
+
 bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t s) {
   Ctx c = P->ctx;
   c.slots = slots;
+  c.vec_runs = P->opts.scalar_runs ? 0 : 1;
   cudaError_t e = cudaSuccess;
   const int T = P->opts.threads;
+  unsigned* ctr = nullptr;
+  if (form == BC_FORM_BATCHED && P->opts.batch_mode == BC_BATCH_PERSISTENT)
+    ctr = counter_for(P, s);
   // Sync rows read the input data: evaluate them into the staging buffer
   // while the ghost kernels run (they write only ghosts), write them back
   // after every kernel that reads data has run
@@ -1735,7 +1805,20 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
   if (sync && form != BC_FORM_BATCHED &&
       (e = launch_sync(P->dtype, SYNC_ROWS, P->sync_ctx, slots, c.slot_ls, s)) != cudaSuccess)
     return cuda_fail(e, "Sync rows");
-  if (form == BC_FORM_BATCHED) {
+  if (ctr) {
+    // one persistent launch over every item; the Sync rows beside it
+    cudaStream_t ys = P->aux[kFamilies - 2];
+    if (sync) {
+      if ((e = cudaEventRecord(P->ev_fork, s)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(ys, P->ev_fork, 0)) != cudaSuccess ||
+          (e = launch_sync(P->dtype, SYNC_ROWS, P->sync_ctx, slots, c.slot_ls, ys)) != cudaSuccess ||
+          (e = cudaEventRecord(P->ev_join[kFamilies - 2], ys)) != cudaSuccess)
+        return cuda_fail(e, "Sync rows");
+    }
+    e = launch_persistent(P->dtype, FAM_ALL, c, P->d_all, (int)P->all_items.size(), T,
+                          P->opts.ctas_per_sm, P->num_sms, ctr, s);
+    if (sync && e == cudaSuccess) e = cudaStreamWaitEvent(s, P->ev_join[kFamilies - 2], 0);
+  } else if (form == BC_FORM_BATCHED) {
     // one launch per kernel family, the families side by side
     int fams[kFamilies], nf = 0;
     for (int f = 0; f < kFamilies; ++f)
@@ -2302,6 +2385,7 @@ bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs, void* stream) 
   if (!slot_ptrs && plan->nslots > 0) return fail(BC_ERR_INVALID_ARG, "slot_ptrs is NULL");
   Ctx c = plan->ctx;
   c.slots = slot_ptrs;
+  c.vec_runs = plan->opts.scalar_runs ? 0 : 1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int T = plan->opts.threads;
   // Sync rows: their data cells' cotangents move to the staging buffer
@@ -2487,6 +2571,7 @@ bc_status bc_plan_check_work(const bc_plan* plan, int64_t* values, int64_t* prob
   }
   int64_t n = check_forward_list(W, items);
   n += check_forward_list(W, fam);
+  n += check_forward_list(W, plan->all_items);
   if (plan->has_adjoint) n += check_adjoint_lists(W, adj);
   n += check_sync(W);
   *values = n;

@@ -34,10 +34,24 @@ def test_hpcg_small(variant, n):
 def test_hpcg_128_full(variant):
     """The 128^3 HPCG-like block, checked in full and through the 27-point
     operator applied to the ghost-filled array."""
+    from oracle.operator import apply
     w = synth.hpcg_block(128, variant, seed=2)
     _, out = run(w)
     op, nexact, _ = compare(w, out)
     assert nexact == len(op.rows) == 130 ** 3 - 128 ** 3
+    # the 27-point operator (diagonal 26, off-diagonals -1) on the GPU's and
+    # on the oracle's ghost-filled arrays
+    ref = apply(op, w["fields"])
+
+    def stencil27(full):
+        x = full[0, 0]
+        box = np.zeros((128, 128, 128))
+        for dk in range(3):
+            for dj in range(3):
+                for di in range(3):
+                    box += x[dk:dk + 128, dj:dj + 128, di:di + 128]
+        return 27.0 * x[1:-1, 1:-1, 1:-1] - box
+    assert np.array_equal(stencil27(out[0].astype(np.float64)), stencil27(ref[0]))
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
@@ -66,7 +80,8 @@ def test_forms_bit_identical(form):
     {"ctas_per_sm": 0, "threads": 128, "units_per_lane": 64},
 ])
 def test_persistent_and_item_shapes(opts):
-    """Persistent grid with an atomic work counter, repeated launches (the
+    """The persistent work-list launch (warps claim items from a device
+    counter) with several resident-grid sizes, repeated launches (the
     counter must reset itself), odd item shapes."""
     w = synth.batching(nblocks=64, side_lo=4, side_hi=64, lev_lo=1, lev_hi=40,
                        h=2, seed=8, dtype="f32")
