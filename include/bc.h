@@ -276,30 +276,33 @@ typedef struct bc_plan_opts {
                               generated on the GPU in the same plan,
                               BC_ERR_UNSUPPORTED                             */
   int32_t batch_mode;      /* how BC_FORM_BATCHED runs: 0 default
-                              (BC_BATCH_PERSISTENT), BC_BATCH_PERSISTENT or
-                              BC_BATCH_FAMILIES                             */
+                              (BC_BATCH_FAMILIES), BC_BATCH_PERSISTENT or
+                              BC_BATCH_FAMILIES; bc_plan_autotune times both */
   int32_t scalar_runs;     /* 1: contiguous runs move one 4- or 8-byte value
                               per lane and load; 0 (default): 16-byte vectors,
                               whatever the runs' alignment                   */
   int32_t level_chunk;     /* levels one lane carries through a table row
                               when levels are far apart in memory
                               (interpolation, CSR and transpose rows): 0
-                              default (4), or 1, 2, 4, 8; the persistent
-                              launch takes at most 4                        */
+                              default (4 for interpolation rows, 8 for CSR
+                              and transpose rows), or 1, 2, 4, 8 for all;
+                              the persistent launch takes at most 4         */
+  int32_t unstaged_interp; /* 1: interpolation rows read their nodes from
+                              global memory lane by lane; 0 (default): with
+                              levels far apart in memory, a warp first
+                              copies the small box of neighbour cells a tile
+                              of 32 ghost cells reads into shared memory    */
 } bc_plan_opts;
 
 /* Execution of BC_FORM_BATCHED (bc_plan_opts.batch_mode). */
 typedef enum bc_batch_mode {
   BC_BATCH_PERSISTENT = 1, /* one resident grid whose warps claim the work
                               items of every kind from a device counter, the
-                              longest first; the adjoint's gather and zero
-                              pass run the same way.  The counter lives in
-                              the plan, one per stream: applies of one plan
-                              may run concurrently on different streams
-                              (up to 64 streams), and a captured graph uses
-                              the counter of the stream it was captured on,
-                              so it must not be replayed while an apply of
-                              the same plan runs on that stream             */
+                              longest first.  The counter (zero between
+                              launches: the last warp resets it) lives in
+                              the plan, one per stream the plan is applied
+                              on; past 64 streams an apply runs as
+                              BC_BATCH_FAMILIES                             */
   BC_BATCH_FAMILIES = 2    /* one plain-grid kernel per kernel family
                               (structured, interpolation, CSR), forked onto
                               plan-owned streams and joined                 */
@@ -402,10 +405,21 @@ bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs,
                         void* stream);
 
 /*
- * Time the candidate work-item shapes and launch forms on the caller's
- * fields (slot_ptrs, device array) and keep the fastest for BC_FORM_BATCHED.
- * Overwrites the covered ghosts (with the operator's own result).  Allocates
- * a temporary L2-flush buffer; synchronises the stream.
+ * Time candidate executions of BC_FORM_BATCHED on the caller's fields
+ * (slot_ptrs, device array) and keep the fastest: the batch mode, the
+ * scalar or vector runs, the work per item (units_per_lane), the threads
+ * per CTA, the levels-per-lane split (level_chunk, when the plan has
+ * chunked units) and the resident CTAs per SM of the persistent launch,
+ * searched one option at a time from the plan's own options (median of
+ * six launches, each after an L2 flush).  Overwrites the covered ghosts
+ * (with the operator's own result).  Allocates a temporary L2-flush buffer;
+ * synchronises the stream.
+ *
+ * Result cache: the choice is remembered under a hash of the plan's rows,
+ * layouts and options, the device's name and SM count, for the rest of the
+ * process; with BC_AUTOTUNE_CACHE=<file> in the environment it is also
+ * read from and appended to that text file (one line per plan), so a later
+ * process applies the stored choice without timing anything.
  */
 bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs,
                            void* stream);
@@ -475,13 +489,13 @@ bc_status bc_plan_export_csr(const bc_plan* plan, int64_t* nrows,
  * Cubed-sphere interpolation stencils without any device allocation.
  *
  * The paper has no counterpart: this is a convenience for callers that cannot
- * call cudaMalloc -- code running while a stream capture in global mode is
- * active, or inside a framework that owns all device memory through its own
- * pool and forbids raw allocations.  bc_plan_create allocates device tables
- * and staging buffers, so such callers cannot build a plan at that moment;
- * this call still gives them the rows the plan's GPU geometry kernel would
- * generate for BC_GEOM_CUBED_SPHERE sub-matrices (same FP64 geometry, same
- * snapping and stencil rules), written to HOST arrays.
+ * call cudaMalloc -- code inside a framework that owns all device memory
+ * through its own pool and forbids raw allocations, or that runs under a
+ * fixed device-memory budget.  bc_plan_create allocates device tables and
+ * staging buffers, so such callers cannot build a plan; this call still
+ * gives them the rows the plan's GPU geometry kernel generates for
+ * BC_GEOM_CUBED_SPHERE sub-matrices (the same device function computes
+ * both: FP64 geometry, snapping and stencil rules), written to HOST arrays.
  *
  * The kernel's scratch (results and an error word) lives in one fixed device
  * array inside the library, sized for BC_NOALLOC_MAX_CELLS cells (about
@@ -501,13 +515,18 @@ bc_status bc_plan_export_csr(const bc_plan* plan, int64_t* nrows,
  *                    (filled only when rot is not NULL)
  * Errors: BC_ERR_INVALID_ARG (p outside 1..8, h < 1, N < p, h > N, NULL
  * output), BC_ERR_UNSUPPORTED (24*N*h > BC_NOALLOC_MAX_CELLS),
- * BC_ERR_GEOMETRY, BC_ERR_CUDA.
- * Synchronous on the legacy default stream of the current device.  The
- * first call on a device looks up the scratch array's device address there;
- * make that first call before any stream capture begins.  All calls share
- * the one scratch array and it keeps the last call's results: calls that
- * overlap on the GPU (several host threads, or processes sharing a context)
- * race with each other.
+ * BC_ERR_GEOMETRY, BC_ERR_CUDA.  After any status other than BC_OK the
+ * contents of the output arrays are undefined.
+ * Synchronous: it uses the legacy default stream of the current device and
+ * returns when the results are on the host.  The first call on a device
+ * looks up the scratch array's device address there (with that device
+ * current) and keeps it for later calls; make that first call before any
+ * stream capture begins.  The address belongs to the device's primary
+ * context, so a cudaDeviceReset between calls is not supported.  All calls
+ * share the one scratch array and it keeps the last call's results (the
+ * error word is cleared by every call): calls that overlap on the GPU
+ * (several host threads, or processes sharing a context) race with each
+ * other.
  */
 #define BC_NOALLOC_MAX_CELLS 65536
 #define BC_NOALLOC_SNAP 0x100

@@ -60,7 +60,8 @@ class BcPlanOpts(ctypes.Structure):
                 ("threads", c_i32), ("ctas_per_sm", c_i32),
                 ("strict_cover", c_i32), ("no_adjoint", c_i32),
                 ("no_runs", c_i32), ("host_only", c_i32), ("ghost_sweeps", c_i32),
-                ("batch_mode", c_i32), ("scalar_runs", c_i32), ("level_chunk", c_i32)]
+                ("batch_mode", c_i32), ("scalar_runs", c_i32), ("level_chunk", c_i32),
+                ("unstaged_interp", c_i32)]
 
 
 class BcStats(ctypes.Structure):

@@ -53,7 +53,20 @@ struct FastDiv {
 //                   contiguous in the destination and (maps) in the source;
 //                   units [u0, u0 + nunits) index the run table (at most 32
 //                   runs) and Item::p lanes (a power of two) share one run
-enum ItemMode : int32_t { MODE_RUNS = -1, MODE_FLAT_CELL = 0, MODE_FLAT_LEVEL = 1 };
+//   MODE_TILE       interpolation items with levels far apart in memory:
+//                   the cells' nodes lie in one small box of the source
+//                   block, which the warp first copies to shared memory
+//                   (cp.async) for its levels and components; the rows then
+//                   read their nodes there (Item::l0 ... bwid, itp_box)
+enum ItemMode : int32_t { MODE_TILE = -2, MODE_RUNS = -1, MODE_FLAT_CELL = 0, MODE_FLAT_LEVEL = 1 };
+
+// itp_box row of a staged interpolation cell: node 0's index in the box
+// (bits 0-15), nodes stepping along the box's second axis, a snapped row
+constexpr int32_t kBoxIndex = 0xffff;
+constexpr int32_t kBoxRows = 1 << 16;
+constexpr int32_t kBoxSnap = 1 << 17;
+constexpr int kStageBytes = 2048;  // shared memory of one warp's staged box
+constexpr int kTileCells = 32;     // cells of one staged interpolation item
 
 struct alignas(16) Item {
   int32_t kind;
@@ -69,8 +82,16 @@ struct alignas(16) Item {
   int32_t table;           // CONST / INTERP / CSR: first table row of cell 0
   int32_t comp;            // INTERP source components: u | v << 16
   int32_t dst_ls, src_ls;  // level strides (elements)
-  int32_t src_org;         // CSR: ELL entry of row 0 of this component
-  int32_t pad[12];
+  int32_t src_org;         // CSR: ELL entry of row 0 of this component;
+                           // MODE_TILE: element offset (level 0) of the
+                           // staged box in the source slots
+  // MODE_TILE interpolation items: levels [l0, l0 + nl) of the cells
+  // [u0, u0 + nunits) (vol divides by nunits), reading a box of bw x bh
+  // cells of the block whose slots start at bsrc, which steps bs0 / bs1
+  // elements along its two axes; bwid divides by bw
+  int32_t l0, nl, bw, bh, bs0, bs1, bsrc;
+  FastDiv bwid;
+  int32_t pad[2];
 };
 static_assert(sizeof(Item) % 16 == 0, "Item must be a multiple of 16 bytes");
 
@@ -90,6 +111,7 @@ struct Ctx {
   const int4* itp_idx;
   const void* itp_w;
   const void* itp_m;
+  const int32_t* itp_box;   // staged cells: node 0 in the item's box
   // CSR rows (global row numbering): entry count per row, ELL entries
   // (a row's entries start at item.src_org + q * item.p), per-row constant
   const int32_t* csr_nnz;

@@ -92,28 +92,27 @@ __device__ void basis(int P, double a, double b, V3& ea, V3& eb) {
   eb = scl(sb / nf, sub(ey, scl(dot(r, ey), r)));
 }
 
-__global__ void k_cs_geometry(CsPanels pan, const int4* __restrict__ cells,
-                              int ncells, int4* idx, double* w, double* m,
-                              unsigned* err) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= ncells) return;
-  const int4 cell = cells[g];
-  const int P = cell.x, i = cell.y, j = cell.z, row = cell.w;
-  const int N = pan.N, p = pan.p;
+// The stencil of one edge ghost (i, j) of panel P (one coordinate out of
+// range): the neighbour panel Q that owns the ghost's grid point, the axis dq
+// of Q normal to the shared edge, the data row rq of Q the point lies on, the
+// first node `start` along Q's other axis with the p Lagrange weights (or a
+// unit copy of node `start` when grid lines align: snap), and, with
+// `rotate`, the 2x2 basis change M.  Returns CsError bits (0: all found).
+struct EdgeStencil {
+  int Q, dq, rq, start, snap;
+  double w[kPMax];
+  double m[4];
+};
+
+__device__ unsigned edge_stencil(int P, int i, int j, int N, int p, bool rotate,
+                                 EdgeStencil& o) {
   const double pi = 3.14159265358979323846;
   const double delta = pi / (2.0 * N);
-  // which edge strip: axis d out of range on side `side`
+  for (int n = 0; n < kPMax; ++n) o.w[n] = 0.0;
+  o.m[0] = 1.0; o.m[1] = 0.0; o.m[2] = 0.0; o.m[3] = 1.0;
+  o.Q = -1; o.dq = 0; o.rq = 0; o.start = 0; o.snap = 0;
   const bool io = (i < 0 || i >= N), jo = (j < 0 || j >= N);
-  int4 out = make_int4(0, 0, 0, 0);
-  double* wr = w + (int64_t)row * kPMax;
-  double* mr = m + (int64_t)row * 4;
-  for (int n = 0; n < kPMax; ++n) wr[n] = 0.0;
-  mr[0] = 1.0; mr[1] = 0.0; mr[2] = 0.0; mr[3] = 1.0;
-  if (io == jo) {
-    atomicOr(err, (unsigned)CS_ERR_NOT_EDGE);
-    idx[row] = out;
-    return;
-  }
+  if (io == jo) return CS_ERR_NOT_EDGE;
   const int d = io ? 0 : 1;
   const int side = io ? (i >= N) : (j >= N);
   // neighbour's depth axis from the middle of the strip
@@ -129,11 +128,7 @@ __global__ void k_cs_geometry(CsPanels pan, const int4* __restrict__ cells,
   const double b = -pi / 4 + (j + 0.5) * delta;
   const V3 v = unit_point(P, a, b, nullptr);
   const int Q = owner_panel(v);
-  if (Q != Qr || Q == P) {
-    atomicOr(err, (unsigned)CS_ERR_NEIGHBOUR);
-    idx[row] = out;
-    return;
-  }
+  if (Q != Qr || Q == P) return CS_ERR_NEIGHBOUR;
   double aq, bq;
   angles_on(Q, v, aq, bq);
   const double fa = (aq + pi / 4) / delta - 0.5;
@@ -141,17 +136,13 @@ __global__ void k_cs_geometry(CsPanels pan, const int4* __restrict__ cells,
   const double fdepth = dq == 0 ? fa : fb;
   const double t = dq == 0 ? fb : fa;
   const double rq = rint(fdepth);
-  if (fabs(fdepth - rq) > 1e-9 || rq < 0 || rq > N - 1) {
-    atomicOr(err, (unsigned)CS_ERR_DEPTH);
-    idx[row] = out;
-    return;
-  }
+  if (fabs(fdepth - rq) > 1e-9 || rq < 0 || rq > N - 1) return CS_ERR_DEPTH;
   const double tr = rint(t);
   const bool snap = fabs(t - tr) < 1e-9 && tr >= 0 && tr <= N - 1;
   int start;
   if (snap) {
     start = (int)tr;
-    wr[0] = 1.0;
+    o.w[0] = 1.0;
   } else {
     start = (int)floor(t) - (p / 2 - 1);
     if (start < 0) start = 0;
@@ -161,21 +152,15 @@ __global__ void k_cs_geometry(CsPanels pan, const int4* __restrict__ cells,
       double acc = 1.0;
       for (int mm = 0; mm < p; ++mm)
         if (mm != k) acc *= (tau - mm) / (double)(k - mm);
-      wr[k] = acc;
+      o.w[k] = acc;
     }
   }
-  if (start < 0 || start + (snap ? 1 : p) > N) atomicOr(err, (unsigned)CS_ERR_RANGE);
-  // node 0 and step on Q (slot pointers address cell (-h, -h))
-  const int cq0 = dq == 0 ? (int)rq : start;
-  const int cq1 = dq == 0 ? start : (int)rq;
-  const int64_t off = (int64_t)(cq0 + pan.h) * pan.s0[Q] + (int64_t)(cq1 + pan.h) * pan.s1[Q];
-  const int64_t step = dq == 0 ? pan.s1[Q] : pan.s0[Q];
-  out.x = pan.slot_base[Q];
-  out.y = (int)off;
-  out.z = (int)step;
-  out.w = snap ? kFlagSnap : 0;
-  idx[row] = out;
-  if (pan.rotate) {
+  o.Q = Q;
+  o.dq = dq;
+  o.rq = (int)rq;
+  o.start = start;
+  o.snap = snap ? 1 : 0;
+  if (rotate) {
     V3 ea, eb, qa, qb;
     basis(P, a, b, ea, eb);
     basis(Q, aq, bq, qa, qb);
@@ -183,11 +168,39 @@ __global__ void k_cs_geometry(CsPanels pan, const int4* __restrict__ cells,
     const double det = g11 * g22 - g12 * g12;
     const V3 da = scl(1.0 / det, sub(scl(g22, qa), scl(g12, qb)));
     const V3 db = scl(1.0 / det, sub(scl(g11, qb), scl(g12, qa)));
-    mr[0] = dot(ea, da);
-    mr[1] = dot(ea, db);
-    mr[2] = dot(eb, da);
-    mr[3] = dot(eb, db);
+    o.m[0] = dot(ea, da);
+    o.m[1] = dot(ea, db);
+    o.m[2] = dot(eb, da);
+    o.m[3] = dot(eb, db);
   }
+  return (start < 0 || start + (snap ? 1 : p) > N) ? (unsigned)CS_ERR_RANGE : 0u;
+}
+
+__global__ void k_cs_geometry(CsPanels pan, const int4* __restrict__ cells,
+                              int ncells, int4* idx, double* w, double* m,
+                              unsigned* err) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ncells) return;
+  const int4 cell = cells[g];
+  const int row = cell.w;
+  EdgeStencil o;
+  const unsigned e = edge_stencil(cell.x, cell.y, cell.z, pan.N, pan.p, pan.rotate != 0, o);
+  double* wr = w + (int64_t)row * kPMax;
+  double* mr = m + (int64_t)row * 4;
+  for (int n = 0; n < kPMax; ++n) wr[n] = o.w[n];
+  for (int n = 0; n < 4; ++n) mr[n] = o.m[n];
+  if (e) atomicOr(err, e);
+  if (o.Q < 0) {
+    idx[row] = make_int4(0, 0, 0, 0);
+    return;
+  }
+  // node 0 and step on Q (slot pointers address cell (-h, -h))
+  const int cq0 = o.dq == 0 ? o.rq : o.start;
+  const int cq1 = o.dq == 0 ? o.start : o.rq;
+  const int64_t off =
+      (int64_t)(cq0 + pan.h) * pan.s0[o.Q] + (int64_t)(cq1 + pan.h) * pan.s1[o.Q];
+  const int64_t step = o.dq == 0 ? pan.s1[o.Q] : pan.s0[o.Q];
+  idx[row] = make_int4(pan.slot_base[o.Q], (int)off, (int)step, o.snap ? kFlagSnap : 0);
 }
 
 }  // namespace
@@ -238,75 +251,14 @@ __global__ void k_cs_stencils_noalloc(int N, int h, int p, int rotate,
   const int P = g / (4 * N * h);
   const int d = strip >> 1, side = strip & 1;
   const int gi = side ? N + r : -1 - r;
-  const int i = d == 0 ? gi : s;
-  const int j = d == 0 ? s : gi;
-  const double pi = 3.14159265358979323846;
-  const double delta = pi / (2.0 * N);
-  for (int n = 0; n < kPMax; ++n) wr[n] = 0.0;
-  mr[0] = 1.0; mr[1] = 0.0; mr[2] = 0.0; mr[3] = 1.0;
-  idx[g] = make_int4(-1, 0, 0, 0);
-  // neighbour's depth axis from the middle of the strip
-  double ref[2] = {0.0, 0.0};
-  ref[d] = (pi / 4 + delta / 2) * (side ? 1.0 : -1.0);
-  const V3 vr = unit_point(P, ref[0], ref[1], nullptr);
-  const int Qr = owner_panel(vr);
-  double ar, br;
-  angles_on(Qr, vr, ar, br);
-  const int dq = fabs(ar) > fabs(br) ? 0 : 1;
-  // the ghost point on the neighbour
-  const double a = -pi / 4 + (i + 0.5) * delta;
-  const double b = -pi / 4 + (j + 0.5) * delta;
-  const V3 v = unit_point(P, a, b, nullptr);
-  const int Q = owner_panel(v);
-  if (Q != Qr || Q == P) {
-    atomicOr(err, (unsigned)CS_ERR_NEIGHBOUR);
-    return;
-  }
-  double aq, bq;
-  angles_on(Q, v, aq, bq);
-  const double fa = (aq + pi / 4) / delta - 0.5;
-  const double fb = (bq + pi / 4) / delta - 0.5;
-  const double fdepth = dq == 0 ? fa : fb;
-  const double t = dq == 0 ? fb : fa;
-  const double rq = rint(fdepth);
-  if (fabs(fdepth - rq) > 1e-9 || rq < 0 || rq > N - 1) {
-    atomicOr(err, (unsigned)CS_ERR_DEPTH);
-    return;
-  }
-  const double tr = rint(t);
-  const bool snap = fabs(t - tr) < 1e-9 && tr >= 0 && tr <= N - 1;
-  int start;
-  if (snap) {
-    start = (int)tr;
-    wr[0] = 1.0;
-  } else {
-    start = (int)floor(t) - (p / 2 - 1);
-    if (start < 0) start = 0;
-    if (start > N - p) start = N - p;
-    const double tau = t - start;
-    for (int k = 0; k < p; ++k) {
-      double acc = 1.0;
-      for (int mm = 0; mm < p; ++mm)
-        if (mm != k) acc *= (tau - mm) / (double)(k - mm);
-      wr[k] = acc;
-    }
-  }
-  const int along = 1 - dq;
-  idx[g] = make_int4(Q, dq == 0 ? (int)rq : start, dq == 0 ? start : (int)rq,
-                     along | (snap ? BC_NOALLOC_SNAP : 0));
-  if (rotate) {
-    V3 ea, eb, qa, qb;
-    basis(P, a, b, ea, eb);
-    basis(Q, aq, bq, qa, qb);
-    const double g11 = dot(qa, qa), g12 = dot(qa, qb), g22 = dot(qb, qb);
-    const double det = g11 * g22 - g12 * g12;
-    const V3 da = scl(1.0 / det, sub(scl(g22, qa), scl(g12, qb)));
-    const V3 db = scl(1.0 / det, sub(scl(g11, qb), scl(g12, qa)));
-    mr[0] = dot(ea, da);
-    mr[1] = dot(ea, db);
-    mr[2] = dot(eb, da);
-    mr[3] = dot(eb, db);
-  }
+  EdgeStencil o;
+  const unsigned e = edge_stencil(P, d == 0 ? gi : s, d == 0 ? s : gi, N, p, rotate != 0, o);
+  for (int n = 0; n < kPMax; ++n) wr[n] = o.w[n];
+  for (int n = 0; n < 4; ++n) mr[n] = o.m[n];
+  if (e) atomicOr(err, e);
+  idx[g] = o.Q < 0 ? make_int4(-1, 0, 0, 0)
+                   : make_int4(o.Q, o.dq == 0 ? o.rq : o.start, o.dq == 0 ? o.start : o.rq,
+                               (1 - o.dq) | (o.snap ? BC_NOALLOC_SNAP : 0));
 }
 
 std::mutex g_noalloc_mu;

@@ -67,6 +67,7 @@ struct Ptrs {
   void* d;
   void* d2;
   const void* s;
+  void* stage;  // this warp's shared-memory staging area (kStageBytes), or null
 };
 
 // ---------------------------------------------------------------------------
@@ -491,6 +492,93 @@ __device__ void interp_pair_chunk(const Item& it, const Ptrs& P, const Ctx& c, i
   }
 }
 
+// Staged interpolation (MODE_TILE): with levels far apart in memory, the
+// nodes of a tile of up to 32 ghost cells lie in a small box of the
+// neighbour block -- a strip of the edge rows or columns (the transposed
+// strip when the nodes step along the neighbour's strided axis).  The warp
+// copies the box, for the item's levels and components, into its shared
+// memory with cp.async (each source value once, lanes over consecutive
+// cells of a box row), then every lane evaluates its (cell, level) rows
+// from shared memory: the p-point sums, the 2x2 rotation of a vector pair,
+// and the store.  Same sums in the same order as the per-lane path.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+template <typename T>
+__device__ void interp_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
+  using B = typename BitsOf<T>::type;
+  T* sm = static_cast<T*>(P.stage);
+  const bool pair = it.kind == IK_INTERP_PAIR;
+  const int nc = pair ? 2 : 1;
+  const int A = it.bw * it.bh;
+  const int cu = it.comp & 0xffff, cv = it.comp >> 16;
+  const int64_t lev0 = (int64_t)it.l0 * it.src_ls + it.src_org;
+  const T* xu = static_cast<const T*>(c.slots[it.bsrc + cu]) + lev0;
+  const T* xv = pair ? static_cast<const T*>(c.slots[it.bsrc + cv]) + lev0 : xu;
+  // stage: [level][component][box row][box column]
+  for (int g = 0; g < it.nl * nc; ++g) {
+    const int l = pair ? g >> 1 : g;
+    const T* src = ((pair && (g & 1)) ? xv : xu) + (int64_t)l * it.src_ls;
+    T* dst = sm + g * A;
+    for (int e = lane; e < A; e += 32) {
+      const int bj = (int)fdiv((uint32_t)e, it.bwid), bi = e - bj * it.bw;
+      cp_async_elem<T>(dst + e, src + (bi * it.bs0 + bj * it.bs1));
+    }
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  const int nq = it.nunits, tot = nq * it.nl;
+  const int p = it.p;
+  B* du = static_cast<B*>(P.d);
+  B* dv = static_cast<B*>(P.d2);
+  for (int u = lane; u < tot; u += 32) {
+    const int l = (int)fdiv((uint32_t)u, it.vol), q = u - l * nq;
+    const int row = it.table + it.u0 + q;
+    const int bx = __ldg(c.itp_box + row);
+    const int st = (bx & kBoxRows) ? it.bw : 1;
+    const bool snap = bx & kBoxSnap;
+    const int64_t off = (int64_t)dst_cell(it, c, it.u0 + q) + (int64_t)(it.l0 + l) * it.dst_ls;
+    const T* su = sm + (pair ? 2 * l : l) * A + (bx & kBoxIndex);
+    const T* wr = static_cast<const T*>(c.itp_w) + row * kPMax;
+    if (!pair) {
+      if (snap) {  // unit row: exact copy of node 0
+        du[off] = reinterpret_cast<const B*>(su)[0];
+        continue;
+      }
+      T acc = T(0);
+#pragma unroll
+      for (int n = 0; n < kPMax; ++n)
+        if (n < p) acc = fma(ldg(wr + n), su[n * st], acc);
+      du[off] = to_bits(acc);
+    } else {
+      const T* sv = su + A;
+      const int pe = snap ? 1 : p;
+      T au = T(0), av = T(0);
+#pragma unroll
+      for (int n = 0; n < kPMax; ++n)
+        if (n < pe) {
+          const T w = snap ? T(1) : ldg(wr + n);
+          au = fma(w, su[n * st], au);
+          av = fma(w, sv[n * st], av);
+        }
+      const T* mr = static_cast<const T*>(c.itp_m) + row * 4;
+      du[off] = to_bits(fma(ldg(mr), au, ldg(mr + 1) * av));
+      dv[off] = to_bits(fma(ldg(mr + 2), au, ldg(mr + 3) * av));
+    }
+  }
+  __syncwarp();  // every lane is done with the stage before the next item
+}
+
 // Flat interpolation: each lane keeps U values (cell, level) in flight; with
 // level-fastest order the lanes of a warp share a cell, so its table row is
 // one broadcast load and the node loads of the warp are contiguous.
@@ -893,12 +981,14 @@ __device__ void adj_flat(const Item& it, const Ptrs& P, const Ctx& c, int lane) 
 // budget (and so its occupancy) independent of the others.
 template <typename T, int FAM, int MAXCH>
 __device__ __forceinline__ void run_item(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
-  const bool flat = it.mode < 2;
+  const bool flat = it.mode < 2 && it.mode != MODE_TILE;
   const bool ch8 = MAXCH > 4 && it.mode > 4;  // level chunks of up to 8
   if constexpr (FAM == FAM_STRUCT) {
     structured_flat<T>(it, P, c, lane);
   } else if constexpr (FAM == FAM_INTERP) {
-    if (it.kind == IK_INTERP_PAIR) {
+    if (it.mode == MODE_TILE) {
+      interp_tile<T>(it, P, c, lane);
+    } else if (it.kind == IK_INTERP_PAIR) {
       if (flat)
         interp_flat<T, true>(it, P, c, lane);
       else if (ch8)
@@ -1009,20 +1099,31 @@ __device__ __forceinline__ Ptrs gather_ptrs(void* mine) {
   P.d = reinterpret_cast<void*>(__shfl_sync(0xffffffffu, v, kWordDst));
   P.d2 = reinterpret_cast<void*>(__shfl_sync(0xffffffffu, v, kWordDst2));
   P.s = reinterpret_cast<const void*>(__shfl_sync(0xffffffffu, v, kWordSrc));
+  P.stage = nullptr;
   return P;
 }
+
+// Shared memory for staged interpolation boxes: one kStageBytes area per
+// warp in the kernels that run interpolation items.
+template <int FAM, int THREADS>
+struct Stage {
+  static constexpr int kWarps = (FAM == FAM_INTERP || FAM == FAM_ALL) ? THREADS / 32 : 0;
+  static constexpr int kBytes = kWarps > 0 ? kWarps * kStageBytes : 16;
+};
 
 // Plain grid: warp w of CTA b processes item b * warps + w.
 template <typename T, int THREADS, int FAM>
 __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     k_items(Ctx c, const Item* __restrict__ items, int nitems) {
   __shared__ Item sit[THREADS / 32];
+  __shared__ __align__(16) unsigned char stage[Stage<FAM, THREADS>::kBytes];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int idx = blockIdx.x * (THREADS / 32) + warp;
   if (idx >= nitems) return;
   const int w = __ldg(reinterpret_cast<const int*>(items + idx) + lane);
   reinterpret_cast<int*>(&sit[warp])[lane] = w;
-  const Ptrs P = gather_ptrs(lookup_slot(c, w, lane));
+  Ptrs P = gather_ptrs(lookup_slot(c, w, lane));
+  if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * kStageBytes;
   __syncwarp();
   run_work<T, FAM>(sit[warp], P, c, lane);
 }
@@ -1035,6 +1136,7 @@ template <typename T, int THREADS, int FAM>
 __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     k_stream(Ctx c, const Item* __restrict__ items, int nitems) {
   __shared__ Item sit[THREADS / 32];
+  __shared__ __align__(16) unsigned char stage[Stage<FAM, THREADS>::kBytes];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int stride = gridDim.x * (THREADS / 32);
   const int* iw = reinterpret_cast<const int*>(items);
@@ -1049,7 +1151,8 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     void* p_nxt = nxt < nitems ? lookup_slot(c, w_nxt, lane) : nullptr;
     const int nxt2 = nxt + stride;
     const int w_nxt2 = nxt2 < nitems ? __ldg(iw + (int64_t)nxt2 * 32 + lane) : 0;
-    const Ptrs P = gather_ptrs(p_cur);
+    Ptrs P = gather_ptrs(p_cur);
+    if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * kStageBytes;
     __syncwarp();
     run_work<T, FAM>(sit[warp], P, c, lane);
     __syncwarp();
@@ -1076,6 +1179,7 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     k_persist(Ctx c, const Item* __restrict__ items, int nitems, unsigned* __restrict__ ctr) {
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ Item sit[THREADS / 32];
+  __shared__ __align__(16) unsigned char stage[Stage<FAM, THREADS>::kBytes];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int* iw = reinterpret_cast<const int*>(items);
   const unsigned n = (unsigned)nitems;
@@ -1100,7 +1204,8 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
   while (a < n) {
     const unsigned raw = issue();  // claim of the fourth item, in flight
     reinterpret_cast<int*>(&sit[warp])[lane] = wa;
-    const Ptrs P = gather_ptrs(pa);
+    Ptrs P = gather_ptrs(pa);
+    if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * kStageBytes;
     __syncwarp();
     run_work<T, FAM>(sit[warp], P, c, lane);
     __syncwarp();

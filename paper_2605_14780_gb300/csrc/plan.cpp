@@ -41,6 +41,9 @@
 
 using namespace bcg;
 
+// cell (i, j, k) of block B at element offset `off` (defined with the C ABI)
+bool decode_cell(const bc_block& B, int64_t off, int& i, int& j, int& k);
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -145,6 +148,7 @@ struct bc_plan {
   // host tables (FP64 copies)
   std::vector<int4> itp_idx;
   std::vector<double> itp_w, itp_m;
+  std::vector<int32_t> itp_box;  // staged interpolation: node 0 in its tile's box
   // user CSR rows stored as ELL blocks (one width per sub-matrix)
   std::vector<int32_t> csr_nnz;
   std::vector<int32_t> csr_slot, csr_off;
@@ -214,6 +218,7 @@ struct bc_plan {
   std::mutex ctr_mu;
   std::vector<void*> ctr_streams;
   int num_sms = 1;
+  uint64_t hash = 0;  // of the rows, layouts and untuned options (autotune cache key)
   bc_plan_opts opts{};
   bc_stats stats{};
 };
@@ -847,10 +852,13 @@ int table_mode(const bc_block& B, int order, int chunk) {
   return std::min(B.nlevels, chunk);
 }
 
-// levels per unit of the chunked unit order (bc_plan_opts.level_chunk); the
-// persistent launch's kernel holds at most 4
-int level_chunk(const bc_plan* P) {
-  const int ch = P->opts.level_chunk;
+// levels per unit of the chunked unit order (bc_plan_opts.level_chunk; by
+// default 4 for interpolation rows, whose pair path keeps two components'
+// sums, and 8 for CSR and transpose rows); the persistent launch's kernel
+// holds at most 4
+int level_chunk(const bc_plan* P, bool interp) {
+  int ch = P->opts.level_chunk;
+  if (ch == 0) ch = interp ? 4 : 8;
   return P->opts.batch_mode == BC_BATCH_PERSISTENT ? std::min(ch, 4) : ch;
 }
 
@@ -962,8 +970,87 @@ void emit_runs(std::vector<Item>& out, Item proto, const std::vector<int4>& runs
   }
 }
 
+// Staged interpolation items of sub-matrix s (levels in chunks of `chunk`):
+// tiles of up to kTileCells consecutive box cells whose nodes all lie in one
+// 2-D source block, with the node box of each tile small enough that `chunk`
+// levels of its components (nc) fit a warp's staging area at least one
+// level at a time.  Writes the cells' itp_box rows.  Returns false (the
+// sub-matrix keeps the per-lane path) when some tile does not qualify.
+bool emit_tiles(bc_plan* P, const Sub& s, const Item& proto, int chunk, int nc,
+                std::vector<Item>& out) {
+  const bc_block& B = P->blocks[s.block];
+  const int L = B.nlevels;
+  const int cap = kStageBytes / P->esize;
+  std::vector<Item> tiles;
+  std::vector<std::pair<int, int32_t>> boxes;  // (row, itp_box) to write on success
+  for (int q0 = 0; q0 < s.vol; q0 += kTileCells) {
+    const int nq = std::min(kTileCells, s.vol - q0);
+    int base = -1, axis_of_step = -1;
+    int imin = INT_MAX, imax = INT_MIN, jmin = INT_MAX, jmax = INT_MIN;
+    struct Node0 {
+      int i, j, rows, snap;
+    };
+    std::vector<Node0> n0(nq);
+    for (int q = 0; q < nq; ++q) {
+      const int4 ix = P->itp_idx[(size_t)(s.table + q0 + q)];
+      if (base < 0) base = ix.x;
+      if (ix.x != base) return false;
+      const bc_block& S = P->blocks[P->slot_block[ix.x]];
+      if (S.n[2] != 1 || S.h[2] != 0) return false;
+      int i, j, k;
+      if (!decode_cell(S, ix.y, i, j, k)) return false;
+      const bool snap = ix.w & kFlagSnap;
+      const int np = snap ? 1 : s.p;
+      int ax;
+      if (np == 1 || ix.z == S.stride[0]) ax = 0;
+      else if (ix.z == S.stride[1]) ax = 1;
+      else return false;
+      (void)axis_of_step;
+      const int i1 = ax == 0 ? i + np - 1 : i, j1 = ax == 1 ? j + np - 1 : j;
+      imin = std::min(imin, i);
+      imax = std::max(imax, i1);
+      jmin = std::min(jmin, j);
+      jmax = std::max(jmax, j1);
+      n0[q] = {i, j, ax, snap ? 1 : 0};
+    }
+    const int bw = imax - imin + 1, bh = jmax - jmin + 1;
+    if ((int64_t)bw * bh > kBoxIndex || (int64_t)bw * bh * nc > cap) return false;
+    const int nl = std::min(chunk, cap / (bw * bh * nc));
+    const bc_block& S = P->blocks[P->slot_block[base]];
+    const int64_t org = cell_offset(S, imin, jmin, 0);
+    if (org > INT32_MAX) return false;
+    for (int q = 0; q < nq; ++q) {
+      const int32_t bx = (n0[q].i - imin) + (n0[q].j - jmin) * bw;
+      boxes.push_back({s.table + q0 + q,
+                       bx | (n0[q].rows ? kBoxRows : 0) | (n0[q].snap ? kBoxSnap : 0)});
+    }
+    for (int l0 = 0; l0 < L; l0 += nl) {
+      Item it = proto;
+      it.mode = MODE_TILE;
+      it.u0 = q0;
+      it.nunits = nq;
+      it.vol = make_div((uint32_t)nq);
+      it.l0 = l0;
+      it.nl = std::min(nl, L - l0);
+      it.bw = bw;
+      it.bh = bh;
+      it.bs0 = (int32_t)S.stride[0];
+      it.bs1 = (int32_t)S.stride[1];
+      it.bsrc = base;
+      it.bwid = make_div((uint32_t)bw);
+      it.src_org = (int32_t)org;
+      it.src_ls = (int32_t)(S.nlevels > 1 ? S.level_stride : 0);
+      tiles.push_back(it);
+    }
+  }
+  for (const auto& b : boxes) P->itp_box[(size_t)b.first] = b.second;
+  out.insert(out.end(), tiles.begin(), tiles.end());
+  return true;
+}
+
 void build_items(bc_plan* P) {
   P->runs.clear();
+  P->itp_box.assign(P->itp_idx.size(), 0);
   // units per warp item: single-level values (flat) or 8-level chunks
   const int upl = std::max(1, std::min(P->opts.units_per_lane, 64));
   // A small plan still gets enough items to keep every SM busy: the value
@@ -1000,9 +1087,9 @@ void build_items(bc_plan* P) {
       run_n[si] = nr;
     }
   }
-  const int chunk = level_chunk(P);
   auto table_emit = [&](std::vector<Item>& out, const Item& it, const bc_block& B, int vol) {
-    const int mode = table_mode(B, P->opts.unit_order, chunk);
+    const bool interp = it.kind == IK_INTERP || it.kind == IK_INTERP_PAIR;
+    const int mode = table_mode(B, P->opts.unit_order, level_chunk(P, interp));
     emit_units(out, it, vol, B.nlevels, mode, mode < 2 ? per_table_flat_item : per_table_item);
   };
   std::vector<std::pair<int, std::vector<Item>>> per_sub(P->subs.size());
@@ -1044,7 +1131,12 @@ void build_items(bc_plan* P) {
           } else {
             it.kind = IK_INTERP;
           }
-          table_emit(out, it, B, s.vol);
+          // levels far apart in memory: stage the nodes of each tile in
+          // shared memory when the tiles' boxes are small
+          const int mode = table_mode(B, P->opts.unit_order, level_chunk(P, true));
+          if (mode < 2 || P->opts.unstaged_interp ||
+              !emit_tiles(P, s, it, mode, it.kind == IK_INTERP_PAIR ? 2 : 1, out))
+            table_emit(out, it, B, s.vol);
           break;
         }
         case BC_CSR: {
@@ -1087,6 +1179,7 @@ void build_items(bc_plan* P) {
   // longest items first, so the last wave of warps holds the short ones
   // (512-block workload, levels innermost: batched step 49.2 -> 48.1 us)
   auto work = [&](const Item& it) -> int64_t {
+    if (it.mode == MODE_TILE) return (int64_t)it.nunits * it.nl;
     if (it.mode != MODE_RUNS) return it.nunits;
     int64_t n = 0;
     for (int r = it.u0; r < it.u0 + it.nunits; ++r) n += P->runs[r].z;
@@ -1471,9 +1564,11 @@ bc_status upload_work(bc_plan* P) {
   const size_t o_a = L.take(P->adj_items.size() * sizeof(Item));
   const size_t o_z = L.take(P->adj_zero.size() * sizeof(Item));
   const size_t o_all = L.take(P->all_items.size() * sizeof(Item));
+  const size_t o_box = L.take(P->itp_box.size() * 4);
   std::vector<char> host(L.off + 256, 0);
   put_raw(host, o_i, P->items);
   put_raw(host, o_all, P->all_items);
+  put_raw(host, o_box, P->itp_box);
   for (int f = 0; f < kFamilies; ++f) put_raw(host, o_f[f], P->fam_items[f]);
   put_raw(host, o_r, P->runs);
   put_raw(host, o_a, P->adj_items);
@@ -1493,6 +1588,7 @@ bc_status upload_work(bc_plan* P) {
   P->d_adj = reinterpret_cast<Item*>(b + o_a);
   P->d_adj_zero = reinterpret_cast<Item*>(b + o_z);
   P->d_all = reinterpret_cast<Item*>(b + o_all);
+  P->ctx.itp_box = reinterpret_cast<const int32_t*>(b + o_box);
   return BC_OK;
 }
 
@@ -1587,13 +1683,15 @@ bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
     return fail(BC_ERR_INVALID_ARG, "bad work-item options");
   if (o.ghost_sweeps < 0 || o.ghost_sweeps > kMaxGhostSweeps)
     return fail(BC_ERR_INVALID_ARG, "ghost_sweeps must be in 0..%d", kMaxGhostSweeps);
-  if (o.batch_mode == 0) o.batch_mode = BC_BATCH_PERSISTENT;
+  if (o.batch_mode == 0) o.batch_mode = BC_BATCH_FAMILIES;
   if (o.batch_mode != BC_BATCH_PERSISTENT && o.batch_mode != BC_BATCH_FAMILIES)
     return fail(BC_ERR_INVALID_ARG, "batch_mode must be 0, BC_BATCH_PERSISTENT or BC_BATCH_FAMILIES");
   if (o.scalar_runs < 0 || o.scalar_runs > 1)
     return fail(BC_ERR_INVALID_ARG, "scalar_runs must be 0 or 1");
-  if (o.level_chunk == 0) o.level_chunk = 4;
-  if (o.level_chunk != 1 && o.level_chunk != 2 && o.level_chunk != 4 && o.level_chunk != 8)
+  if (o.unstaged_interp < 0 || o.unstaged_interp > 1)
+    return fail(BC_ERR_INVALID_ARG, "unstaged_interp must be 0 or 1");
+  if (o.level_chunk != 0 && o.level_chunk != 1 && o.level_chunk != 2 && o.level_chunk != 4 &&
+      o.level_chunk != 8)
     return fail(BC_ERR_INVALID_ARG, "level_chunk must be 0, 1, 2, 4 or 8");
   return BC_OK;
 }
@@ -1615,6 +1713,53 @@ size_t live_ghosts(const bc_block& B, const int32_t* off, int noff) {
         }
       }
   return n;
+}
+
+// FNV-1a over the bytes that decide what the autotuner measures: dtype,
+// block layouts, the explicit rows and the options it does not tune.
+struct Fnv {
+  uint64_t h = 1469598103934665603ull;
+  void bytes(const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+  }
+  template <typename V>
+  void vec(const std::vector<V>& v) {
+    const uint64_t n = v.size();
+    bytes(&n, sizeof(n));
+    if (!v.empty()) bytes(v.data(), v.size() * sizeof(V));
+  }
+  template <typename V>
+  void val(const V& v) { bytes(&v, sizeof(V)); }
+};
+
+uint64_t plan_hash(const bc_plan* P) {
+  Fnv f;
+  f.val(P->dtype);
+  for (const bc_block& b : P->blocks) {
+    f.bytes(b.n, sizeof(b.n));
+    f.bytes(b.h, sizeof(b.h));
+    f.val(b.nlevels);
+    f.val(b.ncomp);
+    f.bytes(b.stride, sizeof(b.stride));
+    f.val(b.level_stride);
+  }
+  const ExplicitRows& R = P->rows;
+  f.vec(R.slot);
+  f.vec(R.off);
+  f.vec(R.ptr);
+  f.vec(R.cslot);
+  f.vec(R.coff);
+  f.vec(R.val);
+  f.vec(R.rhs);
+  f.val(P->sync.stage);
+  f.vec(P->sync.ptr);
+  f.vec(P->sync.w);
+  const bc_plan_opts& o = P->opts;
+  const int32_t fixed[] = {o.unit_order, o.strict_cover, o.no_adjoint, o.no_runs,
+                           o.ghost_sweeps, (int32_t)P->pruned};
+  f.bytes(fixed, sizeof(fixed));
+  return f.h;
 }
 
 bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_t nsubs,
@@ -1760,6 +1905,7 @@ bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_
     P->rows = std::move(all);
   }
   if (!P->opts.no_adjoint) build_transpose(P);
+  P->hash = plan_hash(P);
   build_items(P);
   if (!P->opts.host_only) {
     if ((st = upload_tables(P)) != BC_OK) return st;
@@ -2058,6 +2204,11 @@ struct WorkCheck {
   template <typename F>
   void units(const Item& it, F f) const {
     const int vol = (int)it.vol.d, L = (int)it.lev.d;
+    if (it.mode == MODE_TILE) {
+      for (int l = it.l0; l < it.l0 + it.nl; ++l)
+        for (int q = it.u0; q < it.u0 + it.nunits; ++q) f(q, l);
+      return;
+    }
     for (int u = it.u0; u < it.u0 + it.nunits; ++u) {
       if (it.mode == MODE_FLAT_LEVEL) {
         f(u / L, u % L);
@@ -2151,7 +2302,19 @@ int64_t check_forward_list(WorkCheck& W, const std::vector<Item>& items, bool va
         // the nodes and weights the interpolation kernels read (a snapped
         // row reads node 0 only), rotated for a pair, against the rows
         const size_t cell = (size_t)(it.table + q);
-        const int4 ix = P->itp_idx[cell];
+        int4 ix = P->itp_idx[cell];
+        if (it.mode == MODE_TILE) {
+          // the node offsets a staged item reads: from the cell's place in
+          // its tile's box, not from the per-lane table
+          const int32_t bx = P->itp_box[cell];
+          const int idx = bx & kBoxIndex;
+          ix.x = it.bsrc;
+          ix.y = it.src_org + (idx % it.bw) * it.bs0 + (idx / it.bw) * it.bs1;
+          ix.z = (bx & kBoxRows) ? it.bs1 : it.bs0;
+          ix.w = (bx & kBoxSnap) ? kFlagSnap : 0;
+          if (idx >= it.bw * it.bh)
+            W.problem("a staged row's node lies outside its box", it.dst_slot, E);
+        }
         const int np_ = (ix.w & kFlagSnap) ? 1 : it.p;
         const int cu = it.comp & 0xffff, cv = it.comp >> 16;
         auto node = [&](int comp, int n) {
@@ -2444,64 +2607,172 @@ bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs, void* const* dev_
   return BC_OK;
 }
 
+namespace {
+
+// Autotune results of this process, and of BC_AUTOTUNE_CACHE's file: the
+// tuned options by "<plan hash>:<device name>:<SMs>".
+struct TunedOpts {
+  int32_t batch_mode, scalar_runs, units_per_lane, threads, level_chunk, ctas_per_sm;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TunedOpts> g_tuned;
+
+std::string tune_key(const bc_plan* P) {
+  int dev = 0;
+  cudaDeviceProp prop{};
+  std::string name = "unknown";
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+    name = prop.name;
+  for (char& ch : name)
+    if (ch == ' ' || ch == ':') ch = '_';
+  char buf[64];
+  snprintf(buf, sizeof(buf), "%016llx", (unsigned long long)P->hash);
+  return std::string(buf) + ":" + name + ":" + std::to_string(P->num_sms);
+}
+
+void set_tuned(bc_plan_opts& o, const TunedOpts& t) {
+  o.batch_mode = t.batch_mode;
+  o.scalar_runs = t.scalar_runs;
+  o.units_per_lane = t.units_per_lane;
+  o.threads = t.threads;
+  o.level_chunk = t.level_chunk;
+  o.ctas_per_sm = t.ctas_per_sm;
+}
+
+TunedOpts get_tuned(const bc_plan_opts& o) {
+  return {o.batch_mode, o.scalar_runs, o.units_per_lane, o.threads, o.level_chunk, o.ctas_per_sm};
+}
+
+// the cached choice for `key`, from memory or the cache file
+bool cached_choice(const std::string& key, TunedOpts& out) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(key);
+  if (it != g_tuned.end()) {
+    out = it->second;
+    return true;
+  }
+  const char* path = std::getenv("BC_AUTOTUNE_CACHE");
+  if (!path || !*path) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  while (std::fgets(line, sizeof(line), f)) {
+    char k[320];
+    TunedOpts t{};
+    if (std::sscanf(line, "%319s %d %d %d %d %d %d", k, &t.batch_mode, &t.scalar_runs,
+                    &t.units_per_lane, &t.threads, &t.level_chunk, &t.ctas_per_sm) == 7 &&
+        key == k) {
+      out = t;
+      found = true;  // the last line for a key wins
+    }
+  }
+  std::fclose(f);
+  if (found) g_tuned[key] = out;
+  return found;
+}
+
+void store_choice(const std::string& key, const TunedOpts& t, float ms) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tuned[key] = t;
+  const char* path = std::getenv("BC_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  if (FILE* f = std::fopen(path, "a")) {
+    std::fprintf(f, "%s %d %d %d %d %d %d %.6f\n", key.c_str(), t.batch_mode, t.scalar_runs,
+                 t.units_per_lane, t.threads, t.level_chunk, t.ctas_per_sm, ms);
+    std::fclose(f);
+  }
+}
+
+}  // namespace
+
 bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) {
   TraceRange trace("bc_plan_autotune");
   if (plan && plan->opts.host_only) return fail(BC_ERR_UNSUPPORTED, "host_only plan");
   if (!plan || !slot_ptrs) return fail(BC_ERR_INVALID_ARG, "NULL argument");
   arm_fault_injection();
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bc_plan_opts keep = plan->opts;
+  const std::string key = tune_key(plan);
+  TunedOpts hit{};
+  if (cached_choice(key, hit)) {
+    set_tuned(plan->opts, hit);
+    build_items(plan);
+    bc_status st = upload_work(plan);
+    if (st != BC_OK) {
+      plan->opts = keep;
+      build_items(plan);
+      upload_work(plan);
+    }
+    compute_stats(plan);
+    return st;
+  }
   int dev = 0, l2 = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune device query");
   const size_t flush_bytes = std::max<size_t>((size_t)l2 * 2, size_t(64) << 20);
   void* flush = nullptr;
-  cudaError_t e = dev_malloc(&flush, flush_bytes);
+  e = dev_malloc(&flush, flush_bytes);
   if (e != cudaSuccess) return cuda_fail(e, "autotune flush buffer");
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  const bc_plan_opts keep = plan->opts;
-  bc_plan_opts best = keep;
-  float best_ms = 1e30f;
-  // time one candidate: median of 6 cold-L2 launches after 2 warm-ups
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaFree(flush);
+    return cuda_fail(e, "autotune events");
+  }
+  // one candidate: median of 6 launches after 2 warm-ups, an L2 flush before each
   auto time_candidate = [&](float& med) -> bc_status {
     build_items(plan);
     bc_status st = upload_work(plan);
     if (st != BC_OK) return st;
     std::vector<float> ts;
     for (int rep = 0; rep < 8; ++rep) {
-      cudaMemsetAsync(flush, rep & 0xff, flush_bytes, s);
-      cudaEventRecord(e0, s);
-      if ((st = launch_forward(plan, slot_ptrs, BC_FORM_BATCHED, s)) != BC_OK) return st;
-      cudaEventRecord(e1, s);
-      cudaError_t ee = cudaEventSynchronize(e1);
+      cudaError_t ee = cudaMemsetAsync(flush, rep & 0xff, flush_bytes, s);
+      if (ee == cudaSuccess) ee = cudaEventRecord(e0, s);
       if (ee != cudaSuccess) return cuda_fail(ee, "autotune timing");
+      if ((st = launch_forward(plan, slot_ptrs, BC_FORM_BATCHED, s)) != BC_OK) return st;
+      if ((ee = cudaEventRecord(e1, s)) != cudaSuccess ||
+          (ee = cudaEventSynchronize(e1)) != cudaSuccess)
+        return cuda_fail(ee, "autotune timing");
       float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
+      if ((ee = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+        return cuda_fail(ee, "autotune timing");
       if (rep >= 2) ts.push_back(ms);
     }
     std::sort(ts.begin(), ts.end());
     med = ts[ts.size() / 2];
     return BC_OK;
   };
-  const int threads_c[] = {64, 128, 256};
-  const int units_c[] = {1, 2, 4, 8};
-  const int warps_c[] = {0, 16, 32, 48};  // persistent warps per SM (0: grid)
-  bc_status st = BC_OK;
-  for (int T : threads_c) {
-    for (int U : units_c) {
-      for (int wps : warps_c) {
-        const int cps = wps * 32 / T;
-        if (st != BC_OK || (wps > 0 && cps < 1)) continue;
-        plan->opts.threads = T;
-        plan->opts.units_per_lane = U;
-        plan->opts.ctas_per_sm = cps;
-        float med = 0;
-        st = time_candidate(med);
-        if (st == BC_OK && med < best_ms) {
-          best_ms = med;
-          best = plan->opts;
-        }
+  bool chunked = false, runs = false;
+  for (const Item& it : plan->items) {
+    chunked |= it.mode >= 2 || (it.mode == MODE_FLAT_CELL && it.lev.d > 1);
+    runs |= it.mode == MODE_RUNS;
+  }
+  // one option at a time, from the plan's own options
+  struct Knob {
+    int32_t bc_plan_opts::*field;
+    std::vector<int32_t> values;
+  };
+  std::vector<Knob> knobs = {{&bc_plan_opts::batch_mode, {BC_BATCH_PERSISTENT, BC_BATCH_FAMILIES}}};
+  if (runs) knobs.push_back({&bc_plan_opts::scalar_runs, {0, 1}});
+  knobs.push_back({&bc_plan_opts::units_per_lane, {1, 2, 4, 8}});
+  knobs.push_back({&bc_plan_opts::threads, {128, 256}});
+  if (chunked) knobs.push_back({&bc_plan_opts::level_chunk, {1, 2, 4, 8}});
+  knobs.push_back({&bc_plan_opts::ctas_per_sm, {0, 1, 2}});
+  float best_ms = 0;
+  bc_status st = time_candidate(best_ms);
+  bc_plan_opts best = plan->opts;
+  for (const Knob& k : knobs) {
+    for (int32_t v : k.values) {
+      if (st != BC_OK || best.*(k.field) == v) continue;
+      plan->opts = best;
+      plan->opts.*(k.field) = v;
+      float med = 0;
+      st = time_candidate(med);
+      if (st == BC_OK && med < best_ms) {
+        best_ms = med;
+        best = plan->opts;
       }
     }
   }
@@ -2509,6 +2780,7 @@ bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) 
   build_items(plan);
   bc_status st2 = upload_work(plan);
   if (st == BC_OK) st = st2;
+  if (st == BC_OK) store_choice(key, get_tuned(plan->opts), best_ms);
   compute_stats(plan);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

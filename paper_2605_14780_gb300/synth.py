@@ -2,9 +2,13 @@
 
 The CUDA path's tests and benchmark and the FP64 oracle both consume what this
 module produces.  It holds none of the method's arithmetic: no index maps, no
-interpolation weights, no basis-change matrices and no matrix assembly.  It
-only draws block shapes, boundary-condition *descriptions* (the basic
-sub-matrices a user would write down, Sec. IV-A, Table II) and field values.
+generated interpolation weights, no basis-change matrices and no matrix
+assembly.  It only draws block shapes, boundary-condition *descriptions* (the
+basic sub-matrices a user would write down, Sec. IV-A, Table II) and field
+values.  One workload, :func:`staggered_interp`, is a user-given ``Itp``: its
+description carries the user's own interpolation tables (Lagrange weights
+and rotations written out here as input data, as a user of the library would
+write them), which both sides then read as given.
 
 Workload dictionary
 -------------------

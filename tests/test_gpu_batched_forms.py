@@ -143,3 +143,37 @@ def test_stats_count_one_launch_for_the_persistent_form():
     _, ts = _packed(w["fields"], 0, "innermost")
     assert bc.plan_for_workload(w, ts, {"batch_mode": P}).stats()["launches_fwd"] == 1
     assert bc.plan_for_workload(w, ts, {"batch_mode": F}).stats()["launches_fwd"] == 2
+
+
+def test_autotune_result_cache(tmp_path, monkeypatch):
+    """bc_plan_autotune stores its choice under the plan's hash in
+    BC_AUTOTUNE_CACHE; a second plan of the same operator and layout takes
+    the stored options without timing (no new line), and both still give the
+    oracle's ghosts.  A plan of another layout gets its own line."""
+    import torch
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("BC_AUTOTUNE_CACHE", str(path))
+    w = synth.batching(nblocks=30, side_lo=4, side_hi=40, lev_lo=1, lev_hi=20,
+                       h=2, seed=37, dtype="f32")
+    op = build_operator(w)
+    _, ts = _packed(w["fields"], 1, "innermost")
+    plan = bc.plan_for_workload(w, ts)
+    plan.autotune(bc.slot_table(ts))
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1
+    tuned = plan.stats()
+    _, ts2 = _packed(w["fields"], 1, "innermost")
+    plan2 = bc.plan_for_workload(w, ts2)
+    plan2.autotune(bc.slot_table(ts2))
+    assert path.read_text().splitlines() == lines
+    st2 = plan2.stats()
+    for k in ("form_threads", "form_ctas_per_sm", "units_per_lane", "launches_fwd"):
+        assert st2[k] == tuned[k], k
+    for t, a in zip(ts2, w["fields"]):
+        t.copy_(torch.from_numpy(a))
+    plan2.apply(bc.slot_table(ts2))
+    torch.cuda.synchronize()
+    compare(w, [t.cpu().numpy() for t in ts2], op=op)
+    _, ts3 = _packed(w["fields"], 1, "outermost")
+    bc.plan_for_workload(w, ts3).autotune(bc.slot_table(ts3))
+    assert len(path.read_text().splitlines()) == 2

@@ -1,13 +1,15 @@
 """The allocation-free cubed-sphere stencil entry point.
 
-Callers that cannot allocate device memory (a global-mode stream capture, or
-a framework whose memory pool forbids raw cudaMalloc) get the cubed-sphere
-edge stencils from ``bc_cubed_sphere_stencils_noalloc``, which keeps its
-scratch in a fixed device array inside the library.  Its rows must agree
-with the ones the regular plan generates (``bc_plan_create`` with
+Callers that cannot allocate device memory (a framework whose memory pool
+forbids raw cudaMalloc, or code under a fixed device-memory budget) get the
+cubed-sphere edge stencils from ``bc_cubed_sphere_stencils_noalloc``, which
+keeps its scratch in a fixed device array inside the library.  Its rows must
+agree with the ones the regular plan generates (``bc_plan_create`` with
 ``BC_GEOM_CUBED_SPHERE`` sub-matrices, read back through
 ``bc_plan_export_csr``) within the FP64 tolerance of the other tests, on two
-calls in a row.  This file is collected last on purpose.
+calls in a row, and with the FP64 oracle's own geometry (``oracle.sphere``:
+neighbour panel, depth row, stencil start and Lagrange weights, and the
+basis change).  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -100,3 +102,33 @@ def test_noalloc_rejects_sizes_beyond_the_scratch():
     with pytest.raises(bc.BCError) as e:
         bc.cubed_sphere_stencils_noalloc(4, 2, 6)
     assert e.value.status == "BC_ERR_INVALID_ARG"
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("N,h,p", [(13, 3, 6), (8, 2, 4)])
+def test_noalloc_stencils_match_the_oracle(N, h, p):
+    """Every cell's neighbour panel, node-0 cell, stepping axis, snap flag,
+    weights and basis change against the oracle's strip geometry."""
+    from oracle import sphere
+    res = bc.cubed_sphere_stencils_noalloc(N, h, p, rotate=True)
+    c = 0
+    for P in range(6):
+        for d in range(2):
+            for side in range(2):
+                g = sphere.strip_geometry(P, N, h, d, side)
+                snapped, start, w = sphere.stencil(g["t"], N, p)
+                M = sphere.rotation(P, g["Q"], g["a"], g["b"], g["aq"], g["bq"])
+                n = len(g["rq"])
+                sl = slice(c, c + n)
+                assert np.all(res["nb"][sl] == g["Q"])
+                axis = res["axis"][sl]
+                assert np.all((axis & 0xff) == 1 - g["dq"])
+                assert np.array_equal((axis & bc.NOALLOC_SNAP) != 0, snapped)
+                node = res["node0"][sl]
+                assert np.array_equal(node[:, g["dq"]], g["rq"])
+                assert np.array_equal(node[:, 1 - g["dq"]], start)
+                wexp = np.where(snapped[:, None], np.eye(p)[0][None, :], w)
+                assert np.allclose(res["w"][sl], wexp, rtol=0, atol=TOL)
+                assert np.allclose(res["rot"][sl], M, rtol=0, atol=TOL)
+                c += n
+    assert c == 24 * N * h
