@@ -292,6 +292,9 @@ typedef struct bc_plan_opts {
                               levels far apart in memory, a warp first
                               copies the small box of neighbour cells a tile
                               of 32 ghost cells reads into shared memory    */
+  int32_t stencil_fusion;  /* 1: also build the tables bc_apply_stencil
+                              needs (a row per ghost-frame cell, and the
+                              rows of A in CSR form); 0 (default): none     */
 } bc_plan_opts;
 
 /* Execution of BC_FORM_BATCHED (bc_plan_opts.batch_mode). */
@@ -403,6 +406,34 @@ bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs,
 bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs,
                         void* const* dev_ptrs, void* const* slot_ptrs,
                         void* stream);
+
+/*
+ * Boundary conditions fused with the stencil that reads them (Sec. IV-C:
+ * the boundary rows only feed the next stencil).  One launch computes, for
+ * every data value x of every slot,
+ *     out[x] = sum_p coeffs[p] * f(x + offsets[p])
+ * where f is the field as bc_apply leaves it: data values as stored,
+ * covered ghost values evaluated from their row of A and b where the
+ * stencil reads them, uncovered ghost values as stored.  The same launch
+ * writes every covered ghost value of the fields (bit for bit as bc_apply
+ * does for copies and zero rows), so afterwards the fields are those of a
+ * bc_apply.  With a plan from bc_plan_create_pruned for the same stencil,
+ * only the live ghosts are written.
+ * slot_ptrs: the fields (device array, as bc_apply); out_ptrs: a device
+ * array of nslots device pointers laid out with the same strides as the
+ * fields, whose data values receive the stencil (ghost values of out are
+ * not touched; out must not overlap the fields).  offsets: npoints triples
+ * (di, dj, dk), coeffs: npoints FP64 weights (rounded to the plan's dtype),
+ * both host memory read during the call (they travel as launch
+ * parameters: no allocation, graph-capturable).  Each point's sum runs in
+ * the order of the points.  Needs bc_plan_opts.stencil_fusion = 1 at
+ * creation (else BC_ERR_UNSUPPORTED, as for plans with Sync rows);
+ * BC_ERR_INVALID_ARG for npoints outside 1..125 or a non-finite weight;
+ * BC_ERR_HALO_TOO_WIDE when an offset reaches past a block's ghost width.
+ */
+bc_status bc_apply_stencil(bc_plan* plan, void* const* slot_ptrs, void* const* out_ptrs,
+                           const int32_t* offsets, const double* coeffs, int32_t npoints,
+                           void* stream);
 
 /*
  * Time candidate executions of BC_FORM_BATCHED on the caller's fields

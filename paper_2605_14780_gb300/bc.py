@@ -61,7 +61,7 @@ class BcPlanOpts(ctypes.Structure):
                 ("strict_cover", c_i32), ("no_adjoint", c_i32),
                 ("no_runs", c_i32), ("host_only", c_i32), ("ghost_sweeps", c_i32),
                 ("batch_mode", c_i32), ("scalar_runs", c_i32), ("level_chunk", c_i32),
-                ("unstaged_interp", c_i32)]
+                ("unstaged_interp", c_i32), ("stencil_fusion", c_i32)]
 
 
 class BcStats(ctypes.Structure):
@@ -90,6 +90,7 @@ SIGNATURES = {
     "bc_apply_form": (c_i32, [c_vp, c_vp, c_i32, c_vp]),
     "bc_apply_adjoint": (c_i32, [c_vp, c_vp, c_vp]),
     "bc_apply_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "bc_apply_stencil": (c_i32, [c_vp, c_vp, c_vp, P_i32, P_dbl, c_i32, c_vp]),
     "bc_plan_autotune": (c_i32, [c_vp, c_vp, c_vp]),
     "bc_plan_const_values": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), P_i64]),
     "bc_plan_set_const": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
@@ -372,6 +373,19 @@ class Plan:
     def adjoint(self, slot_table, stream=None):
         _check(self._lib.bc_apply_adjoint(self._h, c_vp(slot_table.data_ptr()),
                                           _stream_handle(stream)))
+
+    def apply_stencil(self, slot_table, out_table, offsets, coeffs, stream=None):
+        """Ghost fill fused with the stencil ``sum_p coeffs[p] f(x +
+        offsets[p])`` (``bc_apply_stencil``): ``out_table`` holds the output
+        slots (same layout as the fields); the fields' covered ghosts are
+        written as by :meth:`apply`."""
+        off = np.ascontiguousarray(np.asarray(offsets, np.int32).reshape(-1, 3))
+        cf = np.ascontiguousarray(np.asarray(coeffs, np.float64).reshape(-1))
+        if len(cf) != len(off):
+            raise ValueError("one weight per stencil point")
+        _check(self._lib.bc_apply_stencil(self._h, c_vp(slot_table.data_ptr()),
+                                          c_vp(out_table.data_ptr()), _ptr(off, c_i32),
+                                          _ptr(cf, c_dbl), len(cf), _stream_handle(stream)))
 
     def apply_host(self, host_ptrs, dev_ptrs, slot_table, stream=None):
         H = (c_vp * len(host_ptrs))(*host_ptrs)

@@ -168,6 +168,40 @@ cudaError_t launch_cs_geometry(const CsPanels& pan, const int4* cells,
                                int ncells, int4* idx, double* w, double* m,
                                unsigned* err, cudaStream_t s);
 
+// Ghost fill fused with a stencil (fused.cu).  One descriptor per slot;
+// the launch's CTAs are cut per slot (cta0: the slot's first CTA), each
+// covering kFuseThreads values: the slot's data values (stencil outputs)
+// first, then its ghost-frame values (ghost fills).
+constexpr int kFuseThreads = 256;
+constexpr int kFuseMaxPoints = 125;  // a 5 x 5 x 5 box
+struct FuseSlot {
+  int32_t n[3], h[3];
+  int32_t L, lfast;   // levels; 1: levels fastest in the value order
+  int64_t s[3], ls;   // element strides of the axes and of the levels (0: one level)
+  int64_t fbase;      // the slot's first frame-table entry
+  int64_t cta0;       // the slot's first CTA
+  int32_t nd, nf;     // data cells and ghost-frame cells of one level
+  FastDiv dL, dnd, dnf, dn0, dn01;  // division by L, nd, nf, n[0], n[0] * n[1]
+};
+struct FuseCtx {
+  int32_t nslots;
+  const FuseSlot* slot;
+  const int32_t* frame_row;  // per slot and frame cell: the row, or -1
+  const int32_t* rptr;       // level-0 rows of A: entries [rptr[r], rptr[r + 1])
+  const int32_t* eslot;
+  const int32_t* eoff;
+  const void* val;           // entry values and row constants b, plan dtype
+  const void* rhs;
+  const int32_t* slot_ls;    // level stride of every slot
+};
+struct FuseStencil {
+  int32_t n;
+  int8_t o[kFuseMaxPoints][3];
+  double c[kFuseMaxPoints];
+};
+cudaError_t launch_fused(int dtype, const FuseCtx& F, const FuseStencil& st, void* const* slots,
+                         void* const* outs, int64_t nctas, cudaStream_t s);
+
 // Sets the message bc_last_error() returns on this thread (plan.cpp).
 void set_last_error(const char* msg);
 

@@ -194,7 +194,9 @@ struct bc_plan {
   std::vector<int> sub_begin, sub_end;
   int type_begin[5] = {0, 0, 0, 0, 0}, type_end[5] = {0, 0, 0, 0, 0};
   // device
-  DevBuf tables, work;
+  DevBuf tables, work, fuse;
+  FuseCtx fuse_ctx{};
+  int64_t fuse_ctas = 0;
   Ctx ctx{};
   Item* d_items = nullptr;
   Item* d_fam[kFamilies] = {nullptr, nullptr, nullptr, nullptr};
@@ -1688,6 +1690,8 @@ bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
     return fail(BC_ERR_INVALID_ARG, "batch_mode must be 0, BC_BATCH_PERSISTENT or BC_BATCH_FAMILIES");
   if (o.scalar_runs < 0 || o.scalar_runs > 1)
     return fail(BC_ERR_INVALID_ARG, "scalar_runs must be 0 or 1");
+  if (o.stencil_fusion < 0 || o.stencil_fusion > 1)
+    return fail(BC_ERR_INVALID_ARG, "stencil_fusion must be 0 or 1");
   if (o.unstaged_interp < 0 || o.unstaged_interp > 1)
     return fail(BC_ERR_INVALID_ARG, "unstaged_interp must be 0 or 1");
   if (o.level_chunk != 0 && o.level_chunk != 1 && o.level_chunk != 2 && o.level_chunk != 4 &&
@@ -1713,6 +1717,114 @@ size_t live_ghosts(const bc_block& B, const int32_t* off, int noff) {
         }
       }
   return n;
+}
+
+// Tables of bc_apply_stencil: per slot a descriptor and the row of every
+// ghost-frame cell (level 0, slab order: below, above, then per data plane
+// the bands below and above and the two side columns), and the level-0 rows
+// of A in CSR form, in the plan's dtype.
+bc_status build_fusion(bc_plan* P) {
+  const int S = P->esize;
+  std::vector<FuseSlot> slots(P->nslots);
+  int64_t fbase = 0, cta = 0;
+  for (int sl = 0; sl < P->nslots; ++sl) {
+    const bc_block& B = P->blocks[P->slot_block[sl]];
+    FuseSlot& f = slots[sl];
+    std::memset(&f, 0, sizeof(f));
+    for (int d = 0; d < 3; ++d) {
+      f.n[d] = B.n[d];
+      f.h[d] = B.h[d];
+      f.s[d] = B.stride[d];
+    }
+    f.L = B.nlevels;
+    f.ls = B.nlevels > 1 ? B.level_stride : 0;
+    f.lfast = B.nlevels > 1 && B.level_stride == 1;
+    const int64_t F = (int64_t)(B.n[0] + 2 * B.h[0]) * (B.n[1] + 2 * B.h[1]) * (B.n[2] + 2 * B.h[2]);
+    const int64_t D = (int64_t)B.n[0] * B.n[1] * B.n[2];
+    if (F * B.nlevels >= INT32_MAX)
+      return fail(BC_ERR_UNSUPPORTED, "stencil fusion: slot %d has 2^31 values or more", sl);
+    f.nd = (int32_t)D;
+    f.nf = (int32_t)(F - D);
+    f.dL = make_div((uint32_t)f.L);
+    f.dnd = make_div((uint32_t)std::max<int64_t>(D, 1));
+    f.dnf = make_div((uint32_t)std::max<int64_t>(F - D, 1));
+    f.dn0 = make_div((uint32_t)B.n[0]);
+    f.dn01 = make_div((uint32_t)B.n[0] * (uint32_t)B.n[1]);
+    f.fbase = fbase;
+    f.cta0 = cta;
+    fbase += F - D;
+    cta += ((F * B.nlevels) + kFuseThreads - 1) / kFuseThreads;
+  }
+  P->fuse_ctas = cta;
+  // frame index of a ghost cell (the device's frame_index)
+  auto frame_index = [](const FuseSlot& f, int i, int j, int k) -> int64_t {
+    const int64_t F0 = f.n[0] + 2 * f.h[0], F1 = f.n[1] + 2 * f.h[1];
+    const int64_t slab = (int64_t)f.h[2] * F1 * F0;
+    if (k < 0) return ((int64_t)(k + f.h[2]) * F1 + (j + f.h[1])) * F0 + (i + f.h[0]);
+    if (k >= f.n[2]) return slab + ((int64_t)(k - f.n[2]) * F1 + (j + f.h[1])) * F0 + (i + f.h[0]);
+    const int64_t plane = F1 * F0 - (int64_t)f.n[1] * f.n[0];
+    const int64_t base = 2 * slab + (int64_t)k * plane;
+    if (j < 0) return base + (int64_t)(j + f.h[1]) * F0 + (i + f.h[0]);
+    if (j >= f.n[1]) return base + (int64_t)(f.h[1] + j - f.n[1]) * F0 + (i + f.h[0]);
+    const int64_t b2 = base + 2 * (int64_t)f.h[1] * F0 + (int64_t)j * 2 * f.h[0];
+    return i < 0 ? b2 + (i + f.h[0]) : b2 + f.h[0] + (i - f.n[0]);
+  };
+  std::vector<int32_t> frame((size_t)fbase, -1);
+  const ExplicitRows& R = P->rows;
+  if ((int64_t)R.val.size() >= INT32_MAX)
+    return fail(BC_ERR_UNSUPPORTED, "stencil fusion: 2^31 row entries or more");
+  for (size_t r = 0; r < R.slot.size(); ++r) {
+    const int sl = R.slot[r];
+    const bc_block& B = P->blocks[P->slot_block[sl]];
+    int i, j, k;
+    if (!decode_cell(B, R.off[r], i, j, k) || in_data(B, i, j, k))
+      return fail(BC_ERR_UNSUPPORTED, "stencil fusion: a row is not a ghost cell");
+    frame[(size_t)(slots[sl].fbase + frame_index(slots[sl], i, j, k))] = (int32_t)r;
+  }
+  std::vector<int32_t> rptr(R.ptr.size()), eslot(R.cslot.begin(), R.cslot.end()), eoff(R.coff.size());
+  for (size_t r = 0; r < R.ptr.size(); ++r) rptr[r] = (int32_t)R.ptr[r];
+  for (size_t e = 0; e < R.coff.size(); ++e) eoff[e] = (int32_t)R.coff[e];
+  Layout L;
+  const size_t o_s = L.take(slots.size() * sizeof(FuseSlot));
+  const size_t o_f = L.take(frame.size() * 4);
+  const size_t o_p = L.take(rptr.size() * 4);
+  const size_t o_es = L.take(eslot.size() * 4);
+  const size_t o_eo = L.take(eoff.size() * 4);
+  const size_t o_v = L.take(R.val.size() * S);
+  const size_t o_b = L.take(R.rhs.size() * S);
+  std::vector<char> host(L.off + 256, 0);
+  put_raw(host, o_s, slots);
+  put_raw(host, o_f, frame);
+  put_raw(host, o_p, rptr);
+  put_raw(host, o_es, eslot);
+  put_raw(host, o_eo, eoff);
+  if (P->dtype == BC_F64) {
+    put_dtype<double>(host, o_v, R.val);
+    put_dtype<double>(host, o_b, R.rhs);
+  } else {
+    put_dtype<float>(host, o_v, R.val);
+    put_dtype<float>(host, o_b, R.rhs);
+  }
+  cudaError_t e = dev_malloc(&P->fuse.base, host.size());
+  if (e != cudaSuccess) {
+    P->fuse.base = nullptr;
+    return cuda_fail(e, "stencil fusion tables");
+  }
+  P->fuse.bytes = host.size();
+  if ((e = cudaMemcpy(P->fuse.base, host.data(), host.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "stencil fusion tables upload");
+  char* b = static_cast<char*>(P->fuse.base);
+  FuseCtx& F = P->fuse_ctx;
+  F.nslots = P->nslots;
+  F.slot = reinterpret_cast<const FuseSlot*>(b + o_s);
+  F.frame_row = reinterpret_cast<const int32_t*>(b + o_f);
+  F.rptr = reinterpret_cast<const int32_t*>(b + o_p);
+  F.eslot = reinterpret_cast<const int32_t*>(b + o_es);
+  F.eoff = reinterpret_cast<const int32_t*>(b + o_eo);
+  F.val = b + o_v;
+  F.rhs = b + o_b;
+  F.slot_ls = P->ctx.slot_ls;
+  return BC_OK;
 }
 
 // FNV-1a over the bytes that decide what the autotuner measures: dtype,
@@ -1910,6 +2022,8 @@ bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_
   if (!P->opts.host_only) {
     if ((st = upload_tables(P)) != BC_OK) return st;
     if ((st = upload_work(P)) != BC_OK) return st;
+    if (P->opts.stencil_fusion && P->sync.row.empty() && (st = build_fusion(P)) != BC_OK)
+      return st;
   }
   compute_stats(P);
   return BC_OK;
@@ -2566,6 +2680,41 @@ bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs, void* stream) 
     e = launch_family(plan->dtype, FAM_STRUCT, c, plan->d_adj_zero,
                       (int)plan->adj_zero.size(), T, stream_grid(plan, FAM_STRUCT), s);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+  return BC_OK;
+}
+
+bc_status bc_apply_stencil(bc_plan* plan, void* const* slot_ptrs, void* const* out_ptrs,
+                           const int32_t* offsets, const double* coeffs, int32_t npoints,
+                           void* stream) {
+  TraceRange trace("bc_apply_stencil");
+  if (!plan) return fail(BC_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->opts.host_only) return fail(BC_ERR_UNSUPPORTED, "host_only plan");
+  if (!plan->fuse.base)
+    return fail(BC_ERR_UNSUPPORTED, plan->sync.row.empty()
+                                        ? "plan built without bc_plan_opts.stencil_fusion"
+                                        : "stencil fusion does not take Sync rows");
+  if ((!slot_ptrs || !out_ptrs) && plan->nslots > 0)
+    return fail(BC_ERR_INVALID_ARG, "slot_ptrs or out_ptrs is NULL");
+  if (npoints < 1 || npoints > kFuseMaxPoints || !offsets || !coeffs)
+    return fail(BC_ERR_INVALID_ARG, "need 1..%d stencil points", kFuseMaxPoints);
+  FuseStencil st;
+  std::memset(&st, 0, sizeof(st));
+  st.n = npoints;
+  for (int p = 0; p < npoints; ++p) {
+    if (!std::isfinite(coeffs[p])) return fail(BC_ERR_INVALID_ARG, "stencil weight %d is not finite", p);
+    for (int d = 0; d < 3; ++d) {
+      const int o = offsets[3 * p + d];
+      for (const bc_block& B : plan->blocks)
+        if (o > B.h[d] || o < -B.h[d])
+          return fail(BC_ERR_HALO_TOO_WIDE, "stencil point %d reaches %d cells along axis %d, "
+                      "past a ghost width of %d", p, o, d, B.h[d]);
+      st.o[p][d] = (int8_t)o;
+    }
+    st.c[p] = coeffs[p];
+  }
+  cudaError_t e = launch_fused(plan->dtype, plan->fuse_ctx, st, slot_ptrs, out_ptrs,
+                               plan->fuse_ctas, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "stencil launch");
   return BC_OK;
 }
 

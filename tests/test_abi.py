@@ -46,7 +46,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(bc.BcBlock) == 64
-    assert ctypes.sizeof(bc.BcPlanOpts) == 52
+    assert ctypes.sizeof(bc.BcPlanOpts) == 56
     # the sub-matrix struct: offsets of a few fields against the C layout
     assert bc.BcSubmatrix.comps.offset == 40
     assert bc.BcSubmatrix.row_ptr.offset > bc.BcSubmatrix.itp_rot.offset
