@@ -306,9 +306,14 @@ typedef enum bc_batch_mode {
                               the plan, one per stream the plan is applied
                               on; past 64 streams an apply runs as
                               BC_BATCH_FAMILIES                             */
-  BC_BATCH_FAMILIES = 2    /* one plain-grid kernel per kernel family
+  BC_BATCH_FAMILIES = 2,   /* one plain-grid kernel per kernel family
                               (structured, interpolation, CSR), forked onto
                               plan-owned streams and joined                 */
+  BC_BATCH_FAMILIES_PERSISTENT = 3 /* one persistent kernel per family, forked
+                              and joined, each claiming its family's items
+                              from its own counter; the SMs are shared out
+                              between the families in proportion to their
+                              work, so the kernels run side by side        */
 } bc_batch_mode;
 
 typedef struct bc_plan bc_plan;

@@ -155,6 +155,8 @@ int resident_ctas(int dtype, int family, int threads);
 cudaError_t launch_persistent(int dtype, int family, const Ctx& ctx, const Item* items,
                               int nitems, int threads, int ctas_per_sm, int sms,
                               unsigned* counter, cudaStream_t s);
+// CTAs of the persistent kernel of `family` that fit on an SM at once.
+int persistent_fit(int dtype, int family, int threads);
 
 // Cubed-sphere geometry (geometry.cu).
 struct CsPanels {

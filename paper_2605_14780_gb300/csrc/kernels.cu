@@ -234,7 +234,7 @@ __device__ void structured_runs(const Item& it, const Ptrs& P, const Ctx& c, int
 // allocation); full chunks are stored as one vector, the chunks at the ends
 // of a run element by element, so no value outside a run is written.
 // ---------------------------------------------------------------------------
-constexpr int kVecUnroll = 4;
+constexpr int kVecUnroll = 2;  // 4 spills under the 48-register budget
 constexpr int kNoChunk = INT_MIN;  // a lane's chunk slot past the item's last chunk
 
 enum RunOp : int { RUN_ZERO = 0, RUN_COPY = 1, RUN_ADD = 2 };
@@ -1275,10 +1275,38 @@ cudaError_t persist_any(int fam, const Ctx& c, const Item* items, int nitems, in
   switch (fam) {
     case FAM_STRUCT:
       return persist_fam<T, FAM_STRUCT>(c, items, nitems, threads, ctas_per_sm, sms, ctr, s);
+    case FAM_INTERP:
+      return persist_fam<T, FAM_INTERP>(c, items, nitems, threads, ctas_per_sm, sms, ctr, s);
+    case FAM_CSR:
+      return persist_fam<T, FAM_CSR>(c, items, nitems, threads, ctas_per_sm, sms, ctr, s);
     case FAM_ADJ:
       return persist_fam<T, FAM_ADJ>(c, items, nitems, threads, ctas_per_sm, sms, ctr, s);
     default:
       return persist_fam<T, FAM_ALL>(c, items, nitems, threads, ctas_per_sm, sms, ctr, s);
+  }
+}
+
+template <typename T, int FAM>
+int persist_fit_fam(int threads) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (threads) {
+    case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persist<T, 64, FAM>, 64, 0); break;
+    case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persist<T, 128, FAM>, 128, 0); break;
+    case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persist<T, 512, FAM>, 512, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persist<T, 256, FAM>, 256, 0); break;
+  }
+  return e == cudaSuccess && n > 0 ? n : 1;
+}
+
+template <typename T>
+int persist_fit_any(int fam, int threads) {
+  switch (fam) {
+    case FAM_STRUCT: return persist_fit_fam<T, FAM_STRUCT>(threads);
+    case FAM_INTERP: return persist_fit_fam<T, FAM_INTERP>(threads);
+    case FAM_CSR: return persist_fit_fam<T, FAM_CSR>(threads);
+    case FAM_ADJ: return persist_fit_fam<T, FAM_ADJ>(threads);
+    default: return persist_fit_fam<T, FAM_ALL>(threads);
   }
 }
 
@@ -1352,6 +1380,11 @@ cudaError_t launch_persistent(int dtype, int family, const Ctx& ctx, const Item*
   return dtype == 1
              ? persist_any<double>(family, ctx, items, nitems, threads, ctas_per_sm, sms, counter, s)
              : persist_any<float>(family, ctx, items, nitems, threads, ctas_per_sm, sms, counter, s);
+}
+
+int persistent_fit(int dtype, int family, int threads) {
+  return dtype == 1 ? persist_fit_any<double>(family, threads)
+                    : persist_fit_any<float>(family, threads);
 }
 
 int resident_ctas(int dtype, int family, int threads) {

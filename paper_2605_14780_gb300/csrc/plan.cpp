@@ -1464,7 +1464,7 @@ bc_status upload_tables(bc_plan* P) {
   const size_t o_ycs = L.take(Y.cstage.size() * 4);
   const size_t o_ycw = L.take(Y.cw.size() * S);
   const size_t o_yst = L.take((size_t)Y.stage * S);
-  const size_t o_ctr = L.take(2 * kCounterStreams * sizeof(unsigned));  // zero
+  const size_t o_ctr = L.take(2 * kFamilies * kCounterStreams * sizeof(unsigned));  // zero
   std::vector<char> host(L.off + 256, 0);
   put_raw(host, o_yr, Y.row);
   put_raw(host, o_yp, Y.ptr);
@@ -1686,8 +1686,8 @@ bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
   if (o.ghost_sweeps < 0 || o.ghost_sweeps > kMaxGhostSweeps)
     return fail(BC_ERR_INVALID_ARG, "ghost_sweeps must be in 0..%d", kMaxGhostSweeps);
   if (o.batch_mode == 0) o.batch_mode = BC_BATCH_FAMILIES;
-  if (o.batch_mode != BC_BATCH_PERSISTENT && o.batch_mode != BC_BATCH_FAMILIES)
-    return fail(BC_ERR_INVALID_ARG, "batch_mode must be 0, BC_BATCH_PERSISTENT or BC_BATCH_FAMILIES");
+  if (o.batch_mode < BC_BATCH_PERSISTENT || o.batch_mode > BC_BATCH_FAMILIES_PERSISTENT)
+    return fail(BC_ERR_INVALID_ARG, "batch_mode must be 0 or a bc_batch_mode");
   if (o.scalar_runs < 0 || o.scalar_runs > 1)
     return fail(BC_ERR_INVALID_ARG, "scalar_runs must be 0 or 1");
   if (o.stencil_fusion < 0 || o.stencil_fusion > 1)
@@ -2043,10 +2043,31 @@ unsigned* counter_for(bc_plan* P, cudaStream_t stream) {
   std::lock_guard<std::mutex> lock(P->ctr_mu);
   void* key = static_cast<void*>(stream);
   for (size_t i = 0; i < P->ctr_streams.size(); ++i)
-    if (P->ctr_streams[i] == key) return P->d_ctr + 2 * i;
+    if (P->ctr_streams[i] == key) return P->d_ctr + 2 * kFamilies * i;
   if ((int)P->ctr_streams.size() >= kCounterStreams) return nullptr;
   P->ctr_streams.push_back(key);
-  return P->d_ctr + 2 * (P->ctr_streams.size() - 1);
+  return P->d_ctr + 2 * kFamilies * (P->ctr_streams.size() - 1);
+}
+
+// Resident CTAs per SM of each family's persistent kernel when the families
+// run side by side: shares of the SM in proportion to the family's bytes,
+// at least one CTA each.
+void persistent_split(bc_plan* P, int per_sm[kFamilies]) {
+  double bytes[kFamilies] = {0, 0, 0, 0}, total = 0;
+  for (int f = 0; f < kFamilies; ++f) {
+    for (const Item& it : P->fam_items[f]) {
+      double v = it.mode == MODE_RUNS ? 0 : (double)it.nunits * (it.mode >= 2 ? it.mode : 1);
+      if (it.mode == MODE_RUNS)
+        for (int r = it.u0; r < it.u0 + it.nunits; ++r) v += P->runs[(size_t)r].z;
+      if (it.mode == MODE_TILE) v = (double)it.nunits * it.nl;
+      bytes[f] += v * (it.kind == IK_MAP ? 2 : it.kind == IK_CSR ? 1 + it.p : it.kind >= IK_INTERP ? 3 : 1);
+    }
+    total += bytes[f];
+  }
+  for (int f = 0; f < kFamilies; ++f) {
+    const int fit = persistent_fit(P->dtype, f, P->opts.threads);
+    per_sm[f] = total > 0 ? std::max(1, (int)(fit * bytes[f] / total)) : 1;
+  }
 }
 
 bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t s) {
@@ -2056,8 +2077,9 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
   cudaError_t e = cudaSuccess;
   const int T = P->opts.threads;
   unsigned* ctr = nullptr;
-  if (form == BC_FORM_BATCHED && P->opts.batch_mode == BC_BATCH_PERSISTENT)
+  if (form == BC_FORM_BATCHED && P->opts.batch_mode != BC_BATCH_FAMILIES)
     ctr = counter_for(P, s);
+  const bool all_in_one = ctr && P->opts.batch_mode == BC_BATCH_PERSISTENT;
   // Sync rows read the input data: evaluate them into the staging buffer
   // while the ghost kernels run (they write only ghosts), write them back
   // after every kernel that reads data has run
@@ -2065,7 +2087,7 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
   if (sync && form != BC_FORM_BATCHED &&
       (e = launch_sync(P->dtype, SYNC_ROWS, P->sync_ctx, slots, c.slot_ls, s)) != cudaSuccess)
     return cuda_fail(e, "Sync rows");
-  if (ctr) {
+  if (all_in_one) {
     // one persistent launch over every item; the Sync rows beside it
     cudaStream_t ys = P->aux[kFamilies - 2];
     if (sync) {
@@ -2094,11 +2116,16 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
           (e = cudaEventRecord(P->ev_join[kFamilies - 2], ys)) != cudaSuccess)
         return cuda_fail(e, "Sync rows");
     }
+    int split[kFamilies] = {0, 0, 0, 0};
+    if (ctr) persistent_split(P, split);
     for (int t = 0; t < nf && e == cudaSuccess; ++t) {
       cudaStream_t st = t == 0 ? s : P->aux[t - 1];
       if (t > 0 && (e = cudaStreamWaitEvent(st, P->ev_fork, 0)) != cudaSuccess) break;
-      e = launch_family(P->dtype, fams[t], c, P->d_fam[fams[t]],
-                        (int)P->fam_items[fams[t]].size(), T, stream_grid(P, fams[t]), st);
+      const int f = fams[t];
+      e = ctr ? launch_persistent(P->dtype, f, c, P->d_fam[f], (int)P->fam_items[f].size(), T,
+                                  split[f], P->num_sms, ctr + 2 * f, st)
+              : launch_family(P->dtype, f, c, P->d_fam[f], (int)P->fam_items[f].size(), T,
+                              stream_grid(P, f), st);
       if (e == cudaSuccess && t > 0) e = cudaEventRecord(P->ev_join[t - 1], st);
     }
     for (int t = 1; t < nf && e == cudaSuccess; ++t)
@@ -2903,7 +2930,8 @@ bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) 
     int32_t bc_plan_opts::*field;
     std::vector<int32_t> values;
   };
-  std::vector<Knob> knobs = {{&bc_plan_opts::batch_mode, {BC_BATCH_PERSISTENT, BC_BATCH_FAMILIES}}};
+  std::vector<Knob> knobs = {{&bc_plan_opts::batch_mode,
+                              {BC_BATCH_FAMILIES, BC_BATCH_FAMILIES_PERSISTENT, BC_BATCH_PERSISTENT}}};
   if (runs) knobs.push_back({&bc_plan_opts::scalar_runs, {0, 1}});
   knobs.push_back({&bc_plan_opts::units_per_lane, {1, 2, 4, 8}});
   knobs.push_back({&bc_plan_opts::threads, {128, 256}});

@@ -13,7 +13,7 @@ from paper_2605_14780_gb300 import bc, synth
 
 pytestmark = pytest.mark.gpu
 
-P, F = bc.BC_BATCH_PERSISTENT, bc.BC_BATCH_FAMILIES
+P, F, FP = bc.BC_BATCH_PERSISTENT, bc.BC_BATCH_FAMILIES, bc.BC_BATCH_FAMILIES_PERSISTENT
 
 
 def _packed(arrays, shift, layout):
@@ -58,6 +58,7 @@ def _adjoint(w, plan, cot, shift, layout):
 
 OPTS = [{"batch_mode": P}, {"batch_mode": P, "scalar_runs": 1},
         {"batch_mode": F}, {"batch_mode": F, "scalar_runs": 1},
+        {"batch_mode": FP}, {"batch_mode": FP, "threads": 256},
         {"batch_mode": P, "threads": 256, "units_per_lane": 8},
         {"batch_mode": P, "units_per_lane": 1, "ctas_per_sm": 1}]
 
@@ -89,7 +90,7 @@ def test_vector_runs_on_every_alignment(layout, dtype, shift):
 
 
 @pytest.mark.parametrize("chunk", [1, 2, 4, 8])
-@pytest.mark.parametrize("mode", [P, F])
+@pytest.mark.parametrize("mode", [P, F, FP])
 def test_level_chunks(chunk, mode):
     """Every levels-per-lane split of the chunked unit order (levels
     outermost: interpolation with rotation, CSR corners, and the transpose
@@ -107,7 +108,8 @@ def test_level_chunks(chunk, mode):
     assert np.array_equal(bits(adj), bits(adj0))
 
 
-def test_persistent_launches_on_several_streams():
+@pytest.mark.parametrize("mode", [P, FP])
+def test_persistent_launches_on_several_streams(mode):
     """Applies of one persistent plan alternating over three streams (one
     work counter each) and a captured graph replayed on another stream,
     every result against the oracle."""
@@ -116,7 +118,7 @@ def test_persistent_launches_on_several_streams():
                        h=2, seed=35, dtype="f32")
     op = build_operator(w)
     sets = [_packed(w["fields"], k, "innermost") for k in range(3)]
-    plan = bc.plan_for_workload(w, sets[0][1], {"batch_mode": P})
+    plan = bc.plan_for_workload(w, sets[0][1], {"batch_mode": mode})
     streams = [torch.cuda.Stream() for _ in range(3)]
     tables = [bc.slot_table(v) for _, v in sets]
     for rep in range(4):
@@ -143,6 +145,7 @@ def test_stats_count_one_launch_for_the_persistent_form():
     _, ts = _packed(w["fields"], 0, "innermost")
     assert bc.plan_for_workload(w, ts, {"batch_mode": P}).stats()["launches_fwd"] == 1
     assert bc.plan_for_workload(w, ts, {"batch_mode": F}).stats()["launches_fwd"] == 2
+    assert bc.plan_for_workload(w, ts, {"batch_mode": FP}).stats()["launches_fwd"] == 2
 
 
 def test_autotune_result_cache(tmp_path, monkeypatch):
