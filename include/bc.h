@@ -571,6 +571,35 @@ bc_status bc_cubed_sphere_stencils_noalloc(int32_t N, int32_t h, int32_t p,
                                            int32_t* axis, double* w,
                                            double* rot);
 
+/*
+ * Packing of block boxes for an exchange between processes (Sec. V-B: a
+ * process that owns only some blocks receives, for every remote block its
+ * boundary rows read, the bounding box of the cells read).  A bc_box is the
+ * cell range [lo, hi) of one block of `grid` (inside its full region),
+ * taken with every component and level.  bc_pack_create checks the boxes
+ * and uploads their descriptors (synchronous; allocates); bc_pack_run then
+ * copies the boxes from the fields (slot_ptrs: device array of the grid's
+ * nslots slot pointers, as bc_apply) into `buffer` (device memory of
+ * bc_pack_size() elements of the grid's dtype): box after box, each stored
+ * [component][level][k][j][i] -- the layout of a block of extents hi - lo,
+ * no ghost cells, levels outermost.  bc_pack_run allocates nothing and does
+ * not synchronise (graph-capturable); the values are copied bit for bit.
+ * Errors: BC_ERR_INVALID_ARG (NULL, an empty box, a block out of range),
+ * BC_ERR_OUT_OF_RANGE (a box outside its block's full region),
+ * BC_ERR_UNSUPPORTED (a box of 2^31 values or more), BC_ERR_NOMEM / CUDA.
+ */
+typedef struct bc_box {
+  int32_t block;
+  int32_t lo[3];
+  int32_t hi[3];
+} bc_box;
+typedef struct bc_pack bc_pack;
+bc_status bc_pack_create(const bc_grid* grid, const bc_box* boxes, int32_t nboxes,
+                         bc_pack** out);
+int64_t bc_pack_size(const bc_pack* pack);
+bc_status bc_pack_run(bc_pack* pack, void* const* slot_ptrs, void* buffer, void* stream);
+void bc_pack_destroy(bc_pack* pack);
+
 /* Release the plan and its device tables (NULL is a no-op). */
 void bc_plan_destroy(bc_plan* plan);
 

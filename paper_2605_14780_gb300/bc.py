@@ -55,6 +55,10 @@ class BcSubmatrix(ctypes.Structure):
                 ("nquad", c_i32)]
 
 
+class BcBox(ctypes.Structure):
+    _fields_ = [("block", c_i32), ("lo", c_i32 * 3), ("hi", c_i32 * 3)]
+
+
 class BcPlanOpts(ctypes.Structure):
     _fields_ = [("units_per_lane", c_i32), ("unit_order", c_i32),
                 ("threads", c_i32), ("ctas_per_sm", c_i32),
@@ -100,6 +104,11 @@ SIGNATURES = {
                                    P_i32, P_i64, P_dbl, P_dbl]),
     "bc_cubed_sphere_stencils_noalloc": (c_i32, [c_i32, c_i32, c_i32, P_i32, P_i32,
                                                  P_i32, P_dbl, P_dbl]),
+    "bc_pack_create": (c_i32, [ctypes.POINTER(BcGrid), ctypes.POINTER(BcBox), c_i32,
+                               ctypes.POINTER(c_vp)]),
+    "bc_pack_size": (c_i64, [c_vp]),
+    "bc_pack_run": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "bc_pack_destroy": (None, [c_vp]),
     "bc_plan_destroy": (None, [c_vp]),
     "bc_status_string": (ctypes.c_char_p, [c_i32]),
     "bc_last_error": (ctypes.c_char_p, []),
@@ -396,6 +405,55 @@ class Plan:
     def autotune(self, slot_table, stream=None):
         _check(self._lib.bc_plan_autotune(self._h, c_vp(slot_table.data_ptr()),
                                           _stream_handle(stream)))
+
+
+def _grid(blocks, dtype):
+    cb = (BcBlock * max(1, len(blocks)))()
+    for k, b in enumerate(blocks):
+        cb[k].n[:] = list(b["n"])
+        cb[k].h[:] = list(b["h"])
+        cb[k].nlevels = b["nlevels"]
+        cb[k].ncomp = b["ncomp"]
+        cb[k].stride[:] = list(b["stride"])
+        cb[k].level_stride = b["level_stride"]
+    return BcGrid(BC_F64 if dtype == "f64" else BC_F32, len(blocks), cb), cb
+
+
+class Pack:
+    """Boxes of blocks packed into one buffer (``bc_pack_create`` /
+    ``bc_pack_run``): ``boxes`` is a list of ``(block, lo, hi)``; every
+    component and level of a box goes to the buffer, stored
+    [component][level][k][j][i], boxes back to back."""
+
+    def __init__(self, blocks, boxes, dtype):
+        lib = load_library()
+        self._lib = lib
+        self._h = None
+        grid, keep = _grid(blocks, dtype)
+        cbx = (BcBox * max(1, len(boxes)))()
+        for k, (b, lo, hi) in enumerate(boxes):
+            cbx[k].block = int(b)
+            cbx[k].lo[:] = [int(v) for v in lo]
+            cbx[k].hi[:] = [int(v) for v in hi]
+        handle = c_vp()
+        _check(lib.bc_pack_create(ctypes.byref(grid), cbx, len(boxes), ctypes.byref(handle)))
+        self._h = handle
+        self.size = int(lib.bc_pack_size(handle))
+
+    def run(self, slot_table, buffer, stream=None):
+        _check(self._lib.bc_pack_run(self._h, c_vp(slot_table.data_ptr()),
+                                     c_vp(buffer.data_ptr()), _stream_handle(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bc_pack_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class _DeviceArray:

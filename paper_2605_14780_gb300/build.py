@@ -1,6 +1,6 @@
 """Build ``libbcgb300.so`` in-tree with nvcc for sm_103a.
 
-Seven translation units compiled in parallel, then linked with the static
+Eight translation units compiled in parallel, then linked with the static
 CUDA runtime into ``paper_2605_14780_gb300/_lib/libbcgb300.so``.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 SOURCES = ["plan.cpp", "prune.cpp", "quadrature.cpp", "kernels.cu", "geometry.cu", "sync.cu",
-           "fused.cu"]
+           "fused.cu", "pack.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]

@@ -204,6 +204,21 @@ struct FuseStencil {
 cudaError_t launch_fused(int dtype, const FuseCtx& F, const FuseStencil& st, void* const* slots,
                          void* const* outs, int64_t nctas, cudaStream_t s);
 
+// Box packing (pack.cu): one descriptor per box; CTAs are cut per box.
+constexpr int kPackThreads = 256;
+struct PackBox {
+  int32_t slot0;          // slot of component 0 of the box's block
+  int32_t lo[3], e[3];    // first cell (data coordinates) and extents
+  int32_t L, ncomp;
+  int64_t s[3], ls;       // element strides of the block (ls: 0 for one level)
+  int64_t dst;            // first buffer element of the box
+  int64_t count;          // values: ncomp * L * e[0] * e[1] * e[2]
+  int64_t cta0;           // the box's first CTA
+  FastDiv d0, d1, d2, dL; // division by e[0], e[1], e[2], L
+};
+cudaError_t launch_pack(int esize, const PackBox* boxes, int nboxes, int64_t nctas,
+                        void* const* slots, void* buf, cudaStream_t s);
+
 // Sets the message bc_last_error() returns on this thread (plan.cpp).
 void set_last_error(const char* msg);
 

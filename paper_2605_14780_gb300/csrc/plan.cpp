@@ -2745,6 +2745,102 @@ bc_status bc_apply_stencil(bc_plan* plan, void* const* slot_ptrs, void* const* o
   return BC_OK;
 }
 
+}  // extern "C"
+
+struct bc_pack {
+  int esize = 4;
+  int64_t size = 0, nctas = 0;
+  int nboxes = 0;
+  DevBuf boxes;
+};
+
+extern "C" {
+
+bc_status bc_pack_create(const bc_grid* grid, const bc_box* boxes, int32_t nboxes,
+                         bc_pack** out) {
+  if (!out) return fail(BC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid || !grid->blocks || grid->nblocks <= 0 || nboxes < 0 || (nboxes > 0 && !boxes))
+    return fail(BC_ERR_INVALID_ARG, "bad grid or box list");
+  if (grid->dtype != BC_F32 && grid->dtype != BC_F64) return fail(BC_ERR_INVALID_ARG, "bad dtype");
+  std::vector<int32_t> slot0(grid->nblocks);
+  int32_t ns = 0;
+  for (int b = 0; b < grid->nblocks; ++b) {
+    slot0[b] = ns;
+    ns += grid->blocks[b].ncomp;
+  }
+  std::vector<PackBox> desc(nboxes);
+  int64_t pos = 0, cta = 0;
+  for (int t = 0; t < nboxes; ++t) {
+    const bc_box& x = boxes[t];
+    if (x.block < 0 || x.block >= grid->nblocks)
+      return fail(BC_ERR_INVALID_ARG, "box %d: block %d out of range", t, x.block);
+    const bc_block& B = grid->blocks[x.block];
+    PackBox& d = desc[t];
+    std::memset(&d, 0, sizeof(d));
+    int64_t cells = 1;
+    for (int a = 0; a < 3; ++a) {
+      if (x.hi[a] <= x.lo[a]) return fail(BC_ERR_INVALID_ARG, "box %d is empty along axis %d", t, a);
+      if (x.lo[a] < -B.h[a] || x.hi[a] > B.n[a] + B.h[a])
+        return fail(BC_ERR_OUT_OF_RANGE, "box %d leaves block %d's full region", t, x.block);
+      d.lo[a] = x.lo[a];
+      d.e[a] = x.hi[a] - x.lo[a];
+      d.s[a] = B.stride[a];
+      cells *= d.e[a];
+    }
+    d.slot0 = slot0[x.block];
+    d.L = B.nlevels;
+    d.ncomp = B.ncomp;
+    d.ls = B.nlevels > 1 ? B.level_stride : 0;
+    d.count = cells * B.nlevels * B.ncomp;
+    if (d.count >= INT32_MAX) return fail(BC_ERR_UNSUPPORTED, "box %d holds 2^31 values or more", t);
+    // offsets relative to the slot pointer, which addresses cell (-h, -h, -h)
+    for (int a = 0; a < 3; ++a) d.lo[a] += B.h[a];
+    d.dst = pos;
+    d.cta0 = cta;
+    d.d0 = make_div((uint32_t)d.e[0]);
+    d.d1 = make_div((uint32_t)d.e[1]);
+    d.d2 = make_div((uint32_t)d.e[2]);
+    d.dL = make_div((uint32_t)d.L);
+    pos += d.count;
+    cta += (d.count + kPackThreads - 1) / kPackThreads;
+  }
+  std::unique_ptr<bc_pack> P(new (std::nothrow) bc_pack);
+  if (!P) return fail(BC_ERR_NOMEM, "host allocation");
+  P->esize = grid->dtype == BC_F64 ? 8 : 4;
+  P->size = pos;
+  P->nctas = cta;
+  P->nboxes = nboxes;
+  if (nboxes > 0) {
+    arm_fault_injection();
+    cudaError_t e = dev_malloc(&P->boxes.base, desc.size() * sizeof(PackBox));
+    if (e != cudaSuccess) {
+      P->boxes.base = nullptr;
+      return cuda_fail(e, "pack descriptors");
+    }
+    if ((e = cudaMemcpy(P->boxes.base, desc.data(), desc.size() * sizeof(PackBox),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "pack descriptors upload");
+  }
+  *out = P.release();
+  return BC_OK;
+}
+
+int64_t bc_pack_size(const bc_pack* pack) { return pack ? pack->size : 0; }
+
+bc_status bc_pack_run(bc_pack* pack, void* const* slot_ptrs, void* buffer, void* stream) {
+  if (!pack) return fail(BC_ERR_INVALID_ARG, "pack is NULL");
+  if (pack->nboxes == 0) return BC_OK;
+  if (!slot_ptrs || !buffer) return fail(BC_ERR_INVALID_ARG, "slot_ptrs or buffer is NULL");
+  cudaError_t e = launch_pack(pack->esize, static_cast<const PackBox*>(pack->boxes.base),
+                              pack->nboxes, pack->nctas, slot_ptrs, buffer,
+                              static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "pack launch");
+  return BC_OK;
+}
+
+void bc_pack_destroy(bc_pack* pack) { delete pack; }
+
 bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs, void* const* dev_ptrs,
                         void* const* slot_ptrs, void* stream) {
   TraceRange trace("bc_apply_host");
