@@ -2,13 +2,17 @@
 
 Headline workload: 512 uneven 2-D blocks (sides log-uniform in [16, 256],
 1-64 levels, h = 2, FP32), every edge drawing a halo copy, circular or
-symmetric map, zero padding or a CSR user matrix, corners zero.  One step is
-one batched, graph-captured launch of the whole operator.  The JSON line also
-carries the per-sub-matrix and per-kind launch forms, the end-to-end number
-through the host-buffer C-ABI call, the roofline of the dominant kernel, the
-FP64 oracle on the host cores, and the SM clocks seen during the timed loop.
+symmetric map, zero padding or a CSR user matrix, corners zero.  The plan is
+autotuned first (bc_plan_autotune; --no-autotune keeps its defaults); one
+step is one batched, graph-captured apply of the whole operator.  The JSON
+line also carries the per-sub-matrix and per-kind launch forms, the
+end-to-end number from host memory, the roofline of the dominant kernel, the
+FP64 oracle's product on the host cores, the other workloads of the scope
+table (with their sector-granular DRAM floors), the fused boundary-and-
+stencil workload, and the SM clocks seen during the timed loop.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --oracle-all     # the oracle on every workload, then exit
 
 Multi-GPU runs are independent replicas (the operator has no exchange step
 on one GPU's resident blocks): value = all ranks' ghost values / max time.
@@ -35,6 +39,7 @@ METRIC = ("ghost cells/s and HBM GB/s (% of 8 TB/s), batched vs per-BC "
 UNIT = "ghost values/s"
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 8000.0
+FP64_TFLOPS = 1.25  # non-tensor FP64 of the part (nominal)
 
 
 # ----------------------------------------------------------------------------
@@ -257,6 +262,9 @@ def measure_forward(w, device, stream, steps, warmup, layout="level_outermost",
            "layout": layout, "field_copies": ncopies}
     if floor:
         out["dram_floor"] = dram_floor(plan, w, copies[0][1], copies[0][0])
+        for g in (32, 64):
+            fb = out["dram_floor"][f"granule_{g}B_bytes"]
+            out["dram_floor"][f"frac_of_floor_{g}B"] = fb / (ms / 1e3) / 1e9 / hbm
     del gs
     if adjoint:
         ga = [capture(lambda t=t: plan.adjoint(t, stream=stream), stream) for t in tables]
@@ -272,6 +280,42 @@ def measure_forward(w, device, stream, steps, warmup, layout="level_outermost",
     import torch
     torch.cuda.empty_cache()
     return out
+
+
+def measure_fused(device, stream, steps, warmup, nblocks=16):
+    """The ghost fill fused with the 27-point operator (diagonal 26,
+    off-diagonals -1) on ``nblocks`` independent 128^3 FP64 blocks, x
+    periodic and zero elsewhere: one bc_apply_stencil per step.  FP64 on
+    this GPU: 27 fused multiply-adds per output make it bound by the FP64
+    pipes, not by HBM."""
+    from paper_2605_14780_gb300 import bc, synth
+    w = synth.hpcg_block(128, "P", seed=2, nblocks=nblocks)
+    offs = bc.box_stencil(3, 1)
+    cf = np.array([26.0 if tuple(o) == (0, 0, 0) else -1.0 for o in offs])
+    copies = field_copies(w, 2, device)
+    outs = field_copies(w, 2, device)
+    plan = bc.plan_for_workload(w, copies[0][1], {"stencil_fusion": 1})
+    tabs = [bc.slot_table(v) for _, v in copies]
+    otabs = [bc.slot_table(v) for _, v in outs]
+    gs = [capture(lambda k=k: plan.apply_stencil(tabs[k], otabs[k], offs, cf, stream=stream),
+                  stream) for k in range(2)]
+    per, tot = time_steps([g.replay for g in gs], steps, warmup, stream, 1)
+    ms = tot / steps
+    nd = nblocks * 128 ** 3
+    ng = nblocks * (130 ** 3 - 128 ** 3)
+    byts = (nd + ng) * 8 + (nd + ng) * 8   # read every value, write outputs and ghosts
+    flops = 2 * len(cf) * nd
+    st = plan.stats()
+    return {"workload": f"{nblocks} x 128^3 FP64 blocks, x periodic, 27-point operator",
+            "ms": ms, "outputs": nd, "ghost_values": int(st["ghost_values"]),
+            "outputs_per_s": nd / (ms / 1e3),
+            "useful_gbs": byts / (ms / 1e3) / 1e9,
+            "frac_of_measured_hbm": byts / (ms / 1e3) / 1e9 / measured_peaks()[0],
+            "fp64_tflops": flops / (ms / 1e3) / 1e12,
+            "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12,
+                         "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                         "frac": flops / (ms / 1e3) / 1e12 / FP64_TFLOPS,
+                         "peak_source": "nominal FP64 rate of the part (no measured FP64 peak)"}}
 
 
 def capture(fn, stream):
@@ -316,39 +360,45 @@ def time_steps(step_fns, steps, warmup, stream, world, min_warm_s=0.0):
 # the oracle on the host cores (CPU baseline / reference arm)
 # ----------------------------------------------------------------------------
 def oracle_timing(w, budget_s=12.0, max_reps=None):
-    from oracle.operator import apply, build_operator
+    """The FP64 oracle's product ``g = A x + b`` on the host cores, timed
+    alone: ``A`` (explicit CSR) and ``x`` (the data values in FP64) are built
+    first, outside the timing.  SciPy's CSR product runs on one core."""
+    from oracle.operator import build_operator
     t0 = time.time()
     op = build_operator(w)
+    x = op.layout.data_vector(w["fields"])
     t_build = time.time() - t0
     reps, t_apply = 0, 0.0
     while t_apply < budget_s and (max_reps is None or reps < max_reps):
         t1 = time.time()
-        apply(op, w["fields"])
+        g = op.A @ x + op.b
         t_apply += time.time() - t1
         reps += 1
+    del g
     nvals = len(op.rows)
     return {"value": nvals * reps / t_apply, "unit": UNIT, "cores": 1,
-            "kind": "oracle",
-            "sample": (f"full workload ({nvals} ghost values), {reps} FP64 "
-                       f"scipy-CSR applies in {t_apply:.1f} s after a "
-                       f"{t_build:.1f} s explicit assembly of A"),
-            "apply_s": t_apply / reps, "build_s": t_build}
+            "host_cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"full workload ({nvals} ghost values): {reps} FP64 SciPy CSR "
+                       f"products g = A x + b in {t_apply:.1f} s on one core (of "
+                       f"{os.cpu_count()}), after {t_build:.1f} s building A and x"),
+            "spmv_s": t_apply / reps, "build_s": t_build}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     w, desc = make_workload(args.workload)
-    from oracle.operator import apply, build_operator
+    from oracle.operator import build_operator
     t0 = time.time()
     op = build_operator(w)
+    x = op.layout.data_vector(w["fields"])
     t_build = time.time() - t0
     for _ in range(args.warmup):
-        apply(op, w["fields"])
+        op.A @ x + op.b
     times = []
     for _ in range(args.steps):
         t1 = time.time()
-        apply(op, w["fields"])
+        op.A @ x + op.b
         times.append(time.time() - t1)
     nvals = len(op.rows)
     value = nvals * len(times) / sum(times)
@@ -360,11 +410,24 @@ def run_reference(args, rank, world):
         "data": "synthetic",
         "config": {"workload": desc, "ghost_values": nvals},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1,
-                         "kind": "oracle",
-                         "sample": f"full workload, {len(times)} timed applies "
-                                   f"after {t_build:.1f} s of assembly"},
+                         "host_cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"full workload, {len(times)} timed FP64 SciPy CSR "
+                                   f"products g = A x + b on one core after "
+                                   f"{t_build:.1f} s building A and x"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))
+
+
+def oracle_all(args):
+    """The oracle's product timed on every workload of the scope table
+    (``--oracle-all``; several minutes)."""
+    out = {}
+    for name in ("tiny", "hpcg", "swe", "batching", "adjoint"):
+        w = make_workload_named(name)
+        out[name] = oracle_timing(w, budget_s=args.oracle_budget_s)
+        del w
+        print(json.dumps({name: out[name]}), flush=True)
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -396,7 +459,7 @@ def dram_floor(plan, w, views, buf):
 
     wr = expand(ex["row_slot"], ex["row_off"])
     rd = expand(ex["col_slot"], ex["col_off"])
-    out = {}
+    out = {"source_values": int(len(np.unique(rd)))}
     for g in (32, 64):
         per = g // esize
         wsec, wcnt = np.unique(wr // per, return_counts=True)
@@ -410,12 +473,13 @@ FAMILY_KINDS = {"structured (zero/const/map)": (0, 1, 2), "interpolation": (3,),
                 "csr": (4,)}
 
 
-def family_plans(w, tensors):
-    """One plan per kernel family over the same fields, to time each family's
-    kernel on its own."""
+def family_plans(w, tensors, opts=None):
+    """One plan per kernel family over the same fields (with the options
+    ``opts``), to time each family's kernel on its own."""
     from paper_2605_14780_gb300 import bc, specs
     subs = specs.submatrices(w)
     blocks = bc.block_descriptors(tensors, w["blocks"])
+    base = dict(opts or {}, no_adjoint=1, batch_mode=bc.BC_BATCH_FAMILIES)
     out = {}
 
     def family_kind(s):
@@ -427,7 +491,7 @@ def family_plans(w, tensors):
     for name, kinds in FAMILY_KINDS.items():
         part = [s for s in subs if family_kind(s) in kinds]
         if part:
-            out[name] = bc.Plan(blocks, part, w["dtype"], {"no_adjoint": 1})
+            out[name] = bc.Plan(blocks, part, w["dtype"], base)
     return out
 
 
@@ -445,8 +509,11 @@ def run_ours(args, rank, world, local):
     copies = field_copies(w, ncopies, device, args.layout)
     plan = bc.plan_for_workload(w, copies[0][1])
     tables = [bc.slot_table(v) for _, v in copies]
-    if args.autotune:
+    tune_s = None
+    if not args.no_autotune:
+        t0 = time.time()
         plan.autotune(tables[0])
+        tune_s = time.time() - t0
     st = plan.stats()
     nvals = st["ghost_values"]
     stream = torch.cuda.Stream(device)
@@ -473,7 +540,9 @@ def run_ours(args, rank, world, local):
     # -- each family kernel on its own: the roofline of the dominant one ----
     kernels = {}
     if not args.only_batched:
-        for name, fp in family_plans(w, copies[0][1]).items():
+        tuned = {"threads": st["form_threads"], "units_per_lane": st["units_per_lane"],
+                 "level_chunk": st["level_chunk"]}
+        for name, fp in family_plans(w, copies[0][1], tuned).items():
             fst = fp.stats()
             gs = graphs_for(fp)
             pk, tk = time_steps([g.replay for g in gs], min(args.steps, 500), 5,
@@ -506,21 +575,41 @@ def run_ours(args, rank, world, local):
         forms["speedup_batched_vs_per_bc"] = forms["per_bc"]["ms"] / t_step
         forms["speedup_batched_vs_typewide"] = forms["typewide"]["ms"] / t_step
 
-    # -- end to end through the host-buffer C-ABI call -----------------------
+    # -- end to end from host memory -----------------------------------------
+    # (a) the fields stay in pinned host memory and the plan's kernels read
+    #     their sources and write the ghosts through the host link (slot
+    #     pointers of mapped host memory; nothing is staged on the device);
+    # (b) bc_apply_host: whole slots copied to the device, applied, copied
+    #     back.
     e2e = None
     if not args.only_batched:
         host = torch.empty(copies[0][0].numel(), dtype=copies[0][0].dtype).pin_memory()
         host.copy_(copies[0][0].cpu())
-        hptrs = bc.slot_pointers(layout_views(host, w, args.layout))
+        hviews = layout_views(host, w, args.layout)
+        hptrs = bc.slot_pointers(hviews)
+        htable = torch.tensor(hptrs, dtype=torch.int64, device=device)
+        e2e_steps = max(3, min(args.steps, 50))
+        pz, totz = time_steps([lambda: plan.apply(htable, stream=stream)], e2e_steps, 3,
+                              stream, world)
+        z_ms = reduce_max(totz, world, device) / e2e_steps
         dptrs = bc.slot_pointers(copies[0][1])
-        e2e_steps = max(3, min(args.steps, 20))
+        c_steps = max(3, min(args.steps, 20))
         pe, tote = time_steps(
             [lambda: plan.apply_host(hptrs, dptrs, tables[0], stream=stream)],
-            e2e_steps, 2, stream, world)
-        e2e_ms = reduce_max(tote, world, device) / e2e_steps
-        e2e = {"value": nvals * world / (e2e_ms / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(field_bytes),
-               "d2h_bytes_per_step": int(field_bytes), "ms_per_step": e2e_ms}
+            c_steps, 2, stream, world)
+        e2e_ms = reduce_max(tote, world, device) / c_steps
+        src_values = dram_floor(plan, w, copies[0][1], copies[0][0])["source_values"]
+        e2e = {"value": nvals * world / (z_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(src_values * esize),
+               "d2h_bytes_per_step": int(nvals * esize), "ms_per_step": z_ms,
+               "path": ("fields in pinned host memory: one bc_apply whose kernels read "
+                        "the sources and write the ghost values through the host link "
+                        "(h2d = the distinct source values read, d2h = the ghost values "
+                        "written)"),
+               "copies": {"value": nvals * world / (e2e_ms / 1e3), "ms_per_step": e2e_ms,
+                          "h2d_bytes_per_step": int(field_bytes),
+                          "d2h_bytes_per_step": int(field_bytes),
+                          "path": "bc_apply_host: every slot copied in, applied, copied out"}}
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -529,8 +618,11 @@ def run_ours(args, rank, world, local):
         "dtype": w["dtype"], "data": "synthetic",
         "config": {"workload": desc, "ghost_values": int(nvals),
                    "layout": LAYOUT_DESC[args.layout],
-                   "form": "batched: one graph launch, one kernel per family, concurrent",
+                   "form": FORM_DESC.get(st["batch_mode"], str(st["batch_mode"])),
                    "threads": st["form_threads"],
+                   "autotuned": tune_s is not None,
+                   "autotune_s": tune_s,
+                   "level_chunk": st["level_chunk"],
                    "units_per_lane": st["units_per_lane"],
                    "l2": (f"{ncopies} rotating copies of the fields "
                           f"({ncopies * field_bytes / 1e9:.2f} GB), a copy is "
@@ -569,7 +661,7 @@ def run_ours(args, rank, world, local):
                 ("sync_grid_8x8_n129_L32", lambda: make_workload_named("sync"), True)):
             ww = fn()
             others[name] = measure_forward(ww, device, stream, min(args.steps, 300), 5,
-                                           adjoint=adj)
+                                           adjoint=adj, floor=True)
             del ww
         # reconstruction-and-quadrature rows (user CSR rows of 16 / 32
         # entries); recorded as an error entry rather than losing the line
@@ -577,10 +669,16 @@ def run_ours(args, rank, world, local):
         try:
             ww = make_workload_named("hope")
             others["hope_cubed_sphere_6x384_L32_p4_q2"] = measure_forward(
-                ww, device, stream, min(args.steps, 300), 5, adjoint=True)
+                ww, device, stream, min(args.steps, 300), 5, adjoint=True, floor=True)
             del ww
         except Exception as e:  # noqa: BLE001
             others["hope_cubed_sphere_6x384_L32_p4_q2"] = {"error": f"{type(e).__name__}: {e}"}
+        # boundary rows fused with the stencil that reads them (Sec. IV-C)
+        try:
+            others["fused_27pt_hpcg_16x128"] = measure_fused(device, stream,
+                                                             min(args.steps, 50), 3)
+        except Exception as e:  # noqa: BLE001
+            others["fused_27pt_hpcg_16x128"] = {"error": f"{type(e).__name__}: {e}"}
         result["other_workloads"] = others
         # dead-ghost elimination (Sec. IV-C): the same workloads, plans cut
         # to the ghost values a following stencil reads
@@ -610,6 +708,12 @@ def n_family_kernels(st):
     return int(st["launches_fwd"])
 
 
+FORM_DESC = {
+    1: "batched, persistent: one resident grid claiming the items of every kind",
+    2: "batched: one graph launch, one plain-grid kernel per family, concurrent",
+    3: "batched: one persistent kernel per family, concurrent",
+}
+
 LAYOUT_DESC = {
     "level_innermost": "levels innermost: each component stored [k][j][i][level]",
     "level_outermost": "levels outermost: each component stored [level][k][j][i]",
@@ -624,7 +728,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batching",
                     choices=["batching", "swe", "adjoint", "hpcg", "sync", "hope"])
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the plan's default options (no bc_plan_autotune)")
+    ap.add_argument("--oracle-all", action="store_true",
+                    help="time the oracle's product on every workload and exit")
+    ap.add_argument("--oracle-budget-s", type=float, default=10.0)
     ap.add_argument("--layout", default="level_innermost",
                     choices=["level_innermost", "level_outermost"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -636,6 +744,10 @@ def main():
                     help="minimum seconds of warm-up before the timed steps")
     args = ap.parse_args()
     rank, world, local = dist_env()
+    if args.oracle_all:
+        if rank == 0:
+            print(json.dumps({"oracle_all": oracle_all(args)}))
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

@@ -337,6 +337,9 @@ typedef struct bc_stats {
   int32_t launches_fwd;       /* kernel launches of one batched forward      */
   int32_t launches_adj;       /* kernel launches of one adjoint              */
   int64_t sync_values;        /* Sync rows over all levels (data values)    */
+  int32_t batch_mode;         /* the bc_batch_mode BC_FORM_BATCHED runs in  */
+  int32_t level_chunk;        /* bc_plan_opts.level_chunk in use (0: the
+                                 per-family default)                         */
 } bc_stats;
 
 /*

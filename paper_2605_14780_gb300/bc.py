@@ -77,7 +77,7 @@ class BcStats(ctypes.Structure):
                 ("element_size", c_i32), ("form_threads", c_i32),
                 ("form_ctas_per_sm", c_i32), ("units_per_lane", c_i32),
                 ("launches_fwd", c_i32), ("launches_adj", c_i32),
-                ("sync_values", c_i64)]
+                ("sync_values", c_i64), ("batch_mode", c_i32), ("level_chunk", c_i32)]
 
 
 #: every function the header declares, with (restype, argtypes)

@@ -722,30 +722,35 @@ __device__ void csr_flat_w(const Item& it, const Ptrs& P, const Ctx& c, int lane
   T* dbase = static_cast<T*>(P.d);
   const T* sb = static_cast<const T*>(P.s);
   const bool common = sb != nullptr;
+  const int RW = it.p;  // the row width: W, or a multiple of 8 for wide rows
   for (int f = it.u0 + lane; f < end; f += 32) {
     int q, l;
     flat_of(f, it, q, l);
     const int row = it.table + q;
     const int nnz = __ldg(c.csr_nnz + row);
-    int off[W], slot[W];
-    T a[W], x[W];
-    load_ell<T, W>(c, it.src_org + q * W, common, off, a, slot);
     T acc = ldg(static_cast<const T*>(c.csr_rhs) + row);
-    if (common) {
-      const T* xl = sb + l * it.src_ls;
+    // wide rows (reconstruction-and-quadrature, folded rows) go in blocks
+    // of W entries, each loaded as vectors, in entry order
+    for (int b0 = 0; b0 < nnz; b0 += W) {
+      int off[W], slot[W];
+      T a[W], x[W];
+      load_ell<T, W>(c, it.src_org + q * RW + b0, common, off, a, slot);
+      if (common) {
+        const T* xl = sb + l * it.src_ls;
 #pragma unroll
-      for (int j = 0; j < W; ++j) x[j] = ldg(xl + off[j]);
-    } else {
+        for (int j = 0; j < W; ++j) x[j] = ldg(xl + off[j]);
+      } else {
 #pragma unroll
-      for (int j = 0; j < W; ++j) {
-        x[j] = T(0);
-        if (j < nnz)
-          x[j] = ldg(static_cast<const T*>(c.slots[slot[j]]) +
-                     (off[j] + l * __ldg(c.slot_ls + slot[j])));
+        for (int j = 0; j < W; ++j) {
+          x[j] = T(0);
+          if (b0 + j < nnz)
+            x[j] = ldg(static_cast<const T*>(c.slots[slot[j]]) +
+                       (off[j] + l * __ldg(c.slot_ls + slot[j])));
+        }
       }
-    }
 #pragma unroll
-    for (int j = 0; j < W; ++j) acc = j < nnz ? fma(a[j], x[j], acc) : acc;
+      for (int j = 0; j < W; ++j) acc = b0 + j < nnz ? fma(a[j], x[j], acc) : acc;
+    }
     dbase[dst_cell(it, c, q) + l * it.dst_ls] = acc;
   }
 }
@@ -758,6 +763,7 @@ __device__ void csr_chunk_w(const Item& it, const Ptrs& P, const Ctx& c, int lan
   const int chn = it.mode;
   const T* sb = static_cast<const T*>(P.s);
   const bool common = sb != nullptr;
+  const int RW = it.p;  // the row width: W, or a multiple of 8 for wide rows
   for (int u = it.u0 + lane; u < end; u += 32) {
     int q, ch;
     unit_of(u, it, q, ch);
@@ -765,42 +771,44 @@ __device__ void csr_chunk_w(const Item& it, const Ptrs& P, const Ctx& c, int lan
     const int nl = min(chn, (int)it.lev.d - l0);
     const int row = it.table + q;
     const int nnz = __ldg(c.csr_nnz + row);
-    int off[W], slot[W];
-    T a[W];
-    load_ell<T, W>(c, it.src_org + q * W, common, off, a, slot);
     T* d = static_cast<T*>(P.d) + (dst_cell(it, c, q) + l0 * ls);
     const T rhs = ldg(static_cast<const T*>(c.csr_rhs) + row);
     T acc[CH];
 #pragma unroll
     for (int l = 0; l < CH; ++l) acc[l] = T(0);
-    if (common) {  // padding entries read offset 0 of the slot, dropped below
-      const int sls = it.src_ls;
+    for (int b0 = 0; b0 < nnz; b0 += W) {  // wide rows: blocks of W entries
+      int off[W], slot[W];
+      T a[W];
+      load_ell<T, W>(c, it.src_org + q * RW + b0, common, off, a, slot);
+      if (common) {  // padding entries read offset 0 of the slot, dropped below
+        const int sls = it.src_ls;
 #pragma unroll
-      for (int j = 0; j < W; ++j) {
-        const T* xs = sb + (off[j] + l0 * sls);
-        const T aj = j < nnz ? a[j] : T(0);
-#pragma unroll
-        for (int l = 0; l < CH; ++l)
-          if (l < nl) {
-            const T xv = ldg(xs + l * sls);
-            acc[l] = j < nnz ? fma(aj, xv, acc[l]) : acc[l];
-          }
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < W; ++j)
-        if (j < nnz) {
-          const int sls = __ldg(c.slot_ls + slot[j]);
-          const T* xs = static_cast<const T*>(c.slots[slot[j]]) + (off[j] + l0 * sls);
+        for (int j = 0; j < W; ++j) {
+          const T* xs = sb + (off[j] + l0 * sls);
+          const T aj = b0 + j < nnz ? a[j] : T(0);
 #pragma unroll
           for (int l = 0; l < CH; ++l)
-            if (l < nl) acc[l] = fma(a[j], ldg(xs + l * sls), acc[l]);
+            if (l < nl) {
+              const T xv = ldg(xs + l * sls);
+              acc[l] = b0 + j < nnz ? fma(aj, xv, acc[l]) : acc[l];
+            }
         }
-    }
+      } else {
 #pragma unroll
-    for (int l = 0; l < CH; ++l)
-      if (l < nl) d[l * ls] = acc[l] + rhs;
-  }
+        for (int j = 0; j < W; ++j)
+          if (b0 + j < nnz) {
+            const int sls = __ldg(c.slot_ls + slot[j]);
+            const T* xs = static_cast<const T*>(c.slots[slot[j]]) + (off[j] + l0 * sls);
+#pragma unroll
+            for (int l = 0; l < CH; ++l)
+              if (l < nl) acc[l] = fma(a[j], ldg(xs + l * sls), acc[l]);
+          }
+      }
+      }
+#pragma unroll
+      for (int l = 0; l < CH; ++l)
+        if (l < nl) d[l * ls] = acc[l] + rhs;
+    }
 }
 
 // Rows are processed E entries at a time: the E offsets and values load
@@ -1004,7 +1012,7 @@ __device__ __forceinline__ void run_item(const Item& it, const Ptrs& P, const Ct
         interp_scalar_chunk<T, 4>(it, P, c, lane);
     }
   } else if constexpr (FAM == FAM_CSR) {
-    if (it.p == 8) {
+    if (it.p % 8 == 0) {  // 8, or wide rows in blocks of 8
       if (flat)
         csr_flat_w<T, 8>(it, P, c, lane);
       else if (ch8)

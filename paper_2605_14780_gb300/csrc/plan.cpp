@@ -450,9 +450,10 @@ bc_status add_csr(bc_plan* P, const bc_submatrix& m, int idx, Sub& s) {
   // ELL width of this sub-matrix: its longest row
   int64_t w = 1;
   for (int64_t r = 0; r < nrows; ++r) w = std::max<int64_t>(w, m.row_ptr[r + 1] - m.row_ptr[r]);
-  // widths up to 8 are padded to 4 or 8 and rows start on 16-byte
-  // boundaries, so the kernels load a row's entries as vectors
-  if (w <= 8) w = w <= 4 ? 4 : 8;
+  // widths up to 8 are padded to 4 or 8, wider rows to a multiple of 8, and
+  // rows start on 16-byte boundaries, so the kernels load a row's entries
+  // as vectors (wide rows in blocks of 8)
+  w = w <= 4 ? 4 : (w + 7) / 8 * 8;
   if (w * nrows > (int64_t(1) << 30))
     return fail(BC_ERR_UNSUPPORTED, "sub-matrix %d: CSR rows too long", idx);
   while (P->csr_slot.size() % 4) {
@@ -1661,6 +1662,8 @@ void compute_stats(bc_plan* P) {
   st.form_threads = P->opts.threads;
   st.form_ctas_per_sm = P->opts.ctas_per_sm;
   st.units_per_lane = P->opts.units_per_lane;
+  st.batch_mode = P->opts.batch_mode;
+  st.level_chunk = P->opts.level_chunk;
   const int ys = P->sync_ctx.nrows > 0 ? 2 : 0;
   st.launches_fwd = ys;
   if (P->opts.batch_mode == BC_BATCH_PERSISTENT)
