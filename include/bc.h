@@ -603,6 +603,25 @@ int64_t bc_pack_size(const bc_pack* pack);
 bc_status bc_pack_run(bc_pack* pack, void* const* slot_ptrs, void* buffer, void* stream);
 void bc_pack_destroy(bc_pack* pack);
 
+/*
+ * The circular or symmetric face of Sec. III-B as a BC_MAP sub-matrix, so a
+ * C caller need not derive the affine map.  On axis `axis` of block `block`
+ * (grid->blocks[block], extent N = n[axis], ghost width h = h[axis]), side 0
+ * is the low face (ghost indices -h..-1), side 1 the high face (N..N+h-1);
+ * the box spans the data range along the other axes.  The paper's fmap:
+ * BC_FMAP_SYMMETRIC reads the mirror image (low: -1-i; high: 2N-1-i),
+ * BC_FMAP_CIRCULAR the periodic image (low: i+N; high: i-N), the other
+ * axes unchanged.  comps (ncomps entries, the caller's array) is stored in
+ * *out as given, so it must live until bc_plan_create has copied it.
+ * Errors: BC_ERR_INVALID_ARG (NULL, bad block / axis / side / kind, a
+ * component out of range), BC_ERR_HALO_TOO_WIDE (h > N: fmap is defined for
+ * depths 0 < x <= N), BC_ERR_OUT_OF_RANGE (h = 0: the face has no ghosts).
+ */
+typedef enum bc_fmap { BC_FMAP_CIRCULAR = 0, BC_FMAP_SYMMETRIC = 1 } bc_fmap;
+bc_status bc_fmap_submatrix(const bc_grid* grid, int32_t block, int32_t axis, int32_t side,
+                            int32_t fmap, const int32_t* comps, int32_t ncomps,
+                            bc_submatrix* out);
+
 /* Release the plan and its device tables (NULL is a no-op). */
 void bc_plan_destroy(bc_plan* plan);
 

@@ -109,6 +109,8 @@ SIGNATURES = {
     "bc_pack_size": (c_i64, [c_vp]),
     "bc_pack_run": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "bc_pack_destroy": (None, [c_vp]),
+    "bc_fmap_submatrix": (c_i32, [ctypes.POINTER(BcGrid), c_i32, c_i32, c_i32, c_i32, P_i32,
+                                  c_i32, ctypes.POINTER(BcSubmatrix)]),
     "bc_plan_destroy": (None, [c_vp]),
     "bc_status_string": (ctypes.c_char_p, [c_i32]),
     "bc_last_error": (ctypes.c_char_p, []),
@@ -417,6 +419,23 @@ def _grid(blocks, dtype):
         cb[k].stride[:] = list(b["stride"])
         cb[k].level_stride = b["level_stride"]
     return BcGrid(BC_F64 if dtype == "f64" else BC_F32, len(blocks), cb), cb
+
+
+BC_FMAP_CIRCULAR, BC_FMAP_SYMMETRIC = 0, 1
+
+
+def fmap_submatrix(blocks, block, axis, side, fmap, comps, dtype="f64"):
+    """The C ABI's circular / symmetric face (``bc_fmap_submatrix``) as a
+    sub-matrix dict for :class:`Plan`."""
+    lib = load_library()
+    grid, keep = _grid(blocks, dtype)
+    cc = np.ascontiguousarray(np.asarray(comps, np.int32))
+    m = BcSubmatrix()
+    _check(lib.bc_fmap_submatrix(ctypes.byref(grid), int(block), int(axis), int(side),
+                                 int(fmap), _ptr(cc, c_i32), len(cc), ctypes.byref(m)))
+    return {"kind": m.kind, "block": m.block, "lo": tuple(m.lo), "hi": tuple(m.hi),
+            "comps": [int(c) for c in cc], "src_block": m.src_block, "perm": tuple(m.perm),
+            "sign": tuple(m.sign), "offset": tuple(m.offset)}
 
 
 class Pack:

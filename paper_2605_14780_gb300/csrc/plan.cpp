@@ -2844,6 +2844,47 @@ bc_status bc_pack_run(bc_pack* pack, void* const* slot_ptrs, void* buffer, void*
 
 void bc_pack_destroy(bc_pack* pack) { delete pack; }
 
+bc_status bc_fmap_submatrix(const bc_grid* grid, int32_t block, int32_t axis, int32_t side,
+                            int32_t fmap, const int32_t* comps, int32_t ncomps,
+                            bc_submatrix* out) {
+  if (!grid || !grid->blocks || !out || !comps || ncomps <= 0)
+    return fail(BC_ERR_INVALID_ARG, "NULL argument or no component");
+  if (block < 0 || block >= grid->nblocks) return fail(BC_ERR_INVALID_ARG, "bad block %d", block);
+  if (axis < 0 || axis > 2 || side < 0 || side > 1)
+    return fail(BC_ERR_INVALID_ARG, "axis must be 0..2 and side 0 or 1");
+  if (fmap != BC_FMAP_CIRCULAR && fmap != BC_FMAP_SYMMETRIC)
+    return fail(BC_ERR_INVALID_ARG, "fmap must be BC_FMAP_CIRCULAR or BC_FMAP_SYMMETRIC");
+  const bc_block& B = grid->blocks[block];
+  for (int c = 0; c < ncomps; ++c)
+    if (comps[c] < 0 || comps[c] >= B.ncomp)
+      return fail(BC_ERR_INVALID_ARG, "component %d out of range", comps[c]);
+  const int N = B.n[axis], h = B.h[axis];
+  if (h <= 0) return fail(BC_ERR_OUT_OF_RANGE, "axis %d has no ghost cells", axis);
+  if (h > N) return fail(BC_ERR_HALO_TOO_WIDE, "ghost width %d exceeds the extent %d", h, N);
+  std::memset(out, 0, sizeof(*out));
+  out->kind = BC_MAP;
+  out->block = block;
+  out->src_block = block;
+  out->ncomps = ncomps;
+  out->comps = comps;
+  for (int d = 0; d < 3; ++d) {
+    out->lo[d] = 0;
+    out->hi[d] = B.n[d];
+    out->perm[d] = d;
+    out->sign[d] = 1;
+    out->offset[d] = 0;
+  }
+  out->lo[axis] = side ? N : -h;
+  out->hi[axis] = side ? N + h : 0;
+  if (fmap == BC_FMAP_SYMMETRIC) {
+    out->sign[axis] = -1;
+    out->offset[axis] = side ? 2 * N - 1 : -1;
+  } else {
+    out->offset[axis] = side ? -N : N;
+  }
+  return BC_OK;
+}
+
 bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs, void* const* dev_ptrs,
                         void* const* slot_ptrs, void* stream) {
   TraceRange trace("bc_apply_host");

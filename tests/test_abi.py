@@ -241,3 +241,27 @@ def test_tensor_layout_checks_on_the_host(lib):
         plan2.check_tensors(inner)
     with pytest.raises(ValueError, match="stride"):
         plan2.check_tensors(outer)
+
+
+@pytest.mark.parametrize("kind", ["circular", "symmetric"])
+@pytest.mark.parametrize("axis,side", [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0), (2, 1)])
+def test_fmap_submatrix_is_the_paper_map(lib, kind, axis, side):
+    """bc_fmap_submatrix gives the face sub-matrix the Python face
+    description builds (the paper's fmap, both sides; those rows are
+    pinned against the oracle by the host-plan tests)."""
+    w = synth.hpcg_block((5, 4, 6), "Z", seed=3)
+    blk = w["blocks"][0]
+    fm = bc.BC_FMAP_CIRCULAR if kind == "circular" else bc.BC_FMAP_SYMMETRIC
+    sub = bc.fmap_submatrix([specs.contiguous_block(blk)], 0, axis, side, fm, [0])
+    face = [s for s in specs.faces_submatrices(
+        {"block": 0, "corners": "zero",
+         "faces": [{"axis": a, "side": sd, "type": kind if (a, sd) == (axis, side) else "zero"}
+                   for a in range(3) for sd in (0, 1)]}, w["blocks"])
+        if s["kind"] == specs.BC_MAP]
+    assert len(face) == 1
+    for key in ("lo", "hi", "src_block", "perm", "sign", "offset"):
+        assert tuple(np.atleast_1d(sub[key])) == tuple(np.atleast_1d(face[0][key])), key
+    bad = dict(blk, h=(7, 1, 1))
+    with pytest.raises(bc.BCError) as e:
+        bc.fmap_submatrix([specs.contiguous_block(bad)], 0, 0, 0, fm, [0])
+    assert e.value.status == "BC_ERR_HALO_TOO_WIDE"
