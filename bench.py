@@ -712,6 +712,7 @@ FORM_DESC = {
     1: "batched, persistent: one resident grid claiming the items of every kind",
     2: "batched: one graph launch, one plain-grid kernel per family, concurrent",
     3: "batched: one persistent kernel per family, concurrent",
+    4: "batched: one plain-grid kernel over every item of every kind, longest first",
 }
 
 LAYOUT_DESC = {

@@ -286,7 +286,9 @@ typedef struct bc_plan_opts {
                               (interpolation, CSR and transpose rows): 0
                               default (4 for interpolation rows, 8 for CSR
                               and transpose rows), or 1, 2, 4, 8 for all;
-                              the persistent launch takes at most 4         */
+                              the launches of every kind in one kernel
+                              (BC_BATCH_PERSISTENT, BC_BATCH_SINGLE) take
+                              at most 4                                     */
   int32_t unstaged_interp; /* 1: interpolation rows read their nodes from
                               global memory lane by lane; 0 (default): with
                               levels far apart in memory, a warp first
@@ -309,11 +311,14 @@ typedef enum bc_batch_mode {
   BC_BATCH_FAMILIES = 2,   /* one plain-grid kernel per kernel family
                               (structured, interpolation, CSR), forked onto
                               plan-owned streams and joined                 */
-  BC_BATCH_FAMILIES_PERSISTENT = 3 /* one persistent kernel per family, forked
-                              and joined, each claiming its family's items
-                              from its own counter; the SMs are shared out
-                              between the families in proportion to their
-                              work, so the kernels run side by side        */
+  BC_BATCH_FAMILIES_PERSISTENT = 3, /* one persistent kernel per family,
+                              forked and joined, each claiming its family's
+                              items from its own counter; the SMs are shared
+                              out between the families in proportion to
+                              their work, so the kernels run side by side  */
+  BC_BATCH_SINGLE = 4      /* one plain-grid kernel over the work items of
+                              every kind, the longest first (one launch, no
+                              fork; the hardware hands the CTAs out)        */
 } bc_batch_mode;
 
 typedef struct bc_plan bc_plan;

@@ -17,7 +17,7 @@ LIB_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib")
 
 BC_F32, BC_F64 = 0, 1
 BC_FORM_BATCHED, BC_FORM_TYPEWIDE, BC_FORM_PER_BC = 0, 1, 2
-BC_BATCH_PERSISTENT, BC_BATCH_FAMILIES, BC_BATCH_FAMILIES_PERSISTENT = 1, 2, 3
+BC_BATCH_PERSISTENT, BC_BATCH_FAMILIES, BC_BATCH_FAMILIES_PERSISTENT, BC_BATCH_SINGLE = 1, 2, 3, 4
 STATUS = {0: "BC_OK", 1: "BC_ERR_INVALID_ARG", 2: "BC_ERR_OVERLAP",
           3: "BC_ERR_COLUMN_NOT_DATA", 4: "BC_ERR_UNCOVERED",
           5: "BC_ERR_HALO_TOO_WIDE", 6: "BC_ERR_OUT_OF_RANGE",

@@ -716,7 +716,7 @@ __device__ __forceinline__ void load_ell(const Ctx& c, int e0, bool common, int 
 // are loaded too and dropped by a select, so the W loads issue without
 // branches; measured on the 512-block workload (levels innermost) this took
 // the CSR kernel from 38 to 26 us.
-template <typename T, int W>
+template <typename T, int W, bool WIDE>
 __device__ void csr_flat_w(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
   const int end = it.u0 + it.nunits;
   T* dbase = static_cast<T*>(P.d);
@@ -730,8 +730,10 @@ __device__ void csr_flat_w(const Item& it, const Ptrs& P, const Ctx& c, int lane
     const int nnz = __ldg(c.csr_nnz + row);
     T acc = ldg(static_cast<const T*>(c.csr_rhs) + row);
     // wide rows (reconstruction-and-quadrature, folded rows) go in blocks
-    // of W entries, each loaded as vectors, in entry order
-    for (int b0 = 0; b0 < nnz; b0 += W) {
+    // of W entries, each loaded as vectors, in entry order; a row of width
+    // W is one block (the padded entries are dropped by the selects)
+    const int nb = WIDE ? nnz : 1;
+    for (int b0 = 0; b0 < nb; b0 += W) {
       int off[W], slot[W];
       T a[W], x[W];
       load_ell<T, W>(c, it.src_org + q * RW + b0, common, off, a, slot);
@@ -756,7 +758,7 @@ __device__ void csr_flat_w(const Item& it, const Ptrs& P, const Ctx& c, int lane
 }
 
 // A cell times a chunk of levels per lane, a whole ELL row of width W.
-template <typename T, int W, int CH>
+template <typename T, int W, int CH, bool WIDE>
 __device__ void csr_chunk_w(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
   const int end = it.u0 + it.nunits;
   const int ls = it.dst_ls;
@@ -776,7 +778,8 @@ __device__ void csr_chunk_w(const Item& it, const Ptrs& P, const Ctx& c, int lan
     T acc[CH];
 #pragma unroll
     for (int l = 0; l < CH; ++l) acc[l] = T(0);
-    for (int b0 = 0; b0 < nnz; b0 += W) {  // wide rows: blocks of W entries
+    const int nb = WIDE ? nnz : 1;  // a row of width W: one block
+    for (int b0 = 0; b0 < nb; b0 += W) {  // wide rows: blocks of W entries
       int off[W], slot[W];
       T a[W];
       load_ell<T, W>(c, it.src_org + q * RW + b0, common, off, a, slot);
@@ -1012,20 +1015,27 @@ __device__ __forceinline__ void run_item(const Item& it, const Ptrs& P, const Ct
         interp_scalar_chunk<T, 4>(it, P, c, lane);
     }
   } else if constexpr (FAM == FAM_CSR) {
-    if (it.p % 8 == 0) {  // 8, or wide rows in blocks of 8
+    if (it.p == 8) {
       if (flat)
-        csr_flat_w<T, 8>(it, P, c, lane);
+        csr_flat_w<T, 8, false>(it, P, c, lane);
       else if (ch8)
-        csr_chunk_w<T, 8, (MAXCH > 4 ? 8 : 4)>(it, P, c, lane);
+        csr_chunk_w<T, 8, (MAXCH > 4 ? 8 : 4), false>(it, P, c, lane);
       else
-        csr_chunk_w<T, 8, 4>(it, P, c, lane);
+        csr_chunk_w<T, 8, 4, false>(it, P, c, lane);
+    } else if (it.p % 8 == 0) {  // wide rows in blocks of 8
+      if (flat)
+        csr_flat_w<T, 8, true>(it, P, c, lane);
+      else if (ch8)
+        csr_chunk_w<T, 8, (MAXCH > 4 ? 8 : 4), true>(it, P, c, lane);
+      else
+        csr_chunk_w<T, 8, 4, true>(it, P, c, lane);
     } else if (it.p == 4) {
       if (flat)
-        csr_flat_w<T, 4>(it, P, c, lane);
+        csr_flat_w<T, 4, false>(it, P, c, lane);
       else if (ch8)
-        csr_chunk_w<T, 4, (MAXCH > 4 ? 8 : 4)>(it, P, c, lane);
+        csr_chunk_w<T, 4, (MAXCH > 4 ? 8 : 4), false>(it, P, c, lane);
       else
-        csr_chunk_w<T, 4, 4>(it, P, c, lane);
+        csr_chunk_w<T, 4, 4, false>(it, P, c, lane);
     } else if (flat) {
       csr_flat<T>(it, P, c, lane);
     } else if (ch8) {
@@ -1077,11 +1087,11 @@ template <int FAM, int THREADS> struct Occ {
 #define BC_STRUCT_WARPS 40
 #endif
 #ifndef BC_ALL_WARPS
-#define BC_ALL_WARPS 16
+#define BC_ALL_WARPS 32
 #endif
-  // the persistent kernel of every kind carries the union of the paths:
-  // 16 warps per SM (128 registers) keep its CSR and transpose rows in
-  // registers, and each warp moves 16-byte vectors with several in flight
+  // the kernel of every kind carries the union of the paths at 64
+  // registers (32 warps per SM): no spills in the plain grid; the
+  // persistent loop spills some but measured faster than at 16 or 24 warps
   static constexpr int kWarps =
       FAM == FAM_STRUCT ? BC_STRUCT_WARPS : (FAM == FAM_ALL ? BC_ALL_WARPS : 32);
   // resident CTAs asked of the register allocator: the warp budget in CTAs,
@@ -1357,6 +1367,7 @@ cudaError_t launch_any(int fam, const Ctx& c, const Item* items, int nitems,
     case FAM_STRUCT: return launch_fam<T, FAM_STRUCT>(c, items, nitems, threads, grid, s);
     case FAM_INTERP: return launch_fam<T, FAM_INTERP>(c, items, nitems, threads, grid, s);
     case FAM_CSR: return launch_fam<T, FAM_CSR>(c, items, nitems, threads, grid, s);
+    case FAM_ALL: return launch_fam<T, FAM_ALL>(c, items, nitems, threads, grid, s);
     default: return launch_fam<T, FAM_ADJ>(c, items, nitems, threads, grid, s);
   }
 }
@@ -1367,6 +1378,7 @@ int resident_any(int fam, int threads) {
     case FAM_STRUCT: return resident_fam<T, FAM_STRUCT>(threads);
     case FAM_INTERP: return resident_fam<T, FAM_INTERP>(threads);
     case FAM_CSR: return resident_fam<T, FAM_CSR>(threads);
+    case FAM_ALL: return resident_fam<T, FAM_ALL>(threads);
     default: return resident_fam<T, FAM_ADJ>(threads);
   }
 }

@@ -862,7 +862,9 @@ int table_mode(const bc_block& B, int order, int chunk) {
 int level_chunk(const bc_plan* P, bool interp) {
   int ch = P->opts.level_chunk;
   if (ch == 0) ch = interp ? 4 : 8;
-  return P->opts.batch_mode == BC_BATCH_PERSISTENT ? std::min(ch, 4) : ch;
+  const bool all_kinds =
+      P->opts.batch_mode == BC_BATCH_PERSISTENT || P->opts.batch_mode == BC_BATCH_SINGLE;
+  return all_kinds ? std::min(ch, 4) : ch;
 }
 
 // split the unit space into warp-sized items: vol * L single values (flat
@@ -1666,7 +1668,7 @@ void compute_stats(bc_plan* P) {
   st.level_chunk = P->opts.level_chunk;
   const int ys = P->sync_ctx.nrows > 0 ? 2 : 0;
   st.launches_fwd = ys;
-  if (P->opts.batch_mode == BC_BATCH_PERSISTENT)
+  if (P->opts.batch_mode == BC_BATCH_PERSISTENT || P->opts.batch_mode == BC_BATCH_SINGLE)
     st.launches_fwd += P->all_items.empty() ? 0 : 1;
   else
     for (const auto& v : P->fam_items) st.launches_fwd += v.empty() ? 0 : 1;
@@ -1689,7 +1691,7 @@ bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
   if (o.ghost_sweeps < 0 || o.ghost_sweeps > kMaxGhostSweeps)
     return fail(BC_ERR_INVALID_ARG, "ghost_sweeps must be in 0..%d", kMaxGhostSweeps);
   if (o.batch_mode == 0) o.batch_mode = BC_BATCH_FAMILIES;
-  if (o.batch_mode < BC_BATCH_PERSISTENT || o.batch_mode > BC_BATCH_FAMILIES_PERSISTENT)
+  if (o.batch_mode < BC_BATCH_PERSISTENT || o.batch_mode > BC_BATCH_SINGLE)
     return fail(BC_ERR_INVALID_ARG, "batch_mode must be 0 or a bc_batch_mode");
   if (o.scalar_runs < 0 || o.scalar_runs > 1)
     return fail(BC_ERR_INVALID_ARG, "scalar_runs must be 0 or 1");
@@ -2080,9 +2082,10 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
   cudaError_t e = cudaSuccess;
   const int T = P->opts.threads;
   unsigned* ctr = nullptr;
-  if (form == BC_FORM_BATCHED && P->opts.batch_mode != BC_BATCH_FAMILIES)
+  const bool single = form == BC_FORM_BATCHED && P->opts.batch_mode == BC_BATCH_SINGLE;
+  if (form == BC_FORM_BATCHED && P->opts.batch_mode != BC_BATCH_FAMILIES && !single)
     ctr = counter_for(P, s);
-  const bool all_in_one = ctr && P->opts.batch_mode == BC_BATCH_PERSISTENT;
+  const bool all_in_one = single || (ctr && P->opts.batch_mode == BC_BATCH_PERSISTENT);
   // Sync rows read the input data: evaluate them into the staging buffer
   // while the ghost kernels run (they write only ghosts), write them back
   // after every kernel that reads data has run
@@ -2100,8 +2103,10 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
           (e = cudaEventRecord(P->ev_join[kFamilies - 2], ys)) != cudaSuccess)
         return cuda_fail(e, "Sync rows");
     }
-    e = launch_persistent(P->dtype, FAM_ALL, c, P->d_all, (int)P->all_items.size(), T,
-                          P->opts.ctas_per_sm, P->num_sms, ctr, s);
+    e = single ? launch_family(P->dtype, FAM_ALL, c, P->d_all, (int)P->all_items.size(), T,
+                               stream_grid(P, FAM_ALL), s)
+               : launch_persistent(P->dtype, FAM_ALL, c, P->d_all, (int)P->all_items.size(), T,
+                                   P->opts.ctas_per_sm, P->num_sms, ctr, s);
     if (sync && e == cudaSuccess) e = cudaStreamWaitEvent(s, P->ev_join[kFamilies - 2], 0);
   } else if (form == BC_FORM_BATCHED) {
     // one launch per kernel family, the families side by side
@@ -3071,7 +3076,8 @@ bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) 
     std::vector<int32_t> values;
   };
   std::vector<Knob> knobs = {{&bc_plan_opts::batch_mode,
-                              {BC_BATCH_FAMILIES, BC_BATCH_FAMILIES_PERSISTENT, BC_BATCH_PERSISTENT}}};
+                              {BC_BATCH_FAMILIES, BC_BATCH_SINGLE, BC_BATCH_FAMILIES_PERSISTENT,
+                               BC_BATCH_PERSISTENT}}};
   if (runs) knobs.push_back({&bc_plan_opts::scalar_runs, {0, 1}});
   knobs.push_back({&bc_plan_opts::units_per_lane, {1, 2, 4, 8}});
   knobs.push_back({&bc_plan_opts::threads, {128, 256}});

@@ -14,6 +14,7 @@ from paper_2605_14780_gb300 import bc, synth
 pytestmark = pytest.mark.gpu
 
 P, F, FP = bc.BC_BATCH_PERSISTENT, bc.BC_BATCH_FAMILIES, bc.BC_BATCH_FAMILIES_PERSISTENT
+S1 = bc.BC_BATCH_SINGLE
 
 
 def _packed(arrays, shift, layout):
@@ -59,6 +60,7 @@ def _adjoint(w, plan, cot, shift, layout):
 OPTS = [{"batch_mode": P}, {"batch_mode": P, "scalar_runs": 1},
         {"batch_mode": F}, {"batch_mode": F, "scalar_runs": 1},
         {"batch_mode": FP}, {"batch_mode": FP, "threads": 256},
+        {"batch_mode": S1}, {"batch_mode": S1, "threads": 64},
         {"batch_mode": P, "threads": 256, "units_per_lane": 8},
         {"batch_mode": P, "units_per_lane": 1, "ctas_per_sm": 1}]
 
@@ -90,7 +92,7 @@ def test_vector_runs_on_every_alignment(layout, dtype, shift):
 
 
 @pytest.mark.parametrize("chunk", [1, 2, 4, 8])
-@pytest.mark.parametrize("mode", [P, F, FP])
+@pytest.mark.parametrize("mode", [P, F, FP, S1])
 def test_level_chunks(chunk, mode):
     """Every levels-per-lane split of the chunked unit order (levels
     outermost: interpolation with rotation, CSR corners, and the transpose
@@ -146,6 +148,7 @@ def test_stats_count_one_launch_for_the_persistent_form():
     assert bc.plan_for_workload(w, ts, {"batch_mode": P}).stats()["launches_fwd"] == 1
     assert bc.plan_for_workload(w, ts, {"batch_mode": F}).stats()["launches_fwd"] == 2
     assert bc.plan_for_workload(w, ts, {"batch_mode": FP}).stats()["launches_fwd"] == 2
+    assert bc.plan_for_workload(w, ts, {"batch_mode": S1}).stats()["launches_fwd"] == 1
 
 
 def test_autotune_result_cache(tmp_path, monkeypatch):
