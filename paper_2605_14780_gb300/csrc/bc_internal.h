@@ -150,8 +150,12 @@ cudaError_t launch_family(int dtype, int family, const Ctx& ctx,
 int resident_ctas(int dtype, int family, int threads);
 // Persistent work-list launch: ctas_per_sm resident CTAs per SM (0: as many
 // as fit) on `sms` SMs, whose warps claim the items through `counter`
-// (two words, zero before the launch and zero again after it).  family:
-// FAM_ALL (every forward kind), FAM_ADJ or FAM_STRUCT.
+// (kCtrWords words: a done count, then kSpread claim counters kCtrStride
+// words apart; zero before the launch and zero again after it).  family:
+// FAM_ALL (every forward kind) or one family.
+constexpr unsigned kSpread = 8;      // claim counters per list
+constexpr unsigned kCtrStride = 64;  // words between counters (own 256-byte lines)
+constexpr unsigned kCtrWords = (kSpread + 1) * kCtrStride;
 cudaError_t launch_persistent(int dtype, int family, const Ctx& ctx, const Item* items,
                               int nitems, int threads, int ctas_per_sm, int sms,
                               unsigned* counter, cudaStream_t s);

@@ -1182,33 +1182,51 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
   }
 }
 
-// Persistent work-list form: a resident grid whose warps claim items from a
-// device counter (one atomic per item, issued by lane 0 while the warp still
-// works on an earlier item; nothing ever waits on another warp).  Three items
-// are in the pipeline of a warp: the one it works on, the next one (its slot
-// pointers already loaded) and the one after (its descriptor in flight), plus
-// the claim of a fourth.  A warp stops claiming at its first claim past the
-// end of the list; it then counts itself done, and the last warp of the
-// launch to do so puts both counters back to zero, so the next launch on the
-// stream (or the next replay of a captured graph) starts from item 0.  Items
-// are ordered longest first, so the last items claimed are the short ones.
+// Persistent work-list form: a resident grid whose warps claim items from
+// device counters (lane 0's atomic is issued while the warp still works on
+// an earlier item; nothing ever waits on another warp).  Claims on one
+// address serialise in its L2 slice, so the list is dealt over kSpread
+// counters, each in its own 256-byte line: counter k hands out items k,
+// k + kSpread, k + 2 kSpread, ... (longest first within each), a warp starts
+// on counter (warp index mod kSpread) and moves to the next counter when its
+// own runs dry, until it has found all kSpread dry in a row.  Three items
+// are in a warp's pipeline: the one it works on, the next one (its slot
+// pointers already loaded) and the one after (its descriptor in flight),
+// plus the claim of a fourth.  A warp that stops counts itself done; the
+// last warp of the launch puts every counter back to zero, so the next
+// launch on the stream (or the next replay of a captured graph) starts
+// from item 0.
 template <typename T, int THREADS, int FAM>
 __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     k_persist(Ctx c, const Item* __restrict__ items, int nitems, unsigned* __restrict__ ctr) {
   constexpr unsigned FULL = 0xffffffffu;
+  constexpr unsigned S = kSpread;
   __shared__ Item sit[THREADS / 32];
   __shared__ __align__(16) unsigned char stage[Stage<FAM, THREADS>::kBytes];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int* iw = reinterpret_cast<const int*>(items);
   const unsigned n = (unsigned)nitems;
+  unsigned k = (blockIdx.x * (THREADS / 32) + warp) % S;  // this warp's counter
+  unsigned dry = 0;                                        // dry counters in a row
   bool more = true;
+  auto counter = [&](unsigned j) { return ctr + (1 + j) * kCtrStride; };
+  auto issue = [&]() -> unsigned { return (more && lane == 0) ? atomicAdd(counter(k), 1u) : 0u; };
+  // the item a claim `raw` on counter k gave, or the next counter's
   auto finish = [&](unsigned raw) -> unsigned {
     if (!more) return n;
-    const unsigned v = __shfl_sync(FULL, raw, 0);
-    if (v >= n) more = false;
-    return v < n ? v : n;
+    unsigned v = __shfl_sync(FULL, raw, 0) * S + k;
+    while (v >= n) {
+      if (++dry == S) {
+        more = false;
+        return n;
+      }
+      k = (k + 1) % S;
+      const unsigned r = lane == 0 ? atomicAdd(counter(k), 1u) : 0u;
+      v = __shfl_sync(FULL, r, 0) * S + k;
+    }
+    dry = 0;
+    return v;
   };
-  auto issue = [&]() -> unsigned { return (more && lane == 0) ? atomicAdd(ctr, 1u) : 0u; };
   auto words = [&](unsigned i) -> int { return i < n ? __ldg(iw + (size_t)i * 32 + lane) : 0; };
   // prologue: the first three items
   unsigned a = finish(issue());
@@ -1242,9 +1260,9 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
   if (lane == 0) {
     __threadfence();
     const unsigned warps = gridDim.x * (THREADS / 32);
-    if (atomicAdd(ctr + 1, 1u) == warps - 1) {
+    if (atomicAdd(ctr, 1u) == warps - 1) {
+      for (unsigned j = 0; j < S; ++j) atomicExch(counter(j), 0u);
       atomicExch(ctr, 0u);
-      atomicExch(ctr + 1, 0u);
     }
   }
 }

@@ -1467,7 +1467,7 @@ bc_status upload_tables(bc_plan* P) {
   const size_t o_ycs = L.take(Y.cstage.size() * 4);
   const size_t o_ycw = L.take(Y.cw.size() * S);
   const size_t o_yst = L.take((size_t)Y.stage * S);
-  const size_t o_ctr = L.take(2 * kFamilies * kCounterStreams * sizeof(unsigned));  // zero
+  const size_t o_ctr = L.take(kCtrWords * kFamilies * kCounterStreams * sizeof(unsigned));  // zero
   std::vector<char> host(L.off + 256, 0);
   put_raw(host, o_yr, Y.row);
   put_raw(host, o_yp, Y.ptr);
@@ -2048,10 +2048,10 @@ unsigned* counter_for(bc_plan* P, cudaStream_t stream) {
   std::lock_guard<std::mutex> lock(P->ctr_mu);
   void* key = static_cast<void*>(stream);
   for (size_t i = 0; i < P->ctr_streams.size(); ++i)
-    if (P->ctr_streams[i] == key) return P->d_ctr + 2 * kFamilies * i;
+    if (P->ctr_streams[i] == key) return P->d_ctr + kCtrWords * kFamilies * i;
   if ((int)P->ctr_streams.size() >= kCounterStreams) return nullptr;
   P->ctr_streams.push_back(key);
-  return P->d_ctr + 2 * kFamilies * (P->ctr_streams.size() - 1);
+  return P->d_ctr + kCtrWords * kFamilies * (P->ctr_streams.size() - 1);
 }
 
 // Resident CTAs per SM of each family's persistent kernel when the families
@@ -2131,7 +2131,7 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
       if (t > 0 && (e = cudaStreamWaitEvent(st, P->ev_fork, 0)) != cudaSuccess) break;
       const int f = fams[t];
       e = ctr ? launch_persistent(P->dtype, f, c, P->d_fam[f], (int)P->fam_items[f].size(), T,
-                                  split[f], P->num_sms, ctr + 2 * f, st)
+                                  split[f], P->num_sms, ctr + kCtrWords * f, st)
               : launch_family(P->dtype, f, c, P->d_fam[f], (int)P->fam_items[f].size(), T,
                               stream_grid(P, f), st);
       if (e == cudaSuccess && t > 0) e = cudaEventRecord(P->ev_join[t - 1], st);
