@@ -3080,7 +3080,7 @@ bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) 
                                BC_BATCH_PERSISTENT}}};
   if (runs) knobs.push_back({&bc_plan_opts::scalar_runs, {0, 1}});
   knobs.push_back({&bc_plan_opts::units_per_lane, {1, 2, 4, 8}});
-  knobs.push_back({&bc_plan_opts::threads, {128, 256}});
+  knobs.push_back({&bc_plan_opts::threads, {64, 128, 256}});
   if (chunked) knobs.push_back({&bc_plan_opts::level_chunk, {1, 2, 4, 8}});
   knobs.push_back({&bc_plan_opts::ctas_per_sm, {0, 1, 2}});
   float best_ms = 0;
