@@ -239,9 +239,10 @@ def layout_views(buf, w, layout):
 
 
 def measure_forward(w, device, stream, steps, warmup, layout="level_outermost",
-                    adjoint=False, floor=False, stencil=None):
+                    adjoint=False, floor=False, stencil=None, autotune=True):
     """Device time of the batched forward (and optionally the adjoint) of a
-    workload with rotating field copies; returns a dict of numbers."""
+    workload with rotating field copies, after bc_plan_autotune; returns a
+    dict of numbers."""
     from paper_2605_14780_gb300 import bc
     esize = 4 if w["dtype"] == "f32" else 8
     field_bytes = sum(a.size for a in w["fields"]) * esize
@@ -249,6 +250,8 @@ def measure_forward(w, device, stream, steps, warmup, layout="level_outermost",
     copies = field_copies(w, ncopies, device, layout)
     plan = bc.plan_for_workload(w, copies[0][1], stencil=stencil)
     tables = [bc.slot_table(v) for _, v in copies]
+    if autotune:
+        plan.autotune(tables[0])
     st = plan.stats()
     hbm, _ = measured_peaks()
     gs = [capture(lambda t=t: plan.apply(t, stream=stream), stream) for t in tables]
@@ -259,7 +262,10 @@ def measure_forward(w, device, stream, steps, warmup, layout="level_outermost",
            "algorithmic_bytes": int(st["bytes_fwd"]),
            "useful_gbs": st["bytes_fwd"] / (ms / 1e3) / 1e9,
            "frac_of_measured_hbm": st["bytes_fwd"] / (ms / 1e3) / 1e9 / hbm,
-           "layout": layout, "field_copies": ncopies}
+           "layout": layout, "field_copies": ncopies,
+           "form": FORM_DESC.get(st["batch_mode"], str(st["batch_mode"])),
+           "threads": st["form_threads"], "units_per_lane": st["units_per_lane"],
+           "level_chunk": st["level_chunk"]}
     if floor:
         out["dram_floor"] = dram_floor(plan, w, copies[0][1], copies[0][0])
         for g in (32, 64):
@@ -650,7 +656,8 @@ def run_ours(args, rank, world, local):
     if not args.only_batched and not args.no_variants:
         other = "level_outermost" if args.layout == "level_innermost" else "level_innermost"
         result["layout_variants"] = {other: measure_forward(
-            w, device, stream, min(args.steps, 500), 5, other, floor=True)}
+            w, device, stream, min(args.steps, 500), 5, other, floor=True,
+            autotune=not args.no_autotune)}
         # the other workloads of the scope table, batched forward (+ adjoint)
         others = {}
         for name, fn, adj in (
@@ -661,7 +668,8 @@ def run_ours(args, rank, world, local):
                 ("sync_grid_8x8_n129_L32", lambda: make_workload_named("sync"), True)):
             ww = fn()
             others[name] = measure_forward(ww, device, stream, min(args.steps, 300), 5,
-                                           adjoint=adj, floor=True)
+                                           adjoint=adj, floor=True,
+                                           autotune=not args.no_autotune)
             del ww
         # reconstruction-and-quadrature rows (user CSR rows of 16 / 32
         # entries); recorded as an error entry rather than losing the line
@@ -669,7 +677,8 @@ def run_ours(args, rank, world, local):
         try:
             ww = make_workload_named("hope")
             others["hope_cubed_sphere_6x384_L32_p4_q2"] = measure_forward(
-                ww, device, stream, min(args.steps, 300), 5, adjoint=True, floor=True)
+                ww, device, stream, min(args.steps, 300), 5, adjoint=True, floor=True,
+                autotune=not args.no_autotune)
             del ww
         except Exception as e:  # noqa: BLE001
             others["hope_cubed_sphere_6x384_L32_p4_q2"] = {"error": f"{type(e).__name__}: {e}"}
