@@ -13,6 +13,7 @@ stencil workload, and the SM clocks seen during the timed loop.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
     python bench.py --oracle-all     # the oracle on every workload, then exit
+    python bench.py --profile-case batching:level_innermost:struct   # for ncu
 
 Multi-GPU runs are independent replicas (the operator has no exchange step
 on one GPU's resident blocks): value = all ranks' ghost values / max time.
@@ -717,6 +718,42 @@ def n_family_kernels(st):
     return int(st["launches_fwd"])
 
 
+def profile_case(spec):
+    """A few applies of one case, for a profiler capture of one launch:
+    ``<workload>:<layout>:<what>`` with what = struct | interp | csr (that
+    family's plan alone), all (the batched apply), adjoint, or fused (the
+    27-point fused workload on 4 blocks)."""
+    import torch
+    from paper_2605_14780_gb300 import bc, synth
+    wname, layout, what = spec.split(":")
+    dev = torch.device("cuda", 0)
+    if what == "fused":
+        w = synth.hpcg_block(128, "P", seed=2, nblocks=4)
+        offs = bc.box_stencil(3, 1)
+        cf = np.array([26.0 if tuple(o) == (0, 0, 0) else -1.0 for o in offs])
+        copies = field_copies(w, 2, dev)
+        outs = field_copies(w, 2, dev)
+        plan = bc.plan_for_workload(w, copies[0][1], {"stencil_fusion": 1})
+        for k in range(4):
+            plan.apply_stencil(bc.slot_table(copies[k % 2][1]), bc.slot_table(outs[k % 2][1]),
+                               offs, cf)
+    else:
+        w = make_workload_named(wname)
+        copies = field_copies(w, 2, dev, layout)
+        tables = [bc.slot_table(v) for _, v in copies]
+        if what in ("all", "adjoint"):
+            plan = bc.plan_for_workload(w, copies[0][1])
+        else:
+            name = {"struct": "structured (zero/const/map)", "csr": "csr",
+                    "interp": "interpolation"}[what]
+            plan = family_plans(w, copies[0][1])[name]
+        for k in range(4):
+            (plan.adjoint if what == "adjoint" else plan.apply)(tables[k % 2])
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": spec, "bytes_fwd": plan.stats()["bytes_fwd"],
+                      "bytes_adj": plan.stats()["bytes_adj"]}))
+
+
 FORM_DESC = {
     1: "batched, persistent: one resident grid claiming the items of every kind",
     2: "batched: one graph launch, one plain-grid kernel per family, concurrent",
@@ -743,6 +780,9 @@ def main():
     ap.add_argument("--oracle-all", action="store_true",
                     help="time the oracle's product on every workload and exit")
     ap.add_argument("--oracle-budget-s", type=float, default=10.0)
+    ap.add_argument("--profile-case", default=None,
+                    help="<workload>:<layout>:<struct|interp|csr|all|adjoint|fused>: a few "
+                         "applies of one case for a profiler capture, then exit")
     ap.add_argument("--layout", default="level_innermost",
                     choices=["level_innermost", "level_outermost"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -754,6 +794,9 @@ def main():
                     help="minimum seconds of warm-up before the timed steps")
     args = ap.parse_args()
     rank, world, local = dist_env()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     if args.oracle_all:
         if rank == 0:
             print(json.dumps({"oracle_all": oracle_all(args)}))
