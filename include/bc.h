@@ -442,7 +442,9 @@ bc_status bc_apply_host(bc_plan* plan, void* const* host_ptrs,
  * the order of the points.  Needs bc_plan_opts.stencil_fusion = 1 at
  * creation (else BC_ERR_UNSUPPORTED, as for plans with Sync rows);
  * BC_ERR_INVALID_ARG for npoints outside 1..125 or a non-finite weight;
- * BC_ERR_HALO_TOO_WIDE when an offset reaches past a block's ghost width.
+ * BC_ERR_HALO_TOO_WIDE when an offset reaches past a block's ghost width,
+ * BC_ERR_UNSUPPORTED past 2 cells (the kernel stages tiles with a halo of
+ * at most 2).
  */
 bc_status bc_apply_stencil(bc_plan* plan, void* const* slot_ptrs, void* const* out_ptrs,
                            const int32_t* offsets, const double* coeffs, int32_t npoints,

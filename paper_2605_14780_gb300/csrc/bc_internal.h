@@ -175,18 +175,24 @@ cudaError_t launch_cs_geometry(const CsPanels& pan, const int4* cells,
                                unsigned* err, cudaStream_t s);
 
 // Ghost fill fused with a stencil (fused.cu).  One descriptor per slot;
-// the launch's CTAs are cut per slot (cta0: the slot's first CTA), each
-// covering kFuseThreads values: the slot's data values (stencil outputs)
-// first, then its ghost-frame values (ghost fills).
+// the launch's CTAs are cut per slot (cta0: the slot's first CTA): first
+// one CTA per tile of kTileX x kTileY x tz data cells and level (the
+// stencil outputs, read from a shared-memory copy of the tile and its
+// halo), then CTAs of kFuseThreads ghost-frame values (ghost fills).
 constexpr int kFuseThreads = 256;
 constexpr int kFuseMaxPoints = 125;  // a 5 x 5 x 5 box
+constexpr int kTileX = 32, kTileY = 8, kTileZ = 4;
+constexpr int kTileVals = (kTileX + 4) * (kTileY + 4) * (kTileZ + 4);  // halo up to 2
 struct FuseSlot {
   int32_t n[3], h[3];
   int32_t L, lfast;   // levels; 1: levels fastest in the value order
   int64_t s[3], ls;   // element strides of the axes and of the levels (0: one level)
   int64_t fbase;      // the slot's first frame-table entry
   int64_t cta0;       // the slot's first CTA
+  int64_t tiles;      // tile CTAs of the slot (all levels); ghost CTAs follow
   int32_t nd, nf;     // data cells and ghost-frame cells of one level
+  int32_t nt[3];      // tiles along each axis (tz cells deep along axis 2)
+  int32_t tz;         // kTileZ, or 1 for 2-D blocks
   FastDiv dL, dnd, dnf, dn0, dn01;  // division by L, nd, nf, n[0], n[0] * n[1]
 };
 struct FuseCtx {
@@ -202,6 +208,7 @@ struct FuseCtx {
 };
 struct FuseStencil {
   int32_t n;
+  int32_t r[3];       // halo of the stencil along each axis (<= 2)
   int8_t o[kFuseMaxPoints][3];
   double c[kFuseMaxPoints];
 };

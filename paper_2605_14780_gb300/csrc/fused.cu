@@ -14,7 +14,11 @@
 //
 // Rows are the plan's level-0 rows of A in CSR form; each slot has a table
 // that maps every cell of its ghost frame (the full region minus the data
-// region, in slab order) to its row, or -1.
+// region, in slab order) to its row, or -1.  The stencil outputs go by
+// tiles of 32 x 8 x 4 cells (x 1 for 2-D blocks) and one level: the CTA
+// stages the tile and its halo in shared memory, evaluating each covered
+// ghost of the halo once, and each thread sums the points for 4 cells
+// along axis 2 from there.
 #include <cstdint>
 
 #include "bc_internal.h"
@@ -121,13 +125,31 @@ __device__ __forceinline__ T eval_row(const FuseCtx& F, void* const* slots, int 
   return acc;
 }
 
+// f at cell (i, j, k) of slot S, level offset lo: a data value, a covered
+// ghost evaluated from its row, or a stored (uncovered) ghost
+template <typename T>
+__device__ __forceinline__ T field_at(const FuseCtx& F, void* const* slots, const FuseSlot& S,
+                                      const T* x, int i, int j, int k, int l, int64_t lo) {
+  if (i >= 0 && i < S.n[0] && j >= 0 && j < S.n[1] && k >= 0 && k < S.n[2])
+    return __ldg(x + (cell_off(S, i, j, k) + lo));
+  const int r = __ldg(F.frame_row + S.fbase + frame_index(S, i, j, k));
+  if (r < 0) return __ldg(x + (cell_off(S, i, j, k) + lo));
+  bool copy;
+  typename FBits<T>::type bits;
+  return eval_row<T>(F, slots, r, l, copy, bits);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kFuseThreads)
     k_fused(FuseCtx F, FuseStencil st, void* const* slots, void* const* outs) {
   using B = typename FBits<T>::type;
   __shared__ FuseSlot S;
   __shared__ int si;
-  if (threadIdx.x == 0) {
+  __shared__ T sm[kTileVals];
+  __shared__ int dp[kFuseMaxPoints];
+  __shared__ T cf[kFuseMaxPoints];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
     // the slot of this CTA: the last slot whose first CTA is <= blockIdx.x
     int lo = 0, hi = F.nslots - 1;
     while (lo < hi) {
@@ -139,66 +161,71 @@ __global__ void __launch_bounds__(kFuseThreads)
     S = F.slot[lo];
   }
   __syncthreads();
-  const int64_t v = ((int64_t)blockIdx.x - S.cta0) * kFuseThreads + threadIdx.x;
-  const int64_t nd = (int64_t)S.nd * S.L, nf = (int64_t)S.nf * S.L;
-  if (v >= nd + nf) return;
-  B* xb = static_cast<B*>(slots[si]);
+  const int64_t lc = (int64_t)blockIdx.x - S.cta0;
   const T* x = static_cast<const T*>(slots[si]);
-  if (v < nd) {
-    // a stencil value at data cell c, level l
-    int c, l;
-    if (S.lfast) {
-      c = (int)fdivf((uint32_t)v, S.dL);
-      l = (int)v - c * S.L;
-    } else {
-      l = (int)fdivf((uint32_t)v, S.dnd);
-      c = (int)v - l * S.nd;
-    }
-    const int k = (int)fdivf((uint32_t)c, S.dn01);
-    const int rem = c - k * S.n[0] * S.n[1];
-    const int j = (int)fdivf((uint32_t)rem, S.dn0);
-    const int i = rem - j * S.n[0];
+  if (lc < S.tiles) {
+    // stencil outputs of one tile at one level: stage the tile and its
+    // halo (covered ghosts evaluated once each), then the sums
+    int t = (int)lc;
+    const int tx = t % S.nt[0];
+    t /= S.nt[0];
+    const int ty = t % S.nt[1];
+    t /= S.nt[1];
+    const int tzi = t % S.nt[2];
+    const int l = t / S.nt[2];
+    const int i0 = tx * kTileX, j0 = ty * kTileY, k0 = tzi * S.tz;
+    const int SX = kTileX + 2 * st.r[0], SY = kTileY + 2 * st.r[1], SZ = S.tz + 2 * st.r[2];
     const int64_t lo = (int64_t)l * S.ls;
-    T acc = T(0);
-    for (int p = 0; p < st.n; ++p) {
-      const int a = i + st.o[p][0], b = j + st.o[p][1], cc = k + st.o[p][2];
-      T val;
-      if (a >= 0 && a < S.n[0] && b >= 0 && b < S.n[1] && cc >= 0 && cc < S.n[2]) {
-        val = __ldg(x + (cell_off(S, a, b, cc) + lo));
-      } else {
-        const int r = __ldg(F.frame_row + S.fbase + frame_index(S, a, b, cc));
-        if (r < 0) {
-          val = __ldg(x + (cell_off(S, a, b, cc) + lo));
-        } else {
-          bool copy;
-          B bits;
-          val = eval_row<T>(F, slots, r, l, copy, bits);
-        }
+    for (int p = tid; p < st.n; p += kFuseThreads) {
+      dp[p] = (st.o[p][2] * SY + st.o[p][1]) * SX + st.o[p][0];
+      cf[p] = (T)st.c[p];
+    }
+    for (int e = tid; e < SX * SY * SZ; e += kFuseThreads) {
+      const int li = e % SX, q = e / SX;
+      const int lj = q % SY, lk = q / SY;
+      const int i = i0 + li - st.r[0], j = j0 + lj - st.r[1], k = k0 + lk - st.r[2];
+      const bool full = i >= -S.h[0] && i < S.n[0] + S.h[0] && j >= -S.h[1] &&
+                        j < S.n[1] + S.h[1] && k >= -S.h[2] && k < S.n[2] + S.h[2];
+      // cells past the full region only border outputs past the data region
+      sm[e] = full ? field_at<T>(F, slots, S, x, i, j, k, l, lo) : T(0);
+    }
+    __syncthreads();
+    const int ix = tid % kTileX, iy = tid / kTileX;
+    const int i = i0 + ix, j = j0 + iy;
+    if (i < S.n[0] && j < S.n[1]) {
+      T* out = static_cast<T*>(outs[si]);
+      for (int kz = 0; kz < S.tz; ++kz) {
+        const int k = k0 + kz;
+        if (k >= S.n[2]) break;
+        const T* c = sm + ((kz + st.r[2]) * SY + (iy + st.r[1])) * SX + (ix + st.r[0]);
+        T acc = T(0);
+        for (int p = 0; p < st.n; ++p) acc = fma(cf[p], c[dp[p]], acc);
+        out[cell_off(S, i, j, k) + lo] = acc;
       }
-      acc = fma((T)st.c[p], val, acc);
     }
-    static_cast<T*>(outs[si])[cell_off(S, i, j, k) + lo] = acc;
-  } else {
-    // the ghost value at frame entry f, level l
-    const int64_t w = v - nd;
-    int64_t f;
-    int l;
-    if (S.lfast) {
-      f = (int64_t)fdivf((uint32_t)w, S.dL);
-      l = (int)(w - f * S.L);
-    } else {
-      l = (int)fdivf((uint32_t)w, S.dnf);
-      f = w - (int64_t)l * S.nf;
-    }
-    const int r = __ldg(F.frame_row + S.fbase + f);
-    if (r < 0) return;
-    int i, j, k;
-    frame_cell(S, f, i, j, k);
-    bool copy;
-    B bits;
-    const T val = eval_row<T>(F, slots, r, l, copy, bits);
-    xb[cell_off(S, i, j, k) + (int64_t)l * S.ls] = copy ? bits : to_bits_f(val);
+    return;
   }
+  // the ghost value at frame entry f, level l
+  const int64_t w = (lc - S.tiles) * kFuseThreads + tid;
+  if (w >= (int64_t)S.nf * S.L) return;
+  B* xb = static_cast<B*>(slots[si]);
+  int64_t f;
+  int l;
+  if (S.lfast) {
+    f = (int64_t)fdivf((uint32_t)w, S.dL);
+    l = (int)(w - f * S.L);
+  } else {
+    l = (int)fdivf((uint32_t)w, S.dnf);
+    f = w - (int64_t)l * S.nf;
+  }
+  const int r = __ldg(F.frame_row + S.fbase + f);
+  if (r < 0) return;
+  int i, j, k;
+  frame_cell(S, f, i, j, k);
+  bool copy;
+  B bits;
+  const T val = eval_row<T>(F, slots, r, l, copy, bits);
+  xb[cell_off(S, i, j, k) + (int64_t)l * S.ls] = copy ? bits : to_bits_f(val);
 }
 
 }  // namespace

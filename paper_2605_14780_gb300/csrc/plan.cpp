@@ -1757,8 +1757,13 @@ bc_status build_fusion(bc_plan* P) {
     f.dn01 = make_div((uint32_t)B.n[0] * (uint32_t)B.n[1]);
     f.fbase = fbase;
     f.cta0 = cta;
+    f.tz = B.n[2] == 1 ? 1 : kTileZ;
+    f.nt[0] = (B.n[0] + kTileX - 1) / kTileX;
+    f.nt[1] = (B.n[1] + kTileY - 1) / kTileY;
+    f.nt[2] = (B.n[2] + f.tz - 1) / f.tz;
+    f.tiles = (int64_t)f.nt[0] * f.nt[1] * f.nt[2] * B.nlevels;
     fbase += F - D;
-    cta += ((F * B.nlevels) + kFuseThreads - 1) / kFuseThreads;
+    cta += f.tiles + ((F - D) * B.nlevels + kFuseThreads - 1) / kFuseThreads;
   }
   P->fuse_ctas = cta;
   // frame index of a ghost cell (the device's frame_index)
@@ -2743,7 +2748,11 @@ bc_status bc_apply_stencil(bc_plan* plan, void* const* slot_ptrs, void* const* o
         if (o > B.h[d] || o < -B.h[d])
           return fail(BC_ERR_HALO_TOO_WIDE, "stencil point %d reaches %d cells along axis %d, "
                       "past a ghost width of %d", p, o, d, B.h[d]);
+      if (o > 2 || o < -2)
+        return fail(BC_ERR_UNSUPPORTED, "stencil point %d reaches %d cells along axis %d "
+                    "(at most 2)", p, o, d);
       st.o[p][d] = (int8_t)o;
+      st.r[d] = std::max(st.r[d], std::abs(o));
     }
     st.c[p] = coeffs[p];
   }
