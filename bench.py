@@ -165,7 +165,8 @@ def profiled_traffic(workload):
         e = d[workload]
         if e.get("kernel_source") != kernel_source_hash():
             return None
-        return int(e["dram_bytes_per_launch"])
+        return {"dram_bytes_per_launch": int(e["dram_bytes_per_launch"]),
+                "l2_write_bytes": int(e.get("l2_write_bytes", 0)) or None}
     except Exception:
         return None
 
@@ -618,6 +619,7 @@ def run_ours(args, rank, world, local):
                           "d2h_bytes_per_step": int(field_bytes),
                           "path": "bc_apply_host: every slot copied in, applied, copied out"}}
 
+    traffic = profiled_traffic(f"{args.workload}:{args.layout}:{dom_name}")
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
@@ -641,7 +643,11 @@ def run_ours(args, rank, world, local):
                      "achieved": dom["achieved_gbs"], "peak": hbm,
                      "unit": "GB/s", "frac": dom["achieved_gbs"] / hbm,
                      "peak_source": peak_kind,
-                     "traffic": profiled_traffic(f"{args.workload}:{args.layout}:{dom_name}"),
+                     "traffic": (traffic or {}).get("dram_bytes_per_launch"),
+                     "traffic_note": ("DRAM read + write bytes of one launch (ncu); the "
+                                      "stores stay in L2 during a short replay, so "
+                                      "l2_write_bytes (L2 write sectors x 32) counts them"),
+                     "l2_write_bytes": (traffic or {}).get("l2_write_bytes"),
                      "algorithmic_bytes_per_launch": int(dom["algorithmic_bytes"]),
                      "kernel_ms": dom["ms"],
                      "step": {"algorithmic_bytes": int(st["bytes_fwd"]),
