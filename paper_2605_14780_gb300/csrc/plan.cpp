@@ -1190,9 +1190,17 @@ void build_items(bc_plan* P) {
     for (int r = it.u0; r < it.u0 + it.nunits; ++r) n += P->runs[r].z;
     return n;
   };
+#ifndef BC_ITEM_COST
+#define BC_ITEM_COST 0  // order of the family lists: 0 by values, 1 by bytes moved
+#endif
+  auto cost = [&](const Item& it) -> int64_t {
+    const int64_t v = work(it);
+    if (!BC_ITEM_COST) return v;
+    return it.kind == IK_MAP ? 2 * v : (it.kind == IK_CSR ? v * (1 + it.p) : v);
+  };
   for (auto& v : P->fam_items) {
     std::vector<std::pair<int64_t, size_t>> key(v.size());
-    for (size_t t = 0; t < v.size(); ++t) key[t] = {-work(v[t]), t};
+    for (size_t t = 0; t < v.size(); ++t) key[t] = {-cost(v[t]), t};
     std::stable_sort(key.begin(), key.end());
     std::vector<Item> sorted(v.size());
     for (size_t t = 0; t < v.size(); ++t) sorted[t] = v[key[t].second];
