@@ -289,11 +289,12 @@ typedef struct bc_plan_opts {
                               the launches of every kind in one kernel
                               (BC_BATCH_PERSISTENT, BC_BATCH_SINGLE) take
                               at most 4                                     */
-  int32_t unstaged_interp; /* 1: interpolation rows read their nodes from
-                              global memory lane by lane; 0 (default): with
-                              levels far apart in memory, a warp first
-                              copies the small box of neighbour cells a tile
-                              of 32 ghost cells reads into shared memory    */
+  int32_t unstaged_rows;   /* 1: interpolation and CSR rows read their
+                              columns from global memory lane by lane; 0
+                              (default): with levels far apart in memory, a
+                              warp first copies the small box of cells a
+                              tile of 32 rows reads (in at most two slots of
+                              one block) into shared memory                 */
   int32_t stencil_fusion;  /* 1: also build the tables bc_apply_stencil
                               needs (a row per ghost-frame cell, and the
                               rows of A in CSR form); 0 (default): none     */

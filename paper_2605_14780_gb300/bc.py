@@ -65,7 +65,7 @@ class BcPlanOpts(ctypes.Structure):
                 ("strict_cover", c_i32), ("no_adjoint", c_i32),
                 ("no_runs", c_i32), ("host_only", c_i32), ("ghost_sweeps", c_i32),
                 ("batch_mode", c_i32), ("scalar_runs", c_i32), ("level_chunk", c_i32),
-                ("unstaged_interp", c_i32), ("stencil_fusion", c_i32)]
+                ("unstaged_rows", c_i32), ("stencil_fusion", c_i32)]
 
 
 class BcStats(ctypes.Structure):

@@ -82,16 +82,16 @@ struct alignas(16) Item {
   int32_t table;           // CONST / INTERP / CSR: first table row of cell 0
   int32_t comp;            // INTERP source components: u | v << 16
   int32_t dst_ls, src_ls;  // level strides (elements)
-  int32_t src_org;         // CSR: ELL entry of row 0 of this component;
-                           // MODE_TILE: element offset (level 0) of the
-                           // staged box in the source slots
-  // MODE_TILE interpolation items: levels [l0, l0 + nl) of the cells
-  // [u0, u0 + nunits) (vol divides by nunits), reading a box of bw x bh
-  // cells of the block whose slots start at bsrc, which steps bs0 / bs1
-  // elements along its two axes; bwid divides by bw
+  int32_t src_org;         // CSR: ELL entry of row 0 of this component
+  // MODE_TILE items: levels [l0, l0 + nl) of the cells [u0, u0 + nunits)
+  // (vol divides by nunits), reading a box of bw x bh cells at element
+  // offset borg (level 0) of a block that steps bs0 / bs1 elements along
+  // its two axes (bwid divides by bw); interpolation: the block's slots
+  // start at bsrc; CSR: the entries read slot bsrc (selector 0) or bsrc2
+  // (selector 1, or -1)
   int32_t l0, nl, bw, bh, bs0, bs1, bsrc;
   FastDiv bwid;
-  int32_t pad[2];
+  int32_t bsrc2, borg;
 };
 static_assert(sizeof(Item) % 16 == 0, "Item must be a multiple of 16 bytes");
 
@@ -112,6 +112,7 @@ struct Ctx {
   const void* itp_w;
   const void* itp_m;
   const int32_t* itp_box;   // staged cells: node 0 in the item's box
+  const int32_t* csr_box;   // staged CSR entries: box index | selector << 16
   // CSR rows (global row numbering): entry count per row, ELL entries
   // (a row's entries start at item.src_org + q * item.p), per-row constant
   const int32_t* csr_nnz;

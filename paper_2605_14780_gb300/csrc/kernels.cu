@@ -522,7 +522,7 @@ __device__ void interp_tile(const Item& it, const Ptrs& P, const Ctx& c, int lan
   const int nc = pair ? 2 : 1;
   const int A = it.bw * it.bh;
   const int cu = it.comp & 0xffff, cv = it.comp >> 16;
-  const int64_t lev0 = (int64_t)it.l0 * it.src_ls + it.src_org;
+  const int64_t lev0 = (int64_t)it.l0 * it.src_ls + it.borg;
   const T* xu = static_cast<const T*>(c.slots[it.bsrc + cu]) + lev0;
   const T* xv = pair ? static_cast<const T*>(c.slots[it.bsrc + cv]) + lev0 : xu;
   // stage: [level][component][box row][box column]
@@ -575,6 +575,52 @@ __device__ void interp_tile(const Item& it, const Ptrs& P, const Ctx& c, int lan
       du[off] = to_bits(fma(ldg(mr), au, ldg(mr + 1) * av));
       dv[off] = to_bits(fma(ldg(mr + 2), au, ldg(mr + 3) * av));
     }
+  }
+  __syncwarp();  // every lane is done with the stage before the next item
+}
+
+// Staged CSR rows (MODE_TILE, levels far apart in memory): the entries of
+// a tile of up to 32 rows lie in one small box of one block, in at most two
+// of its slots (a vector pair's components); the warp copies the box for
+// the item's levels and slots to shared memory, then each lane sums its
+// (row, level) units from there in entry order (as the per-lane path:
+// from zero, then + b).  Each entry carries its box index and slot
+// selector (csr_box).
+template <typename T>
+__device__ void csr_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
+  T* sm = static_cast<T*>(P.stage);
+  const int nsel = it.bsrc2 >= 0 ? 2 : 1;
+  const int A = it.bw * it.bh;
+  const int64_t lev0 = (int64_t)it.l0 * it.src_ls + it.borg;
+  const T* x0 = static_cast<const T*>(c.slots[it.bsrc]) + lev0;
+  const T* x1 = nsel > 1 ? static_cast<const T*>(c.slots[it.bsrc2]) + lev0 : x0;
+  for (int g = 0; g < it.nl * nsel; ++g) {
+    const int l = nsel > 1 ? g >> 1 : g;
+    const T* src = ((nsel > 1 && (g & 1)) ? x1 : x0) + (int64_t)l * it.src_ls;
+    T* dst = sm + g * A;
+    for (int e = lane; e < A; e += 32) {
+      const int bj = (int)fdiv((uint32_t)e, it.bwid), bi = e - bj * it.bw;
+      cp_async_elem<T>(dst + e, src + (bi * it.bs0 + bj * it.bs1));
+    }
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  const int nq = it.nunits, tot = nq * it.nl;
+  const T* val = static_cast<const T*>(c.csr_val);
+  T* d = static_cast<T*>(P.d);
+  for (int u = lane; u < tot; u += 32) {
+    const int l = (int)fdiv((uint32_t)u, it.vol), q = u - l * nq;
+    const int row = it.table + it.u0 + q;
+    const int nnz = __ldg(c.csr_nnz + row);
+    const int e0 = it.src_org + (it.u0 + q) * it.p;
+    const T* s = sm + l * nsel * A;
+    T acc = T(0);
+    for (int e = 0; e < nnz; ++e) {
+      const int bx = __ldg(c.csr_box + e0 + e);
+      acc = fma(ldg(val + e0 + e), s[(bx >> 16) * A + (bx & 0xffff)], acc);
+    }
+    d[(int64_t)dst_cell(it, c, it.u0 + q) + (int64_t)(it.l0 + l) * it.dst_ls] =
+        acc + ldg(static_cast<const T*>(c.csr_rhs) + row);
   }
   __syncwarp();  // every lane is done with the stage before the next item
 }
@@ -1015,7 +1061,9 @@ __device__ __forceinline__ void run_item(const Item& it, const Ptrs& P, const Ct
         interp_scalar_chunk<T, 4>(it, P, c, lane);
     }
   } else if constexpr (FAM == FAM_CSR) {
-    if (it.p == 8) {
+    if (it.mode == MODE_TILE) {
+      csr_tile<T>(it, P, c, lane);
+    } else if (it.p == 8) {
       if (flat)
         csr_flat_w<T, 8, false>(it, P, c, lane);
       else if (ch8)
@@ -1121,11 +1169,12 @@ __device__ __forceinline__ Ptrs gather_ptrs(void* mine) {
   return P;
 }
 
-// Shared memory for staged interpolation boxes: one kStageBytes area per
-// warp in the kernels that run interpolation items.
+// Shared memory for staged boxes: one kStageBytes area per warp in the
+// kernels that run interpolation or CSR items.
 template <int FAM, int THREADS>
 struct Stage {
-  static constexpr int kWarps = (FAM == FAM_INTERP || FAM == FAM_ALL) ? THREADS / 32 : 0;
+  static constexpr int kWarps =
+      (FAM == FAM_INTERP || FAM == FAM_CSR || FAM == FAM_ALL) ? THREADS / 32 : 0;
   static constexpr int kBytes = kWarps > 0 ? kWarps * kStageBytes : 16;
 };
 

@@ -149,6 +149,7 @@ struct bc_plan {
   std::vector<int4> itp_idx;
   std::vector<double> itp_w, itp_m;
   std::vector<int32_t> itp_box;  // staged interpolation: node 0 in its tile's box
+  std::vector<int32_t> csr_box;  // staged CSR entries: box index | selector << 16
   // user CSR rows stored as ELL blocks (one width per sub-matrix)
   std::vector<int32_t> csr_nnz;
   std::vector<int32_t> csr_slot, csr_off;
@@ -1043,7 +1044,8 @@ bool emit_tiles(bc_plan* P, const Sub& s, const Item& proto, int chunk, int nc,
       it.bs1 = (int32_t)S.stride[1];
       it.bsrc = base;
       it.bwid = make_div((uint32_t)bw);
-      it.src_org = (int32_t)org;
+      it.borg = (int32_t)org;
+      it.bsrc2 = -1;
       it.src_ls = (int32_t)(S.nlevels > 1 ? S.level_stride : 0);
       tiles.push_back(it);
     }
@@ -1053,9 +1055,95 @@ bool emit_tiles(bc_plan* P, const Sub& s, const Item& proto, int chunk, int nc,
   return true;
 }
 
+// Staged CSR rows of component ci of sub-matrix s (levels in chunks of
+// `chunk`): tiles of up to kTileCells rows whose entries all lie in one 2-D
+// block, in at most two of its slots, inside a box small enough that
+// `chunk` levels of both slots fit a warp's staging area at least one level
+// at a time.  Writes the entries' csr_box words.  Returns false (the
+// component keeps the per-lane path) when some tile does not qualify.
+bool emit_csr_tiles(bc_plan* P, const Sub& s, int ci, const Item& proto, int chunk,
+                    std::vector<Item>& out) {
+  const bc_block& B = P->blocks[s.block];
+  const int L = B.nlevels;
+  const int cap = kStageBytes / P->esize;
+  const int w = s.ell_w;
+  std::vector<Item> tiles;
+  std::vector<std::pair<size_t, int32_t>> boxes;
+  for (int q0 = 0; q0 < s.vol; q0 += kTileCells) {
+    const int nq = std::min(kTileCells, s.vol - q0);
+    int sl[2] = {-1, -1}, nsel = 0, blk = -1;
+    int imin = INT_MAX, imax = INT_MIN, jmin = INT_MAX, jmax = INT_MIN;
+    struct Ent {
+      size_t e;
+      int sel, i, j;
+    };
+    std::vector<Ent> ents;
+    for (int q = 0; q < nq; ++q) {
+      const size_t row = (size_t)(s.table + ci * s.vol + q0 + q);
+      const size_t e0 = (size_t)s.ell_base + ((size_t)ci * s.vol + q0 + q) * w;
+      for (int k = 0; k < P->csr_nnz[row]; ++k) {
+        const size_t e = e0 + k;
+        const int slot = P->csr_slot[e];
+        const int b = P->slot_block[slot];
+        if (blk < 0) blk = b;
+        if (b != blk) return false;
+        int sel = slot == sl[0] ? 0 : (slot == sl[1] ? 1 : -1);
+        if (sel < 0) {
+          if (nsel == 2) return false;
+          sl[nsel] = slot;
+          sel = nsel++;
+        }
+        const bc_block& S = P->blocks[b];
+        if (S.n[2] != 1 || S.h[2] != 0) return false;
+        int i, j, kk;
+        if (!decode_cell(S, P->csr_off[e], i, j, kk)) return false;
+        imin = std::min(imin, i);
+        imax = std::max(imax, i);
+        jmin = std::min(jmin, j);
+        jmax = std::max(jmax, j);
+        ents.push_back({e, sel, i, j});
+      }
+    }
+    if (blk < 0) return false;
+    const bc_block& S = P->blocks[blk];
+    if (S.nlevels != L) return false;
+    const int bw = imax - imin + 1, bh = jmax - jmin + 1;
+    if ((int64_t)bw * bh > kBoxIndex || (int64_t)bw * bh * nsel > cap) return false;
+    const int nl = std::min(chunk, cap / (bw * bh * nsel));
+    const int64_t org = cell_offset(S, imin, jmin, 0);
+    if (org > INT32_MAX) return false;
+    for (const Ent& x : ents)
+      boxes.push_back({x.e, ((x.i - imin) + (x.j - jmin) * bw) | (x.sel << 16)});
+    for (int l0 = 0; l0 < L; l0 += nl) {
+      Item it = proto;
+      it.mode = MODE_TILE;
+      it.u0 = q0;
+      it.nunits = nq;
+      it.vol = make_div((uint32_t)nq);
+      it.l0 = l0;
+      it.nl = std::min(nl, L - l0);
+      it.bw = bw;
+      it.bh = bh;
+      it.bs0 = (int32_t)S.stride[0];
+      it.bs1 = (int32_t)S.stride[1];
+      it.bsrc = sl[0];
+      it.bsrc2 = sl[1];
+      it.bwid = make_div((uint32_t)bw);
+      it.borg = (int32_t)org;
+      it.src_ls = (int32_t)(S.nlevels > 1 ? S.level_stride : 0);
+      it.src_slot = -1;  // no common-slot lookup: the tile reads its slots itself
+      tiles.push_back(it);
+    }
+  }
+  for (const auto& b : boxes) P->csr_box[b.first] = b.second;
+  out.insert(out.end(), tiles.begin(), tiles.end());
+  return true;
+}
+
 void build_items(bc_plan* P) {
   P->runs.clear();
   P->itp_box.assign(P->itp_idx.size(), 0);
+  P->csr_box.assign(P->csr_off.size(), 0);
   // units per warp item: single-level values (flat) or 8-level chunks
   const int upl = std::max(1, std::min(P->opts.units_per_lane, 64));
   // A small plan still gets enough items to keep every SM busy: the value
@@ -1139,7 +1227,7 @@ void build_items(bc_plan* P) {
           // levels far apart in memory: stage the nodes of each tile in
           // shared memory when the tiles' boxes are small
           const int mode = table_mode(B, P->opts.unit_order, level_chunk(P, true));
-          if (mode < 2 || P->opts.unstaged_interp ||
+          if (mode < 2 || P->opts.unstaged_rows ||
               !emit_tiles(P, s, it, mode, it.kind == IK_INTERP_PAIR ? 2 : 1, out))
             table_emit(out, it, B, s.vol);
           break;
@@ -1154,7 +1242,11 @@ void build_items(bc_plan* P) {
             const bc_block& S = P->blocks[P->slot_block[it.src_slot]];
             it.src_ls = (int32_t)(S.nlevels > 1 ? S.level_stride : 0);
           }
-          table_emit(out, it, B, s.vol);
+          // levels far apart in memory: stage each tile's column box
+          const int mode = table_mode(B, P->opts.unit_order, level_chunk(P, false));
+          if (mode < 2 || P->opts.unstaged_rows ||
+              !emit_csr_tiles(P, s, (int)ci, it, mode, out))
+            table_emit(out, it, B, s.vol);
           break;
         }
       }
@@ -1581,10 +1673,12 @@ bc_status upload_work(bc_plan* P) {
   const size_t o_z = L.take(P->adj_zero.size() * sizeof(Item));
   const size_t o_all = L.take(P->all_items.size() * sizeof(Item));
   const size_t o_box = L.take(P->itp_box.size() * 4);
+  const size_t o_cbox = L.take(P->csr_box.size() * 4);
   std::vector<char> host(L.off + 256, 0);
   put_raw(host, o_i, P->items);
   put_raw(host, o_all, P->all_items);
   put_raw(host, o_box, P->itp_box);
+  put_raw(host, o_cbox, P->csr_box);
   for (int f = 0; f < kFamilies; ++f) put_raw(host, o_f[f], P->fam_items[f]);
   put_raw(host, o_r, P->runs);
   put_raw(host, o_a, P->adj_items);
@@ -1605,6 +1699,7 @@ bc_status upload_work(bc_plan* P) {
   P->d_adj_zero = reinterpret_cast<Item*>(b + o_z);
   P->d_all = reinterpret_cast<Item*>(b + o_all);
   P->ctx.itp_box = reinterpret_cast<const int32_t*>(b + o_box);
+  P->ctx.csr_box = reinterpret_cast<const int32_t*>(b + o_cbox);
   return BC_OK;
 }
 
@@ -1708,8 +1803,8 @@ bc_status normalise_opts(const bc_plan_opts* in, bc_plan_opts& o) {
     return fail(BC_ERR_INVALID_ARG, "scalar_runs must be 0 or 1");
   if (o.stencil_fusion < 0 || o.stencil_fusion > 1)
     return fail(BC_ERR_INVALID_ARG, "stencil_fusion must be 0 or 1");
-  if (o.unstaged_interp < 0 || o.unstaged_interp > 1)
-    return fail(BC_ERR_INVALID_ARG, "unstaged_interp must be 0 or 1");
+  if (o.unstaged_rows < 0 || o.unstaged_rows > 1)
+    return fail(BC_ERR_INVALID_ARG, "unstaged_rows must be 0 or 1");
   if (o.level_chunk != 0 && o.level_chunk != 1 && o.level_chunk != 2 && o.level_chunk != 4 &&
       o.level_chunk != 8)
     return fail(BC_ERR_INVALID_ARG, "level_chunk must be 0, 1, 2, 4 or 8");
@@ -2453,9 +2548,19 @@ int64_t check_forward_list(WorkCheck& W, const std::vector<Item>& items, bool va
         std::vector<std::pair<int64_t, double>> a, b;
         for (int k = 0; k < nnz; ++k) {
           const size_t e = (size_t)it.src_org + (size_t)q * (size_t)it.p + (size_t)k;
-          const int slot = it.src_slot >= 0 ? it.src_slot : P->csr_slot[e];
+          int slot = it.src_slot >= 0 ? it.src_slot : P->csr_slot[e];
+          int64_t off = P->csr_off[e];
+          if (it.mode == MODE_TILE) {
+            // a staged row reads its column from the tile's box
+            const int32_t bx = P->csr_box[e];
+            const int idx = bx & 0xffff;
+            slot = (bx >> 16) ? it.bsrc2 : it.bsrc;
+            off = it.borg + (int64_t)(idx % it.bw) * it.bs0 + (int64_t)(idx / it.bw) * it.bs1;
+            if (idx >= it.bw * it.bh || slot < 0)
+              W.problem("a staged CSR entry lies outside its box", it.dst_slot, E);
+          }
           const int64_t ls = it.src_slot >= 0 ? it.src_ls : W.ls_of_slot(slot);
-          a.push_back({col_key(slot, (int64_t)P->csr_off[e] + l * ls), P->csr_val[e]});
+          a.push_back({col_key(slot, off + l * ls), P->csr_val[e]});
         }
         for (int64_t e = R.ptr[w->r]; e < R.ptr[w->r + 1]; ++e)
           b.push_back({col_key(R.cslot[e], R.coff[e] + w->l * W.ls_of_slot(R.cslot[e])), R.val[e]});
@@ -2474,7 +2579,7 @@ int64_t check_forward_list(WorkCheck& W, const std::vector<Item>& items, bool va
           const int32_t bx = P->itp_box[cell];
           const int idx = bx & kBoxIndex;
           ix.x = it.bsrc;
-          ix.y = it.src_org + (idx % it.bw) * it.bs0 + (idx / it.bw) * it.bs1;
+          ix.y = it.borg + (idx % it.bw) * it.bs0 + (idx / it.bw) * it.bs1;
           ix.z = (bx & kBoxRows) ? it.bs1 : it.bs0;
           ix.w = (bx & kBoxSnap) ? kFlagSnap : 0;
           if (idx >= it.bw * it.bh)
