@@ -289,12 +289,14 @@ typedef struct bc_plan_opts {
                               the launches of every kind in one kernel
                               (BC_BATCH_PERSISTENT, BC_BATCH_SINGLE) take
                               at most 4                                     */
-  int32_t unstaged_rows;   /* 1: interpolation and CSR rows read their
-                              columns from global memory lane by lane; 0
-                              (default): with levels far apart in memory, a
-                              warp first copies the small box of cells a
-                              tile of 32 rows reads (in at most two slots of
-                              one block) into shared memory                 */
+  int32_t unstaged_rows;   /* 1: interpolation, CSR and transpose rows
+                              read their columns from global memory lane by
+                              lane; 0 (default): with levels far apart in
+                              memory, a warp first copies the small box of
+                              cells a tile of 32 rows (16 or 8 when a group
+                              of 4 levels of the box would not fit) reads,
+                              in at most two slots of one block, into
+                              shared memory                                 */
   int32_t stencil_fusion;  /* 1: also build the tables bc_apply_stencil
                               needs (a row per ghost-frame cell, and the
                               rows of A in CSR form); 0 (default): none     */
@@ -456,7 +458,8 @@ bc_status bc_apply_stencil(bc_plan* plan, void* const* slot_ptrs, void* const* o
  * (slot_ptrs, device array) and keep the fastest: the batch mode, the
  * scalar or vector runs, the work per item (units_per_lane), the threads
  * per CTA, the levels-per-lane split (level_chunk, when the plan has
- * chunked units) and the resident CTAs per SM of the persistent launch,
+ * chunked units), the staged or unstaged rows (unstaged_rows, when the
+ * plan stages some) and the resident CTAs per SM of the persistent launch,
  * searched one option at a time from the plan's own options (median of
  * six launches, each after an L2 flush).  Overwrites the covered ghosts
  * (with the operator's own result).  Allocates a temporary L2-flush buffer;

@@ -66,7 +66,8 @@ constexpr int32_t kBoxIndex = 0xffff;
 constexpr int32_t kBoxRows = 1 << 16;
 constexpr int32_t kBoxSnap = 1 << 17;
 constexpr int kStageBytes = 2048;  // shared memory of one warp's staged box
-constexpr int kTileCells = 32;     // cells of one staged interpolation item
+constexpr int kTileCells = 32;     // cells (rows) of one staged item, at most
+constexpr int kTileLevels = 4;     // levels one lane of a staged CSR or transpose tile sums
 
 struct alignas(16) Item {
   int32_t kind;
@@ -113,6 +114,7 @@ struct Ctx {
   const void* itp_m;
   const int32_t* itp_box;   // staged cells: node 0 in the item's box
   const int32_t* csr_box;   // staged CSR entries: box index | selector << 16
+  const int32_t* adj_box;   // staged transpose entries: box index | selector << 16
   // CSR rows (global row numbering): entry count per row, ELL entries
   // (a row's entries start at item.src_org + q * item.p), per-row constant
   const int32_t* csr_nnz;

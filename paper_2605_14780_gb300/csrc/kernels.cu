@@ -582,18 +582,19 @@ __device__ void interp_tile(const Item& it, const Ptrs& P, const Ctx& c, int lan
 // Staged CSR rows (MODE_TILE, levels far apart in memory): the entries of
 // a tile of up to 32 rows lie in one small box of one block, in at most two
 // of its slots (a vector pair's components); the warp copies the box for
-// the item's levels and slots to shared memory, then each lane sums its
-// (row, level) units from there in entry order (as the per-lane path:
-// from zero, then + b).  Each entry carries its box index and slot
+// the item's levels and slots to shared memory, then each lane sums one row
+// for a group of up to kTileLevels levels from there, loading each entry's
+// weight and box word once for the group, in entry order (as the per-lane
+// path: from zero, then + b).  Each entry carries its box index and slot
 // selector (csr_box).
 template <typename T>
-__device__ void csr_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
-  T* sm = static_cast<T*>(P.stage);
+__device__ __forceinline__ void stage_box(const Item& it, const Ctx& c, T* sm, int lane) {
   const int nsel = it.bsrc2 >= 0 ? 2 : 1;
   const int A = it.bw * it.bh;
   const int64_t lev0 = (int64_t)it.l0 * it.src_ls + it.borg;
   const T* x0 = static_cast<const T*>(c.slots[it.bsrc]) + lev0;
   const T* x1 = nsel > 1 ? static_cast<const T*>(c.slots[it.bsrc2]) + lev0 : x0;
+  // stage: [level][slot][box row][box column]
   for (int g = 0; g < it.nl * nsel; ++g) {
     const int l = nsel > 1 ? g >> 1 : g;
     const T* src = ((nsel > 1 && (g & 1)) ? x1 : x0) + (int64_t)l * it.src_ls;
@@ -605,22 +606,82 @@ __device__ void csr_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) 
   }
   cp_async_wait_all();
   __syncwarp();
-  const int nq = it.nunits, tot = nq * it.nl;
+}
+
+template <typename T>
+__device__ void csr_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
+  T* sm = static_cast<T*>(P.stage);
+  stage_box<T>(it, c, sm, lane);
+  const int lstep = (it.bsrc2 >= 0 ? 2 : 1) * it.bw * it.bh;  // stage values per level
+  const int A = it.bw * it.bh;
+  const int nq = it.nunits, tot = nq * ((it.nl + kTileLevels - 1) / kTileLevels);
   const T* val = static_cast<const T*>(c.csr_val);
   T* d = static_cast<T*>(P.d);
   for (int u = lane; u < tot; u += 32) {
-    const int l = (int)fdiv((uint32_t)u, it.vol), q = u - l * nq;
+    const int g = (int)fdiv((uint32_t)u, it.vol), q = u - g * nq;
+    const int lb = g * kTileLevels;
     const int row = it.table + it.u0 + q;
     const int nnz = __ldg(c.csr_nnz + row);
     const int e0 = it.src_org + (it.u0 + q) * it.p;
-    const T* s = sm + l * nsel * A;
-    T acc = T(0);
+    const T* s = sm + lb * lstep;
+    T acc[kTileLevels];
+#pragma unroll
+    for (int l = 0; l < kTileLevels; ++l) acc[l] = T(0);
     for (int e = 0; e < nnz; ++e) {
       const int bx = __ldg(c.csr_box + e0 + e);
-      acc = fma(ldg(val + e0 + e), s[(bx >> 16) * A + (bx & 0xffff)], acc);
+      const T w = ldg(val + e0 + e);
+      const T* se = s + (bx >> 16) * A + (bx & 0xffff);
+#pragma unroll
+      for (int l = 0; l < kTileLevels; ++l)
+        if (lb + l < it.nl) acc[l] = fma(w, se[l * lstep], acc[l]);
     }
-    d[(int64_t)dst_cell(it, c, it.u0 + q) + (int64_t)(it.l0 + l) * it.dst_ls] =
-        acc + ldg(static_cast<const T*>(c.csr_rhs) + row);
+    const T b = ldg(static_cast<const T*>(c.csr_rhs) + row);
+    T* dd = d + (int64_t)dst_cell(it, c, it.u0 + q) + (int64_t)(it.l0 + lb) * it.dst_ls;
+#pragma unroll
+    for (int l = 0; l < kTileLevels; ++l)
+      if (lb + l < it.nl) dd[(int64_t)l * it.dst_ls] = acc[l] + b;
+  }
+  __syncwarp();  // every lane is done with the stage before the next item
+}
+
+// Staged transpose rows (MODE_TILE adjoint gather items, levels far apart in
+// memory): the ghost values that a tile of up to 32 data values' transpose
+// rows read lie in one small box of one block, in at most two slots; the
+// warp copies the box of ghost cotangents for the item's levels to shared
+// memory, then each lane updates one data value for a group of up to
+// kTileLevels levels with the entries in ghost order from there (as
+// adj_chunk: from the value's own cotangent).
+template <typename T>
+__device__ void adj_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
+  T* sm = static_cast<T*>(P.stage);
+  stage_box<T>(it, c, sm, lane);
+  const int lstep = (it.bsrc2 >= 0 ? 2 : 1) * it.bw * it.bh;
+  const int A = it.bw * it.bh;
+  const int nq = it.nunits, tot = nq * ((it.nl + kTileLevels - 1) / kTileLevels);
+  const T* wv = static_cast<const T*>(c.aent_w);
+  for (int u = lane; u < tot; u += 32) {
+    const int g = (int)fdiv((uint32_t)u, it.vol), q = u - g * nq;
+    const int lb = g * kTileLevels;
+    const int r = it.table + it.u0 + q;
+    T* xb = static_cast<T*>(P.d) +
+            ((int64_t)__ldg(c.arow_off + r) + (int64_t)(it.l0 + lb) * it.dst_ls);
+    const int e0 = (int)__ldg(c.adj_ptr + r), e1 = (int)__ldg(c.adj_ptr + r + 1);
+    const T* s = sm + lb * lstep;
+    T acc[kTileLevels];
+#pragma unroll
+    for (int l = 0; l < kTileLevels; ++l)
+      acc[l] = lb + l < it.nl ? xb[(int64_t)l * it.dst_ls] : T(0);
+    for (int e = e0; e < e1; ++e) {
+      const int bx = __ldg(c.adj_box + e);
+      const T w = ldg(wv + e);
+      const T* se = s + (bx >> 16) * A + (bx & 0xffff);
+#pragma unroll
+      for (int l = 0; l < kTileLevels; ++l)
+        if (lb + l < it.nl) acc[l] = fma(w, se[l * lstep], acc[l]);
+    }
+#pragma unroll
+    for (int l = 0; l < kTileLevels; ++l)
+      if (lb + l < it.nl) xb[(int64_t)l * it.dst_ls] = acc[l];
   }
   __syncwarp();  // every lane is done with the stage before the next item
 }
@@ -1092,7 +1153,9 @@ __device__ __forceinline__ void run_item(const Item& it, const Ptrs& P, const Ct
       csr_chunk<T, 4>(it, P, c, lane);
     }
   } else {
-    if (it.kind == IK_ADD && c.vec_runs)
+    if (it.mode == MODE_TILE)
+      adj_tile<T>(it, P, c, lane);
+    else if (it.kind == IK_ADD && c.vec_runs)
       runs_vec<T, RUN_ADD>(it, P, c, lane);
     else if (it.kind == IK_ADD)
       add_runs<T>(it, P, c, lane);
@@ -1170,11 +1233,10 @@ __device__ __forceinline__ Ptrs gather_ptrs(void* mine) {
 }
 
 // Shared memory for staged boxes: one kStageBytes area per warp in the
-// kernels that run interpolation or CSR items.
+// kernels that run interpolation, CSR or transpose-gather items.
 template <int FAM, int THREADS>
 struct Stage {
-  static constexpr int kWarps =
-      (FAM == FAM_INTERP || FAM == FAM_CSR || FAM == FAM_ALL) ? THREADS / 32 : 0;
+  static constexpr int kWarps = FAM != FAM_STRUCT ? THREADS / 32 : 0;
   static constexpr int kBytes = kWarps > 0 ? kWarps * kStageBytes : 16;
 };
 

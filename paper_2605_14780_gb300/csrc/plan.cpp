@@ -150,6 +150,7 @@ struct bc_plan {
   std::vector<double> itp_w, itp_m;
   std::vector<int32_t> itp_box;  // staged interpolation: node 0 in its tile's box
   std::vector<int32_t> csr_box;  // staged CSR entries: box index | selector << 16
+  std::vector<int32_t> adj_box;  // staged transpose entries: box index | selector << 16
   // user CSR rows stored as ELL blocks (one width per sub-matrix)
   std::vector<int32_t> csr_nnz;
   std::vector<int32_t> csr_slot, csr_off;
@@ -1055,93 +1056,179 @@ bool emit_tiles(bc_plan* P, const Sub& s, const Item& proto, int chunk, int nc,
   return true;
 }
 
+// A staged tile's box, the slots it reads and each entry's place in it.
+struct TileBox {
+  int blk = -1, nsel = 0, sl[2] = {-1, -1};
+  int imin = INT_MAX, imax = INT_MIN, jmin = INT_MAX, jmax = INT_MIN;
+  struct Ent {
+    size_t e;
+    int sel, i, j;
+  };
+  std::vector<Ent> ents;
+  // entry e reads (slot, offset); false when it leaves one 2-D block or
+  // its two slots
+  bool add(const bc_plan* P, size_t e, int slot, int64_t off) {
+    const int b = P->slot_block[slot];
+    if (blk < 0) blk = b;
+    if (b != blk) return false;
+    int sel = slot == sl[0] ? 0 : (slot == sl[1] ? 1 : -1);
+    if (sel < 0) {
+      if (nsel == 2) return false;
+      sl[nsel] = slot;
+      sel = nsel++;
+    }
+    const bc_block& S = P->blocks[b];
+    if (S.n[2] != 1 || S.h[2] != 0) return false;
+    int i, j, k;
+    if (!decode_cell(S, off, i, j, k)) return false;
+    imin = std::min(imin, i);
+    imax = std::max(imax, i);
+    jmin = std::min(jmin, j);
+    jmax = std::max(jmax, j);
+    ents.push_back({e, sel, i, j});
+    return true;
+  }
+};
+
+// Items of one staged tile of nq rows from q0 (levels in chunks of `chunk`,
+// L levels): 1 when the box holds at least `need` levels of its slots in a
+// warp's staging area (items and box words appended), 0 when the box is
+// too large for that, -1 when the rows cannot be staged.
+int finish_tile(const bc_plan* P, const TileBox& T, int q0, int nq, const Item& proto, int chunk,
+                int L, int need, std::vector<Item>& tiles,
+                std::vector<std::pair<size_t, int32_t>>& boxes) {
+  if (T.blk < 0) return -1;
+  const bc_block& S = P->blocks[T.blk];
+  if (S.nlevels != L) return -1;
+  const int cap = kStageBytes / P->esize;
+  const int bw = T.imax - T.imin + 1, bh = T.jmax - T.jmin + 1;
+  if ((int64_t)bw * bh > kBoxIndex) return 0;
+  const int64_t fit = cap / ((int64_t)bw * bh * T.nsel);
+  if (fit < need) return 0;
+  const int nl = (int)std::min<int64_t>(chunk, fit);
+  const int64_t org = cell_offset(S, T.imin, T.jmin, 0);
+  if (org > INT32_MAX) return -1;
+  for (const TileBox::Ent& x : T.ents)
+    boxes.push_back({x.e, ((x.i - T.imin) + (x.j - T.jmin) * bw) | (x.sel << 16)});
+  for (int l0 = 0; l0 < L; l0 += nl) {
+    Item it = proto;
+    it.mode = MODE_TILE;
+    it.u0 = q0;
+    it.nunits = nq;
+    // lanes take (row, group of kTileLevels levels) units, rows fastest
+    it.vol = make_div((uint32_t)nq);
+    it.l0 = l0;
+    it.nl = std::min(nl, L - l0);
+    it.bw = bw;
+    it.bh = bh;
+    it.bs0 = (int32_t)S.stride[0];
+    it.bs1 = (int32_t)S.stride[1];
+    it.bsrc = T.sl[0];
+    it.bsrc2 = T.sl[1];
+    it.bwid = make_div((uint32_t)bw);
+    it.borg = (int32_t)org;
+    it.src_ls = (int32_t)(S.nlevels > 1 ? S.level_stride : 0);
+    it.src_slot = -1;  // no common-slot lookup: the tile reads its slots itself
+    tiles.push_back(it);
+  }
+  return 1;
+}
+
+// Levels a staged CSR or transpose tile must hold at once: a full lane
+// group (fewer only when the chunk or the block has fewer).
+int tile_need(int chunk, int L) { return std::min(kTileLevels, std::min(chunk, L)); }
+
 // Staged CSR rows of component ci of sub-matrix s (levels in chunks of
-// `chunk`): tiles of up to kTileCells rows whose entries all lie in one 2-D
-// block, in at most two of its slots, inside a box small enough that
-// `chunk` levels of both slots fit a warp's staging area at least one level
-// at a time.  Writes the entries' csr_box words.  Returns false (the
-// component keeps the per-lane path) when some tile does not qualify.
+// `chunk`): tiles of kTileCells rows (16 or 8 when the boxes of 32 rows are
+// too large) whose entries all lie in one 2-D block, in at most two of its
+// slots, inside a box of which a lane group of levels fits a warp's staging
+// area.  Writes the entries' csr_box words.  Returns false (the component
+// keeps the per-lane path) when some tile does not qualify.
 bool emit_csr_tiles(bc_plan* P, const Sub& s, int ci, const Item& proto, int chunk,
                     std::vector<Item>& out) {
-  const bc_block& B = P->blocks[s.block];
-  const int L = B.nlevels;
-  const int cap = kStageBytes / P->esize;
+  const int L = P->blocks[s.block].nlevels;
   const int w = s.ell_w;
+  const int need = tile_need(chunk, L);
   std::vector<Item> tiles;
   std::vector<std::pair<size_t, int32_t>> boxes;
-  for (int q0 = 0; q0 < s.vol; q0 += kTileCells) {
-    const int nq = std::min(kTileCells, s.vol - q0);
-    int sl[2] = {-1, -1}, nsel = 0, blk = -1;
-    int imin = INT_MAX, imax = INT_MIN, jmin = INT_MAX, jmax = INT_MIN;
-    struct Ent {
-      size_t e;
-      int sel, i, j;
-    };
-    std::vector<Ent> ents;
-    for (int q = 0; q < nq; ++q) {
-      const size_t row = (size_t)(s.table + ci * s.vol + q0 + q);
-      const size_t e0 = (size_t)s.ell_base + ((size_t)ci * s.vol + q0 + q) * w;
-      for (int k = 0; k < P->csr_nnz[row]; ++k) {
-        const size_t e = e0 + k;
-        const int slot = P->csr_slot[e];
-        const int b = P->slot_block[slot];
-        if (blk < 0) blk = b;
-        if (b != blk) return false;
-        int sel = slot == sl[0] ? 0 : (slot == sl[1] ? 1 : -1);
-        if (sel < 0) {
-          if (nsel == 2) return false;
-          sl[nsel] = slot;
-          sel = nsel++;
-        }
-        const bc_block& S = P->blocks[b];
-        if (S.n[2] != 1 || S.h[2] != 0) return false;
-        int i, j, kk;
-        if (!decode_cell(S, P->csr_off[e], i, j, kk)) return false;
-        imin = std::min(imin, i);
-        imax = std::max(imax, i);
-        jmin = std::min(jmin, j);
-        jmax = std::max(jmax, j);
-        ents.push_back({e, sel, i, j});
+  for (int rows = kTileCells; rows >= 8; rows /= 2) {
+    tiles.clear();
+    boxes.clear();
+    bool smaller = false;
+    for (int q0 = 0; q0 < s.vol && !smaller; q0 += rows) {
+      const int nq = std::min(rows, s.vol - q0);
+      TileBox T;
+      for (int q = 0; q < nq; ++q) {
+        const size_t row = (size_t)(s.table + ci * s.vol + q0 + q);
+        const size_t e0 = (size_t)s.ell_base + ((size_t)ci * s.vol + q0 + q) * w;
+        for (int k = 0; k < P->csr_nnz[row]; ++k)
+          if (!T.add(P, e0 + k, P->csr_slot[e0 + k], P->csr_off[e0 + k])) return false;
+      }
+      const int r = finish_tile(P, T, q0, nq, proto, chunk, L, need, tiles, boxes);
+      if (r < 0) return false;
+      smaller = r == 0;
+    }
+    if (smaller) continue;
+    for (const auto& b : boxes) P->csr_box[b.first] = b.second;
+    out.insert(out.end(), tiles.begin(), tiles.end());
+    return true;
+  }
+  return false;
+}
+
+// Staged transpose rows [r0, r0 + nrows) (one data slot, levels in chunks
+// of `chunk`, the chunked unit order): tiles of kTileCells rows (16 or 8
+// when some box of 32 rows is too large); a tile that does not qualify
+// keeps the per-lane gather (one item of its rows per level chunk).
+// Returns false, emitting nothing, when no tile qualifies.
+bool emit_adj_tiles(bc_plan* P, int r0, int nrows, const Item& proto, int chunk, int L,
+                    std::vector<Item>& out) {
+  const int need = tile_need(chunk, L);
+  std::vector<Item> items;
+  std::vector<std::pair<size_t, int32_t>> boxes;
+  int staged = 0;
+  for (int rows = kTileCells; rows >= 8; rows /= 2) {
+    items.clear();
+    boxes.clear();
+    staged = 0;
+    bool smaller = false;
+    for (int q0 = 0; q0 < nrows && !smaller; q0 += rows) {
+      const int nq = std::min(rows, nrows - q0);
+      TileBox T;
+      bool ok = true;
+      for (int q = 0; q < nq && ok; ++q) {
+        const size_t r = (size_t)(r0 + q0 + q);
+        for (int64_t e = P->adj_ptr[r]; e < P->adj_ptr[r + 1] && ok; ++e)
+          ok = T.add(P, (size_t)e, P->aent_slot[(size_t)e], P->aent_off[(size_t)e]);
+      }
+      const int res = ok ? finish_tile(P, T, q0, nq, proto, chunk, L, need, items, boxes) : -1;
+      if (res > 0) {
+        ++staged;
+        continue;
+      }
+      if (res == 0 && rows > 8) {
+        smaller = true;
+        continue;
+      }
+      for (int c = 0; c * chunk < L; ++c) {
+        Item it = proto;
+        it.mode = chunk;
+        it.u0 = q0 + c * nrows;
+        it.nunits = nq;
+        items.push_back(it);
       }
     }
-    if (blk < 0) return false;
-    const bc_block& S = P->blocks[blk];
-    if (S.nlevels != L) return false;
-    const int bw = imax - imin + 1, bh = jmax - jmin + 1;
-    if ((int64_t)bw * bh > kBoxIndex || (int64_t)bw * bh * nsel > cap) return false;
-    const int nl = std::min(chunk, cap / (bw * bh * nsel));
-    const int64_t org = cell_offset(S, imin, jmin, 0);
-    if (org > INT32_MAX) return false;
-    for (const Ent& x : ents)
-      boxes.push_back({x.e, ((x.i - imin) + (x.j - jmin) * bw) | (x.sel << 16)});
-    for (int l0 = 0; l0 < L; l0 += nl) {
-      Item it = proto;
-      it.mode = MODE_TILE;
-      it.u0 = q0;
-      it.nunits = nq;
-      it.vol = make_div((uint32_t)nq);
-      it.l0 = l0;
-      it.nl = std::min(nl, L - l0);
-      it.bw = bw;
-      it.bh = bh;
-      it.bs0 = (int32_t)S.stride[0];
-      it.bs1 = (int32_t)S.stride[1];
-      it.bsrc = sl[0];
-      it.bsrc2 = sl[1];
-      it.bwid = make_div((uint32_t)bw);
-      it.borg = (int32_t)org;
-      it.src_ls = (int32_t)(S.nlevels > 1 ? S.level_stride : 0);
-      it.src_slot = -1;  // no common-slot lookup: the tile reads its slots itself
-      tiles.push_back(it);
-    }
+    if (!smaller) break;
   }
-  for (const auto& b : boxes) P->csr_box[b.first] = b.second;
-  out.insert(out.end(), tiles.begin(), tiles.end());
+  if (!staged) return false;
+  for (const auto& b : boxes) P->adj_box[b.first] = b.second;
+  out.insert(out.end(), items.begin(), items.end());
   return true;
 }
 
 void build_items(bc_plan* P) {
   P->runs.clear();
+  P->adj_box.assign(P->aent_off.size(), 0);
   P->itp_box.assign(P->itp_idx.size(), 0);
   P->csr_box.assign(P->csr_off.size(), 0);
   // units per warp item: single-level values (flat) or 8-level chunks
@@ -1385,7 +1472,11 @@ void build_items(bc_plan* P) {
       const bc_block& G = P->blocks[P->slot_block[common]];
       it.src_ls = (int32_t)(G.nlevels > 1 ? G.level_stride : 0);
     }
-    table_emit(P->adj_items, it, B0, r1 - r0);
+    // levels far apart in memory: stage each tile's box of ghost cotangents
+    const int mode = table_mode(B0, P->opts.unit_order, level_chunk(P, false));
+    if (mode < 2 || P->opts.unstaged_rows ||
+        !emit_adj_tiles(P, r0, r1 - r0, it, mode, B0.nlevels, P->adj_items))
+      table_emit(P->adj_items, it, B0, r1 - r0);
     r0 = r1;
   }
   P->adj_items.insert(P->adj_items.begin(), P->adj_add.begin(), P->adj_add.end());
@@ -1472,6 +1563,47 @@ void split_unit_copies(bc_plan* P) {
   P->adj_ptr.swap(ptr);
 }
 
+// Within each data slot, the transpose rows read by one ghost slot (the
+// slot of their first entry) are made consecutive, in data-offset order:
+// consecutive rows then gather from one neighbour strip, so tiles of them
+// can stage that strip (and more items find one common ghost slot).  Each
+// data value keeps its one row and its entries' ghost order.
+void group_rows_by_reader(bc_plan* P) {
+  const size_t nr = P->arow_slot.size();
+  std::vector<size_t> order(nr);
+  std::iota(order.begin(), order.end(), size_t(0));
+  auto reader = [&](size_t r) {
+    return P->adj_ptr[r + 1] > P->adj_ptr[r] ? P->aent_slot[(size_t)P->adj_ptr[r]] : -1;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    if (P->arow_slot[a] != P->arow_slot[b]) return P->arow_slot[a] < P->arow_slot[b];
+    return reader(a) < reader(b);
+  });
+  std::vector<int32_t> rs(nr), ro(nr), es, eo;
+  std::vector<int64_t> ptr{0};
+  std::vector<double> ew;
+  es.reserve(P->aent_slot.size());
+  eo.reserve(P->aent_off.size());
+  ew.reserve(P->aent_w.size());
+  for (size_t t = 0; t < nr; ++t) {
+    const size_t r = order[t];
+    rs[t] = P->arow_slot[r];
+    ro[t] = P->arow_off[r];
+    for (int64_t e = P->adj_ptr[r]; e < P->adj_ptr[r + 1]; ++e) {
+      es.push_back(P->aent_slot[(size_t)e]);
+      eo.push_back(P->aent_off[(size_t)e]);
+      ew.push_back(P->aent_w[(size_t)e]);
+    }
+    ptr.push_back((int64_t)ew.size());
+  }
+  P->arow_slot.swap(rs);
+  P->arow_off.swap(ro);
+  P->aent_slot.swap(es);
+  P->aent_off.swap(eo);
+  P->aent_w.swap(ew);
+  P->adj_ptr.swap(ptr);
+}
+
 void build_transpose(bc_plan* P) {
   const ExplicitRows& R = P->rows;
   struct E {
@@ -1513,6 +1645,7 @@ void build_transpose(bc_plan* P) {
   P->adj_nnz_total = (int64_t)P->aent_w.size();
   P->has_adjoint = true;
   if (!P->opts.no_runs) split_unit_copies(P);
+  group_rows_by_reader(P);
 }
 
 // -- device upload -------------------------------------------------------------
@@ -1674,11 +1807,13 @@ bc_status upload_work(bc_plan* P) {
   const size_t o_all = L.take(P->all_items.size() * sizeof(Item));
   const size_t o_box = L.take(P->itp_box.size() * 4);
   const size_t o_cbox = L.take(P->csr_box.size() * 4);
+  const size_t o_abox = L.take(P->adj_box.size() * 4);
   std::vector<char> host(L.off + 256, 0);
   put_raw(host, o_i, P->items);
   put_raw(host, o_all, P->all_items);
   put_raw(host, o_box, P->itp_box);
   put_raw(host, o_cbox, P->csr_box);
+  put_raw(host, o_abox, P->adj_box);
   for (int f = 0; f < kFamilies; ++f) put_raw(host, o_f[f], P->fam_items[f]);
   put_raw(host, o_r, P->runs);
   put_raw(host, o_a, P->adj_items);
@@ -1700,6 +1835,7 @@ bc_status upload_work(bc_plan* P) {
   P->d_all = reinterpret_cast<Item*>(b + o_all);
   P->ctx.itp_box = reinterpret_cast<const int32_t*>(b + o_box);
   P->ctx.csr_box = reinterpret_cast<const int32_t*>(b + o_cbox);
+  P->ctx.adj_box = reinterpret_cast<const int32_t*>(b + o_abox);
   return BC_OK;
 }
 
@@ -2658,13 +2794,22 @@ int64_t check_adjoint_lists(WorkCheck& W, const std::vector<Item>& adj_items) {
       ++hits[d];
       int64_t prev = INT64_MIN;
       for (int64_t e = P->adj_ptr[tr]; e < P->adj_ptr[tr + 1]; ++e) {
-        const int gs = P->aent_slot[(size_t)e];
-        const int64_t order = col_key(gs, P->aent_off[(size_t)e]);
+        int gs = P->aent_slot[(size_t)e];
+        int64_t go = P->aent_off[(size_t)e];
+        if (it.mode == MODE_TILE) {
+          // a staged row reads its ghost value from the tile's box
+          const int32_t bx = P->adj_box[(size_t)e];
+          const int idx = bx & 0xffff;
+          gs = (bx >> 16) ? it.bsrc2 : it.bsrc;
+          go = it.borg + (int64_t)(idx % it.bw) * it.bs0 + (int64_t)(idx / it.bw) * it.bs1;
+          if (idx >= it.bw * it.bh || gs < 0)
+            W.problem("a staged transpose entry lies outside its box", it.dst_slot, P->arow_off[tr]);
+        }
+        const int64_t order = col_key(gs, go);
         if (order < prev)
           W.problem("transpose entries out of ghost order", it.dst_slot, P->arow_off[tr]);
         prev = order;
-        got[d].push_back({col_key(gs, (int64_t)P->aent_off[(size_t)e] + l * W.ls_of_slot(gs)),
-                          P->aent_w[(size_t)e]});
+        got[d].push_back({col_key(gs, go + l * W.ls_of_slot(gs)), P->aent_w[(size_t)e]});
       }
     });
   }
@@ -3058,7 +3203,8 @@ namespace {
 // Autotune results of this process, and of BC_AUTOTUNE_CACHE's file: the
 // tuned options by "<plan hash>:<device name>:<SMs>".
 struct TunedOpts {
-  int32_t batch_mode, scalar_runs, units_per_lane, threads, level_chunk, ctas_per_sm;
+  int32_t batch_mode, scalar_runs, units_per_lane, threads, level_chunk, ctas_per_sm,
+      unstaged_rows;
 };
 std::mutex g_tune_mu;
 std::map<std::string, TunedOpts> g_tuned;
@@ -3083,10 +3229,12 @@ void set_tuned(bc_plan_opts& o, const TunedOpts& t) {
   o.threads = t.threads;
   o.level_chunk = t.level_chunk;
   o.ctas_per_sm = t.ctas_per_sm;
+  o.unstaged_rows = t.unstaged_rows;
 }
 
 TunedOpts get_tuned(const bc_plan_opts& o) {
-  return {o.batch_mode, o.scalar_runs, o.units_per_lane, o.threads, o.level_chunk, o.ctas_per_sm};
+  return {o.batch_mode,  o.scalar_runs, o.units_per_lane, o.threads,
+          o.level_chunk, o.ctas_per_sm, o.unstaged_rows};
 }
 
 // the cached choice for `key`, from memory or the cache file
@@ -3106,8 +3254,9 @@ bool cached_choice(const std::string& key, TunedOpts& out) {
   while (std::fgets(line, sizeof(line), f)) {
     char k[320];
     TunedOpts t{};
-    if (std::sscanf(line, "%319s %d %d %d %d %d %d", k, &t.batch_mode, &t.scalar_runs,
-                    &t.units_per_lane, &t.threads, &t.level_chunk, &t.ctas_per_sm) == 7 &&
+    if (std::sscanf(line, "%319s %d %d %d %d %d %d %d", k, &t.batch_mode, &t.scalar_runs,
+                    &t.units_per_lane, &t.threads, &t.level_chunk, &t.ctas_per_sm,
+                    &t.unstaged_rows) == 8 &&
         key == k) {
       out = t;
       found = true;  // the last line for a key wins
@@ -3124,8 +3273,8 @@ void store_choice(const std::string& key, const TunedOpts& t, float ms) {
   const char* path = std::getenv("BC_AUTOTUNE_CACHE");
   if (!path || !*path) return;
   if (FILE* f = std::fopen(path, "a")) {
-    std::fprintf(f, "%s %d %d %d %d %d %d %.6f\n", key.c_str(), t.batch_mode, t.scalar_runs,
-                 t.units_per_lane, t.threads, t.level_chunk, t.ctas_per_sm, ms);
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %.6f\n", key.c_str(), t.batch_mode, t.scalar_runs,
+                 t.units_per_lane, t.threads, t.level_chunk, t.ctas_per_sm, t.unstaged_rows, ms);
     std::fclose(f);
   }
 }
@@ -3190,10 +3339,11 @@ bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) 
     med = ts[ts.size() / 2];
     return BC_OK;
   };
-  bool chunked = false, runs = false;
+  bool chunked = false, runs = false, staged = false;
   for (const Item& it : plan->items) {
     chunked |= it.mode >= 2 || (it.mode == MODE_FLAT_CELL && it.lev.d > 1);
     runs |= it.mode == MODE_RUNS;
+    staged |= it.mode == MODE_TILE;
   }
   // one option at a time, from the plan's own options
   struct Knob {
@@ -3207,6 +3357,7 @@ bc_status bc_plan_autotune(bc_plan* plan, void* const* slot_ptrs, void* stream) 
   knobs.push_back({&bc_plan_opts::units_per_lane, {1, 2, 4, 8}});
   knobs.push_back({&bc_plan_opts::threads, {64, 128, 256}});
   if (chunked) knobs.push_back({&bc_plan_opts::level_chunk, {1, 2, 4, 8}});
+  if (staged) knobs.push_back({&bc_plan_opts::unstaged_rows, {0, 1}});
   knobs.push_back({&bc_plan_opts::ctas_per_sm, {0, 1, 2}});
   float best_ms = 0;
   bc_status st = time_candidate(best_ms);
