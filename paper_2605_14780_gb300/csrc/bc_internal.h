@@ -65,7 +65,13 @@ enum ItemMode : int32_t { MODE_TILE = -2, MODE_RUNS = -1, MODE_FLAT_CELL = 0, MO
 constexpr int32_t kBoxIndex = 0xffff;
 constexpr int32_t kBoxRows = 1 << 16;
 constexpr int32_t kBoxSnap = 1 << 17;
-constexpr int kStageBytes = 2048;  // shared memory of one warp's staged box
+// shared memory of one warp's staged box: interpolation and transpose
+// tiles 2 KB, CSR tiles 4 KB (measured: the 4 x 4 reconstruction rows of a
+// vector pair then stage 16-row tiles of 6 levels instead of 8-row tiles
+// of 5, 135 -> 87 us on the 6 x 384^2 sphere; the interpolation tiles are
+// 3 % faster with 2 KB)
+constexpr int kStageBytesRows = 2048;
+constexpr int kStageBytesCsr = 4096;
 constexpr int kTileCells = 32;     // cells (rows) of one staged item, at most
 constexpr int kTileLevels = 4;     // levels one lane of a staged CSR or transpose tile sums
 

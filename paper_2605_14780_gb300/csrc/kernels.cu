@@ -67,7 +67,7 @@ struct Ptrs {
   void* d;
   void* d2;
   const void* s;
-  void* stage;  // this warp's shared-memory staging area (kStageBytes), or null
+  void* stage;  // this warp's shared-memory staging area (Stage::kPerWarp), or null
 };
 
 // ---------------------------------------------------------------------------
@@ -537,43 +537,70 @@ __device__ void interp_tile(const Item& it, const Ptrs& P, const Ctx& c, int lan
   }
   cp_async_wait_all();
   __syncwarp();
-  const int nq = it.nunits, tot = nq * it.nl;
+  // lanes take (cell, group of kTileLevels levels) units, cells fastest:
+  // a cell's weights, box word and rotation load once for its group
+  const int nq = it.nunits, tot = nq * ((it.nl + kTileLevels - 1) / kTileLevels);
   const int p = it.p;
+  const int lstep = nc * A;  // stage values per level
   B* du = static_cast<B*>(P.d);
   B* dv = static_cast<B*>(P.d2);
   for (int u = lane; u < tot; u += 32) {
-    const int l = (int)fdiv((uint32_t)u, it.vol), q = u - l * nq;
+    const int g = (int)fdiv((uint32_t)u, it.vol), q = u - g * nq;
+    const int lb = g * kTileLevels;
     const int row = it.table + it.u0 + q;
     const int bx = __ldg(c.itp_box + row);
     const int st = (bx & kBoxRows) ? it.bw : 1;
     const bool snap = bx & kBoxSnap;
-    const int64_t off = (int64_t)dst_cell(it, c, it.u0 + q) + (int64_t)(it.l0 + l) * it.dst_ls;
-    const T* su = sm + (pair ? 2 * l : l) * A + (bx & kBoxIndex);
+    const int64_t off = (int64_t)dst_cell(it, c, it.u0 + q) + (int64_t)(it.l0 + lb) * it.dst_ls;
+    const int64_t ls = it.dst_ls;
+    const T* su = sm + lb * lstep + (bx & kBoxIndex);
     const T* wr = static_cast<const T*>(c.itp_w) + row * kPMax;
     if (!pair) {
       if (snap) {  // unit row: exact copy of node 0
-        du[off] = reinterpret_cast<const B*>(su)[0];
+#pragma unroll
+        for (int l = 0; l < kTileLevels; ++l)
+          if (lb + l < it.nl) du[off + l * ls] = reinterpret_cast<const B*>(su)[l * lstep];
         continue;
       }
-      T acc = T(0);
+      T acc[kTileLevels];
+#pragma unroll
+      for (int l = 0; l < kTileLevels; ++l) acc[l] = T(0);
 #pragma unroll
       for (int n = 0; n < kPMax; ++n)
-        if (n < p) acc = fma(ldg(wr + n), su[n * st], acc);
-      du[off] = to_bits(acc);
+        if (n < p) {
+          const T w = ldg(wr + n);
+#pragma unroll
+          for (int l = 0; l < kTileLevels; ++l)
+            if (lb + l < it.nl) acc[l] = fma(w, su[l * lstep + n * st], acc[l]);
+        }
+#pragma unroll
+      for (int l = 0; l < kTileLevels; ++l)
+        if (lb + l < it.nl) du[off + l * ls] = to_bits(acc[l]);
     } else {
       const T* sv = su + A;
       const int pe = snap ? 1 : p;
-      T au = T(0), av = T(0);
+      T au[kTileLevels], av[kTileLevels];
+#pragma unroll
+      for (int l = 0; l < kTileLevels; ++l) au[l] = av[l] = T(0);
 #pragma unroll
       for (int n = 0; n < kPMax; ++n)
         if (n < pe) {
           const T w = snap ? T(1) : ldg(wr + n);
-          au = fma(w, su[n * st], au);
-          av = fma(w, sv[n * st], av);
+#pragma unroll
+          for (int l = 0; l < kTileLevels; ++l)
+            if (lb + l < it.nl) {
+              au[l] = fma(w, su[l * lstep + n * st], au[l]);
+              av[l] = fma(w, sv[l * lstep + n * st], av[l]);
+            }
         }
       const T* mr = static_cast<const T*>(c.itp_m) + row * 4;
-      du[off] = to_bits(fma(ldg(mr), au, ldg(mr + 1) * av));
-      dv[off] = to_bits(fma(ldg(mr + 2), au, ldg(mr + 3) * av));
+      const T m00 = ldg(mr), m01 = ldg(mr + 1), m10 = ldg(mr + 2), m11 = ldg(mr + 3);
+#pragma unroll
+      for (int l = 0; l < kTileLevels; ++l)
+        if (lb + l < it.nl) {
+          du[off + l * ls] = to_bits(fma(m00, au[l], m01 * av[l]));
+          dv[off + l * ls] = to_bits(fma(m10, au[l], m11 * av[l]));
+        }
     }
   }
   __syncwarp();  // every lane is done with the stage before the next item
@@ -608,7 +635,34 @@ __device__ __forceinline__ void stage_box(const Item& it, const Ctx& c, T* sm, i
   __syncwarp();
 }
 
+// four consecutive words / values from a 16-byte boundary
+__device__ __forceinline__ void ld_words4(const int32_t* p, int* w) {
+  const int4 v = __ldg(reinterpret_cast<const int4*>(p));
+  w[0] = v.x;
+  w[1] = v.y;
+  w[2] = v.z;
+  w[3] = v.w;
+}
+
 template <typename T>
+__device__ __forceinline__ void ld_vals4(const T* p, T* a) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    a[0] = v.x;
+    a[1] = v.y;
+    a[2] = v.z;
+    a[3] = v.w;
+  } else {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 u = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    a[0] = v.x;
+    a[1] = v.y;
+    a[2] = u.x;
+    a[3] = u.y;
+  }
+}
+
+template <typename T, int W>
 __device__ void csr_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) {
   T* sm = static_cast<T*>(P.stage);
   stage_box<T>(it, c, sm, lane);
@@ -627,13 +681,29 @@ __device__ void csr_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) 
     T acc[kTileLevels];
 #pragma unroll
     for (int l = 0; l < kTileLevels; ++l) acc[l] = T(0);
-    for (int e = 0; e < nnz; ++e) {
-      const int bx = __ldg(c.csr_box + e0 + e);
-      const T w = ldg(val + e0 + e);
-      const T* se = s + (bx >> 16) * A + (bx & 0xffff);
+    // the row's entries W (4, or 8 when the row width is a multiple of 8)
+    // at a time (rows start on 16-byte boundaries): box words and weights
+    // load as vectors, so a row costs one memory latency per W entries;
+    // padding entries (box 0, weight 0) read a staged value and are dropped
+    for (int e = 0; e < nnz; e += W) {
+      int bx[W];
+      T w[W];
 #pragma unroll
-      for (int l = 0; l < kTileLevels; ++l)
-        if (lb + l < it.nl) acc[l] = fma(w, se[l * lstep], acc[l]);
+      for (int h = 0; h < W; h += 4) {
+        ld_words4(c.csr_box + e0 + e + h, bx + h);
+        ld_vals4<T>(val + e0 + e + h, w + h);
+      }
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        const T* se = s + (bx[j] >> 16) * A + (bx[j] & 0xffff);
+        const bool live = e + j < nnz;
+#pragma unroll
+        for (int l = 0; l < kTileLevels; ++l)
+          if (lb + l < it.nl) {
+            const T xv = se[l * lstep];
+            acc[l] = live ? fma(w[j], xv, acc[l]) : acc[l];
+          }
+      }
     }
     const T b = ldg(static_cast<const T*>(c.csr_rhs) + row);
     T* dd = d + (int64_t)dst_cell(it, c, it.u0 + q) + (int64_t)(it.l0 + lb) * it.dst_ls;
@@ -671,13 +741,24 @@ __device__ void adj_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) 
 #pragma unroll
     for (int l = 0; l < kTileLevels; ++l)
       acc[l] = lb + l < it.nl ? xb[(int64_t)l * it.dst_ls] : T(0);
-    for (int e = e0; e < e1; ++e) {
-      const int bx = __ldg(c.adj_box + e);
-      const T w = ldg(wv + e);
-      const T* se = s + (bx >> 16) * A + (bx & 0xffff);
+    // entries four at a time, their loads issued together
+    for (int e = e0; e < e1; e += 4) {
+      int bx[4];
+      T w[4];
 #pragma unroll
-      for (int l = 0; l < kTileLevels; ++l)
-        if (lb + l < it.nl) acc[l] = fma(w, se[l * lstep], acc[l]);
+      for (int j = 0; j < 4; ++j) {
+        const bool live = e + j < e1;
+        bx[j] = live ? __ldg(c.adj_box + e + j) : 0;
+        w[j] = live ? ldg(wv + e + j) : T(0);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (e + j < e1) {
+          const T* se = s + (bx[j] >> 16) * A + (bx[j] & 0xffff);
+#pragma unroll
+          for (int l = 0; l < kTileLevels; ++l)
+            if (lb + l < it.nl) acc[l] = fma(w[j], se[l * lstep], acc[l]);
+        }
     }
 #pragma unroll
     for (int l = 0; l < kTileLevels; ++l)
@@ -1123,7 +1204,10 @@ __device__ __forceinline__ void run_item(const Item& it, const Ptrs& P, const Ct
     }
   } else if constexpr (FAM == FAM_CSR) {
     if (it.mode == MODE_TILE) {
-      csr_tile<T>(it, P, c, lane);
+      if (it.p % 8 == 0)
+        csr_tile<T, 8>(it, P, c, lane);
+      else
+        csr_tile<T, 4>(it, P, c, lane);
     } else if (it.p == 8) {
       if (flat)
         csr_flat_w<T, 8, false>(it, P, c, lane);
@@ -1232,12 +1316,15 @@ __device__ __forceinline__ Ptrs gather_ptrs(void* mine) {
   return P;
 }
 
-// Shared memory for staged boxes: one kStageBytes area per warp in the
-// kernels that run interpolation, CSR or transpose-gather items.
+// Shared memory for staged boxes: one area per warp in the kernels that
+// run interpolation, CSR or transpose-gather items (the CSR tiles' larger
+// area in the kernels that run CSR items).
 template <int FAM, int THREADS>
 struct Stage {
   static constexpr int kWarps = FAM != FAM_STRUCT ? THREADS / 32 : 0;
-  static constexpr int kBytes = kWarps > 0 ? kWarps * kStageBytes : 16;
+  static constexpr int kPerWarp =
+      (FAM == FAM_CSR || FAM == FAM_ALL) ? kStageBytesCsr : kStageBytesRows;
+  static constexpr int kBytes = kWarps > 0 ? kWarps * kPerWarp : 16;
 };
 
 // Plain grid: warp w of CTA b processes item b * warps + w.
@@ -1252,7 +1339,7 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
   const int w = __ldg(reinterpret_cast<const int*>(items + idx) + lane);
   reinterpret_cast<int*>(&sit[warp])[lane] = w;
   Ptrs P = gather_ptrs(lookup_slot(c, w, lane));
-  if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * kStageBytes;
+  if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * Stage<FAM, THREADS>::kPerWarp;
   __syncwarp();
   run_work<T, FAM>(sit[warp], P, c, lane);
 }
@@ -1281,7 +1368,7 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     const int nxt2 = nxt + stride;
     const int w_nxt2 = nxt2 < nitems ? __ldg(iw + (int64_t)nxt2 * 32 + lane) : 0;
     Ptrs P = gather_ptrs(p_cur);
-    if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * kStageBytes;
+    if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * Stage<FAM, THREADS>::kPerWarp;
     __syncwarp();
     run_work<T, FAM>(sit[warp], P, c, lane);
     __syncwarp();
@@ -1352,7 +1439,7 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     const unsigned raw = issue();  // claim of the fourth item, in flight
     reinterpret_cast<int*>(&sit[warp])[lane] = wa;
     Ptrs P = gather_ptrs(pa);
-    if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * kStageBytes;
+    if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * Stage<FAM, THREADS>::kPerWarp;
     __syncwarp();
     run_work<T, FAM>(sit[warp], P, c, lane);
     __syncwarp();

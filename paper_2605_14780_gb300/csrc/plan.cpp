@@ -987,7 +987,7 @@ bool emit_tiles(bc_plan* P, const Sub& s, const Item& proto, int chunk, int nc,
                 std::vector<Item>& out) {
   const bc_block& B = P->blocks[s.block];
   const int L = B.nlevels;
-  const int cap = kStageBytes / P->esize;
+  const int cap = kStageBytesRows / P->esize;
   std::vector<Item> tiles;
   std::vector<std::pair<int, int32_t>> boxes;  // (row, itp_box) to write on success
   for (int q0 = 0; q0 < s.vol; q0 += kTileCells) {
@@ -1090,19 +1090,25 @@ struct TileBox {
   }
 };
 
+// Staging pays only when a tile's entries read each staged value at least
+// this often on average (a box mostly of values no row reads costs more
+// loads than it saves).
+constexpr int kMinTileReuse = 1;
+
 // Items of one staged tile of nq rows from q0 (levels in chunks of `chunk`,
 // L levels): 1 when the box holds at least `need` levels of its slots in a
 // warp's staging area (items and box words appended), 0 when the box is
-// too large for that, -1 when the rows cannot be staged.
+// too large for that, -1 when the rows cannot (or should not) be staged.
 int finish_tile(const bc_plan* P, const TileBox& T, int q0, int nq, const Item& proto, int chunk,
-                int L, int need, std::vector<Item>& tiles,
+                int L, int need, int stage_bytes, std::vector<Item>& tiles,
                 std::vector<std::pair<size_t, int32_t>>& boxes) {
   if (T.blk < 0) return -1;
   const bc_block& S = P->blocks[T.blk];
   if (S.nlevels != L) return -1;
-  const int cap = kStageBytes / P->esize;
+  const int cap = stage_bytes / P->esize;
   const int bw = T.imax - T.imin + 1, bh = T.jmax - T.jmin + 1;
   if ((int64_t)bw * bh > kBoxIndex) return 0;
+  if ((int64_t)T.ents.size() < (int64_t)kMinTileReuse * bw * bh * T.nsel) return -1;
   const int64_t fit = cap / ((int64_t)bw * bh * T.nsel);
   if (fit < need) return 0;
   const int nl = (int)std::min<int64_t>(chunk, fit);
@@ -1164,7 +1170,7 @@ bool emit_csr_tiles(bc_plan* P, const Sub& s, int ci, const Item& proto, int chu
         for (int k = 0; k < P->csr_nnz[row]; ++k)
           if (!T.add(P, e0 + k, P->csr_slot[e0 + k], P->csr_off[e0 + k])) return false;
       }
-      const int r = finish_tile(P, T, q0, nq, proto, chunk, L, need, tiles, boxes);
+      const int r = finish_tile(P, T, q0, nq, proto, chunk, L, need, kStageBytesCsr, tiles, boxes);
       if (r < 0) return false;
       smaller = r == 0;
     }
@@ -1201,7 +1207,8 @@ bool emit_adj_tiles(bc_plan* P, int r0, int nrows, const Item& proto, int chunk,
         for (int64_t e = P->adj_ptr[r]; e < P->adj_ptr[r + 1] && ok; ++e)
           ok = T.add(P, (size_t)e, P->aent_slot[(size_t)e], P->aent_off[(size_t)e]);
       }
-      const int res = ok ? finish_tile(P, T, q0, nq, proto, chunk, L, need, items, boxes) : -1;
+      const int res =
+          ok ? finish_tile(P, T, q0, nq, proto, chunk, L, need, kStageBytesRows, items, boxes) : -1;
       if (res > 0) {
         ++staged;
         continue;
