@@ -106,6 +106,7 @@ static_assert(sizeof(Item) % 16 == 0, "Item must be a multiple of 16 bytes");
 struct Ctx {
   void* const* slots;       // caller's device array of slot pointers
   int32_t vec_runs;         // 1: runs move 16-byte vectors (runs_vec)
+  int32_t stage_warp;       // bytes of one warp's shared-memory stage in this launch
   const int32_t* slot_ls;   // level stride of every slot (elements)
   // cell tables, one row per cell of every sub-matrix box: the element
   // offset of the ghost cell (level 0) and, for maps, of its source cell
@@ -119,8 +120,8 @@ struct Ctx {
   const void* itp_w;
   const void* itp_m;
   const int32_t* itp_box;   // staged cells: node 0 in the item's box
-  const int32_t* csr_box;   // staged CSR entries: box index | selector << 16
-  const int32_t* adj_box;   // staged transpose entries: box index | selector << 16
+  const int32_t* csr_box;   // staged CSR entries: place in a level's stage (slot-major)
+  const int32_t* adj_box;   // staged transpose entries: the same
   // CSR rows (global row numbering): entry count per row, ELL entries
   // (a row's entries start at item.src_org + q * item.p), per-row constant
   const int32_t* csr_nnz;
@@ -152,11 +153,14 @@ constexpr int FAM_ALL = 4;
 // `threads` per CTA (32..512).  grid <= 0: a plain grid with one warp per
 // item; otherwise `grid` resident CTAs whose warps walk the items with a
 // fixed stride, prefetching the next items' descriptors and slot pointers.
+// stage: bytes of one warp's shared-memory stage that the list's staged
+// tiles (MODE_TILE) need (kStageBytesRows or kStageBytesCsr), 0 when it has
+// none: the launch requests that much dynamic shared memory per warp.
 cudaError_t launch_family(int dtype, int family, const Ctx& ctx,
                           const Item* items, int nitems, int threads, int grid,
-                          cudaStream_t s);
+                          int stage, cudaStream_t s);
 // CTAs of one family kernel that fit on an SM at once.
-int resident_ctas(int dtype, int family, int threads);
+int resident_ctas(int dtype, int family, int threads, int stage);
 // Persistent work-list launch: ctas_per_sm resident CTAs per SM (0: as many
 // as fit) on `sms` SMs, whose warps claim the items through `counter`
 // (kCtrWords words: a done count, then kSpread claim counters kCtrStride
@@ -167,9 +171,9 @@ constexpr unsigned kCtrStride = 64;  // words between counters (own 256-byte lin
 constexpr unsigned kCtrWords = (kSpread + 1) * kCtrStride;
 cudaError_t launch_persistent(int dtype, int family, const Ctx& ctx, const Item* items,
                               int nitems, int threads, int ctas_per_sm, int sms,
-                              unsigned* counter, cudaStream_t s);
+                              unsigned* counter, int stage, cudaStream_t s);
 // CTAs of the persistent kernel of `family` that fit on an SM at once.
-int persistent_fit(int dtype, int family, int threads);
+int persistent_fit(int dtype, int family, int threads, int stage);
 
 // Cubed-sphere geometry (geometry.cu).
 struct CsPanels {

@@ -67,7 +67,7 @@ struct Ptrs {
   void* d;
   void* d2;
   const void* s;
-  void* stage;  // this warp's shared-memory staging area (Stage::kPerWarp), or null
+  void* stage;  // this warp's shared-memory staging area (Ctx::stage_warp bytes), or null
 };
 
 // ---------------------------------------------------------------------------
@@ -612,8 +612,8 @@ __device__ void interp_tile(const Item& it, const Ptrs& P, const Ctx& c, int lan
 // the item's levels and slots to shared memory, then each lane sums one row
 // for a group of up to kTileLevels levels from there, loading each entry's
 // weight and box word once for the group, in entry order (as the per-lane
-// path: from zero, then + b).  Each entry carries its box index and slot
-// selector (csr_box).
+// path: from zero, then + b).  Each entry carries its value's place in one
+// level of the stage (csr_box: slot selector * box cells + box index).
 template <typename T>
 __device__ __forceinline__ void stage_box(const Item& it, const Ctx& c, T* sm, int lane) {
   const int nsel = it.bsrc2 >= 0 ? 2 : 1;
@@ -667,7 +667,6 @@ __device__ void csr_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) 
   T* sm = static_cast<T*>(P.stage);
   stage_box<T>(it, c, sm, lane);
   const int lstep = (it.bsrc2 >= 0 ? 2 : 1) * it.bw * it.bh;  // stage values per level
-  const int A = it.bw * it.bh;
   const int nq = it.nunits, tot = nq * ((it.nl + kTileLevels - 1) / kTileLevels);
   const T* val = static_cast<const T*>(c.csr_val);
   T* d = static_cast<T*>(P.d);
@@ -682,9 +681,10 @@ __device__ void csr_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) 
 #pragma unroll
     for (int l = 0; l < kTileLevels; ++l) acc[l] = T(0);
     // the row's entries W (4, or 8 when the row width is a multiple of 8)
-    // at a time (rows start on 16-byte boundaries): box words and weights
-    // load as vectors, so a row costs one memory latency per W entries;
-    // padding entries (box 0, weight 0) read a staged value and are dropped
+    // at a time (rows start on 16-byte boundaries): the entries' stage
+    // places (csr_box) and weights load as vectors, so a row costs one
+    // memory latency per W entries; in the last, partial block the padding
+    // entries (place 0, weight 0) read a staged value and are dropped
     for (int e = 0; e < nnz; e += W) {
       int bx[W];
       T w[W];
@@ -693,16 +693,23 @@ __device__ void csr_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) 
         ld_words4(c.csr_box + e0 + e + h, bx + h);
         ld_vals4<T>(val + e0 + e + h, w + h);
       }
+      if (e + W <= nnz) {
 #pragma unroll
-      for (int j = 0; j < W; ++j) {
-        const T* se = s + (bx[j] >> 16) * A + (bx[j] & 0xffff);
-        const bool live = e + j < nnz;
+        for (int j = 0; j < W; ++j)
 #pragma unroll
-        for (int l = 0; l < kTileLevels; ++l)
-          if (lb + l < it.nl) {
-            const T xv = se[l * lstep];
-            acc[l] = live ? fma(w[j], xv, acc[l]) : acc[l];
-          }
+          for (int l = 0; l < kTileLevels; ++l)
+            if (lb + l < it.nl) acc[l] = fma(w[j], s[bx[j] + l * lstep], acc[l]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+          const bool live = e + j < nnz;
+#pragma unroll
+          for (int l = 0; l < kTileLevels; ++l)
+            if (lb + l < it.nl) {
+              const T xv = s[bx[j] + l * lstep];
+              acc[l] = live ? fma(w[j], xv, acc[l]) : acc[l];
+            }
+        }
       }
     }
     const T b = ldg(static_cast<const T*>(c.csr_rhs) + row);
@@ -726,7 +733,6 @@ __device__ void adj_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) 
   T* sm = static_cast<T*>(P.stage);
   stage_box<T>(it, c, sm, lane);
   const int lstep = (it.bsrc2 >= 0 ? 2 : 1) * it.bw * it.bh;
-  const int A = it.bw * it.bh;
   const int nq = it.nunits, tot = nq * ((it.nl + kTileLevels - 1) / kTileLevels);
   const T* wv = static_cast<const T*>(c.aent_w);
   for (int u = lane; u < tot; u += 32) {
@@ -754,10 +760,9 @@ __device__ void adj_tile(const Item& it, const Ptrs& P, const Ctx& c, int lane) 
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         if (e + j < e1) {
-          const T* se = s + (bx[j] >> 16) * A + (bx[j] & 0xffff);
 #pragma unroll
           for (int l = 0; l < kTileLevels; ++l)
-            if (lb + l < it.nl) acc[l] = fma(w[j], se[l * lstep], acc[l]);
+            if (lb + l < it.nl) acc[l] = fma(w[j], s[bx[j] + l * lstep], acc[l]);
         }
     }
 #pragma unroll
@@ -1316,30 +1321,43 @@ __device__ __forceinline__ Ptrs gather_ptrs(void* mine) {
   return P;
 }
 
-// Shared memory for staged boxes: one area per warp in the kernels that
-// run interpolation, CSR or transpose-gather items (the CSR tiles' larger
-// area in the kernels that run CSR items).
+// Shared memory for staged boxes: one area per warp (Ctx::stage_warp bytes:
+// 2 KB for interpolation and transpose tiles, 4 KB when the list has CSR
+// tiles) in the kernels that run interpolation, CSR or transpose-gather
+// items, as dynamic shared memory that only launches of lists with staged
+// tiles request: a kernel that reserves no shared memory keeps the SM's
+// default split of L1 and shared memory and shares SMs with the structured
+// kernel beside it (the 512-block step, levels innermost: 51.1 us with a
+// stage reserved in the CSR kernel, 44.9 us without).
 template <int FAM, int THREADS>
 struct Stage {
   static constexpr int kWarps = FAM != FAM_STRUCT ? THREADS / 32 : 0;
-  static constexpr int kPerWarp =
-      (FAM == FAM_CSR || FAM == FAM_ALL) ? kStageBytesCsr : kStageBytesRows;
-  static constexpr int kBytes = kWarps > 0 ? kWarps * kPerWarp : 16;
 };
+
+// dynamic shared memory of a launch with `stage` bytes per warp (the
+// kernel's limit raised first where that exceeds 48 KB: 512 threads with
+// CSR tiles)
+template <int FAM, int THREADS, typename K>
+int stage_smem(K kernel, int stage) {
+  const int bytes = Stage<FAM, THREADS>::kWarps * stage;
+  if (bytes > 48 * 1024)
+    (void)cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return bytes;
+}
 
 // Plain grid: warp w of CTA b processes item b * warps + w.
 template <typename T, int THREADS, int FAM>
 __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     k_items(Ctx c, const Item* __restrict__ items, int nitems) {
   __shared__ Item sit[THREADS / 32];
-  __shared__ __align__(16) unsigned char stage[Stage<FAM, THREADS>::kBytes];
+  extern __shared__ __align__(16) unsigned char stage[];  // Stage, when requested
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int idx = blockIdx.x * (THREADS / 32) + warp;
   if (idx >= nitems) return;
   const int w = __ldg(reinterpret_cast<const int*>(items + idx) + lane);
   reinterpret_cast<int*>(&sit[warp])[lane] = w;
   Ptrs P = gather_ptrs(lookup_slot(c, w, lane));
-  if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * Stage<FAM, THREADS>::kPerWarp;
+  if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * c.stage_warp;
   __syncwarp();
   run_work<T, FAM>(sit[warp], P, c, lane);
 }
@@ -1352,7 +1370,7 @@ template <typename T, int THREADS, int FAM>
 __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     k_stream(Ctx c, const Item* __restrict__ items, int nitems) {
   __shared__ Item sit[THREADS / 32];
-  __shared__ __align__(16) unsigned char stage[Stage<FAM, THREADS>::kBytes];
+  extern __shared__ __align__(16) unsigned char stage[];  // Stage, when requested
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int stride = gridDim.x * (THREADS / 32);
   const int* iw = reinterpret_cast<const int*>(items);
@@ -1368,7 +1386,7 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     const int nxt2 = nxt + stride;
     const int w_nxt2 = nxt2 < nitems ? __ldg(iw + (int64_t)nxt2 * 32 + lane) : 0;
     Ptrs P = gather_ptrs(p_cur);
-    if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * Stage<FAM, THREADS>::kPerWarp;
+    if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * c.stage_warp;
     __syncwarp();
     run_work<T, FAM>(sit[warp], P, c, lane);
     __syncwarp();
@@ -1400,7 +1418,7 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
   constexpr unsigned FULL = 0xffffffffu;
   constexpr unsigned S = kSpread;
   __shared__ Item sit[THREADS / 32];
-  __shared__ __align__(16) unsigned char stage[Stage<FAM, THREADS>::kBytes];
+  extern __shared__ __align__(16) unsigned char stage[];  // Stage, when requested
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int* iw = reinterpret_cast<const int*>(items);
   const unsigned n = (unsigned)nitems;
@@ -1439,7 +1457,7 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
     const unsigned raw = issue();  // claim of the fourth item, in flight
     reinterpret_cast<int*>(&sit[warp])[lane] = wa;
     Ptrs P = gather_ptrs(pa);
-    if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * Stage<FAM, THREADS>::kPerWarp;
+    if (Stage<FAM, THREADS>::kWarps) P.stage = stage + warp * c.stage_warp;
     __syncwarp();
     run_work<T, FAM>(sit[warp], P, c, lane);
     __syncwarp();
@@ -1466,136 +1484,138 @@ __global__ void __launch_bounds__(THREADS, (Occ<FAM, THREADS>::kMinBlocks))
 }
 
 template <typename T, int THREADS, int FAM>
-cudaError_t launch_t(const Ctx& c, const Item* items, int nitems, int grid,
+cudaError_t launch_t(const Ctx& c, const Item* items, int nitems, int grid, int stage,
                      cudaStream_t s) {
   const int wpb = THREADS / 32;
   const int need = (nitems + wpb - 1) / wpb;
-  if (grid <= 0)
-    k_items<T, THREADS, FAM><<<need, THREADS, 0, s>>>(c, items, nitems);
-  else
-    k_stream<T, THREADS, FAM><<<grid < need ? grid : need, THREADS, 0, s>>>(c, items, nitems);
+  if (grid <= 0) {
+    const int smem = stage_smem<FAM, THREADS>(k_items<T, THREADS, FAM>, stage);
+    k_items<T, THREADS, FAM><<<need, THREADS, smem, s>>>(c, items, nitems);
+  } else {
+    const int smem = stage_smem<FAM, THREADS>(k_stream<T, THREADS, FAM>, stage);
+    k_stream<T, THREADS, FAM><<<grid < need ? grid : need, THREADS, smem, s>>>(c, items, nitems);
+  }
   return cudaGetLastError();
 }
 
 template <typename T, int THREADS, int FAM>
 cudaError_t persist_t(const Ctx& c, const Item* items, int nitems, int ctas_per_sm, int sms,
-                      unsigned* ctr, cudaStream_t s) {
+                      unsigned* ctr, int stage, cudaStream_t s) {
+  const int smem = stage_smem<FAM, THREADS>(k_persist<T, THREADS, FAM>, stage);
   int fit = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_persist<T, THREADS, FAM>, THREADS,
-                                                    0) != cudaSuccess || fit < 1)
+                                                    smem) != cudaSuccess || fit < 1)
     fit = 1;
   const int per_sm = ctas_per_sm > 0 ? (ctas_per_sm < fit ? ctas_per_sm : fit) : fit;
   const int wpb = THREADS / 32;
   const int need = (nitems + wpb - 1) / wpb;
   const int grid = per_sm * sms < need ? per_sm * sms : need;
-  k_persist<T, THREADS, FAM><<<grid, THREADS, 0, s>>>(c, items, nitems, ctr);
+  k_persist<T, THREADS, FAM><<<grid, THREADS, smem, s>>>(c, items, nitems, ctr);
   return cudaGetLastError();
 }
 
 template <typename T, int FAM>
 cudaError_t persist_fam(const Ctx& c, const Item* items, int nitems, int threads,
-                        int ctas_per_sm, int sms, unsigned* ctr, cudaStream_t s) {
+                        int ctas_per_sm, int sms, unsigned* ctr, int st, cudaStream_t s) {
   switch (threads) {
-    case 64: return persist_t<T, 64, FAM>(c, items, nitems, ctas_per_sm, sms, ctr, s);
-    case 128: return persist_t<T, 128, FAM>(c, items, nitems, ctas_per_sm, sms, ctr, s);
-    case 512: return persist_t<T, 512, FAM>(c, items, nitems, ctas_per_sm, sms, ctr, s);
-    default: return persist_t<T, 256, FAM>(c, items, nitems, ctas_per_sm, sms, ctr, s);
+    case 64: return persist_t<T, 64, FAM>(c, items, nitems, ctas_per_sm, sms, ctr, st, s);
+    case 128: return persist_t<T, 128, FAM>(c, items, nitems, ctas_per_sm, sms, ctr, st, s);
+    case 512: return persist_t<T, 512, FAM>(c, items, nitems, ctas_per_sm, sms, ctr, st, s);
+    default: return persist_t<T, 256, FAM>(c, items, nitems, ctas_per_sm, sms, ctr, st, s);
   }
 }
 
 template <typename T>
 cudaError_t persist_any(int fam, const Ctx& c, const Item* items, int nitems, int threads,
-                        int ctas_per_sm, int sms, unsigned* ctr, cudaStream_t s) {
+                        int ctas_per_sm, int sms, unsigned* ctr, int st, cudaStream_t s) {
   switch (fam) {
     case FAM_STRUCT:
-      return persist_fam<T, FAM_STRUCT>(c, items, nitems, threads, ctas_per_sm, sms, ctr, s);
+      return persist_fam<T, FAM_STRUCT>(c, items, nitems, threads, ctas_per_sm, sms, ctr, st, s);
     case FAM_INTERP:
-      return persist_fam<T, FAM_INTERP>(c, items, nitems, threads, ctas_per_sm, sms, ctr, s);
+      return persist_fam<T, FAM_INTERP>(c, items, nitems, threads, ctas_per_sm, sms, ctr, st, s);
     case FAM_CSR:
-      return persist_fam<T, FAM_CSR>(c, items, nitems, threads, ctas_per_sm, sms, ctr, s);
+      return persist_fam<T, FAM_CSR>(c, items, nitems, threads, ctas_per_sm, sms, ctr, st, s);
     case FAM_ADJ:
-      return persist_fam<T, FAM_ADJ>(c, items, nitems, threads, ctas_per_sm, sms, ctr, s);
+      return persist_fam<T, FAM_ADJ>(c, items, nitems, threads, ctas_per_sm, sms, ctr, st, s);
     default:
-      return persist_fam<T, FAM_ALL>(c, items, nitems, threads, ctas_per_sm, sms, ctr, s);
+      return persist_fam<T, FAM_ALL>(c, items, nitems, threads, ctas_per_sm, sms, ctr, st, s);
   }
 }
 
-template <typename T, int FAM>
-int persist_fit_fam(int threads) {
+// resident CTAs per SM of `kernel` with its stage requested or not
+template <int FAM, int THREADS, typename K>
+int fit_of(K kernel, int stage) {
+  const int smem = stage_smem<FAM, THREADS>(kernel, stage);
   int n = 0;
-  cudaError_t e = cudaErrorInvalidValue;
-  switch (threads) {
-    case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persist<T, 64, FAM>, 64, 0); break;
-    case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persist<T, 128, FAM>, 128, 0); break;
-    case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persist<T, 512, FAM>, 512, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persist<T, 256, FAM>, 256, 0); break;
-  }
-  return e == cudaSuccess && n > 0 ? n : 1;
-}
-
-template <typename T>
-int persist_fit_any(int fam, int threads) {
-  switch (fam) {
-    case FAM_STRUCT: return persist_fit_fam<T, FAM_STRUCT>(threads);
-    case FAM_INTERP: return persist_fit_fam<T, FAM_INTERP>(threads);
-    case FAM_CSR: return persist_fit_fam<T, FAM_CSR>(threads);
-    case FAM_ADJ: return persist_fit_fam<T, FAM_ADJ>(threads);
-    default: return persist_fit_fam<T, FAM_ALL>(threads);
-  }
-}
-
-template <typename T, int THREADS, int FAM>
-int resident_t() {
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream<T, THREADS, FAM>, THREADS, 0) !=
-      cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, THREADS, smem) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
 
 template <typename T, int FAM>
-cudaError_t launch_fam(const Ctx& c, const Item* items, int nitems, int threads,
-                       int grid, cudaStream_t s) {
+int persist_fit_fam(int threads, int st) {
   switch (threads) {
-    case 32: return launch_t<T, 32, FAM>(c, items, nitems, grid, s);
-    case 64: return launch_t<T, 64, FAM>(c, items, nitems, grid, s);
-    case 128: return launch_t<T, 128, FAM>(c, items, nitems, grid, s);
-    case 512: return launch_t<T, 512, FAM>(c, items, nitems, grid, s);
-    default: return launch_t<T, 256, FAM>(c, items, nitems, grid, s);
+    case 64: return fit_of<FAM, 64>(k_persist<T, 64, FAM>, st);
+    case 128: return fit_of<FAM, 128>(k_persist<T, 128, FAM>, st);
+    case 512: return fit_of<FAM, 512>(k_persist<T, 512, FAM>, st);
+    default: return fit_of<FAM, 256>(k_persist<T, 256, FAM>, st);
+  }
+}
+
+template <typename T>
+int persist_fit_any(int fam, int threads, int st) {
+  switch (fam) {
+    case FAM_STRUCT: return persist_fit_fam<T, FAM_STRUCT>(threads, st);
+    case FAM_INTERP: return persist_fit_fam<T, FAM_INTERP>(threads, st);
+    case FAM_CSR: return persist_fit_fam<T, FAM_CSR>(threads, st);
+    case FAM_ADJ: return persist_fit_fam<T, FAM_ADJ>(threads, st);
+    default: return persist_fit_fam<T, FAM_ALL>(threads, st);
   }
 }
 
 template <typename T, int FAM>
-int resident_fam(int threads) {
+cudaError_t launch_fam(const Ctx& c, const Item* items, int nitems, int threads,
+                       int grid, int st, cudaStream_t s) {
   switch (threads) {
-    case 32: return resident_t<T, 32, FAM>();
-    case 64: return resident_t<T, 64, FAM>();
-    case 128: return resident_t<T, 128, FAM>();
-    case 512: return resident_t<T, 512, FAM>();
-    default: return resident_t<T, 256, FAM>();
+    case 32: return launch_t<T, 32, FAM>(c, items, nitems, grid, st, s);
+    case 64: return launch_t<T, 64, FAM>(c, items, nitems, grid, st, s);
+    case 128: return launch_t<T, 128, FAM>(c, items, nitems, grid, st, s);
+    case 512: return launch_t<T, 512, FAM>(c, items, nitems, grid, st, s);
+    default: return launch_t<T, 256, FAM>(c, items, nitems, grid, st, s);
+  }
+}
+
+template <typename T, int FAM>
+int resident_fam(int threads, int st) {
+  switch (threads) {
+    case 32: return fit_of<FAM, 32>(k_stream<T, 32, FAM>, st);
+    case 64: return fit_of<FAM, 64>(k_stream<T, 64, FAM>, st);
+    case 128: return fit_of<FAM, 128>(k_stream<T, 128, FAM>, st);
+    case 512: return fit_of<FAM, 512>(k_stream<T, 512, FAM>, st);
+    default: return fit_of<FAM, 256>(k_stream<T, 256, FAM>, st);
   }
 }
 
 template <typename T>
 cudaError_t launch_any(int fam, const Ctx& c, const Item* items, int nitems,
-                       int threads, int grid, cudaStream_t s) {
+                       int threads, int grid, int st, cudaStream_t s) {
   switch (fam) {
-    case FAM_STRUCT: return launch_fam<T, FAM_STRUCT>(c, items, nitems, threads, grid, s);
-    case FAM_INTERP: return launch_fam<T, FAM_INTERP>(c, items, nitems, threads, grid, s);
-    case FAM_CSR: return launch_fam<T, FAM_CSR>(c, items, nitems, threads, grid, s);
-    case FAM_ALL: return launch_fam<T, FAM_ALL>(c, items, nitems, threads, grid, s);
-    default: return launch_fam<T, FAM_ADJ>(c, items, nitems, threads, grid, s);
+    case FAM_STRUCT: return launch_fam<T, FAM_STRUCT>(c, items, nitems, threads, grid, st, s);
+    case FAM_INTERP: return launch_fam<T, FAM_INTERP>(c, items, nitems, threads, grid, st, s);
+    case FAM_CSR: return launch_fam<T, FAM_CSR>(c, items, nitems, threads, grid, st, s);
+    case FAM_ALL: return launch_fam<T, FAM_ALL>(c, items, nitems, threads, grid, st, s);
+    default: return launch_fam<T, FAM_ADJ>(c, items, nitems, threads, grid, st, s);
   }
 }
 
 template <typename T>
-int resident_any(int fam, int threads) {
+int resident_any(int fam, int threads, int st) {
   switch (fam) {
-    case FAM_STRUCT: return resident_fam<T, FAM_STRUCT>(threads);
-    case FAM_INTERP: return resident_fam<T, FAM_INTERP>(threads);
-    case FAM_CSR: return resident_fam<T, FAM_CSR>(threads);
-    case FAM_ALL: return resident_fam<T, FAM_ALL>(threads);
-    default: return resident_fam<T, FAM_ADJ>(threads);
+    case FAM_STRUCT: return resident_fam<T, FAM_STRUCT>(threads, st);
+    case FAM_INTERP: return resident_fam<T, FAM_INTERP>(threads, st);
+    case FAM_CSR: return resident_fam<T, FAM_CSR>(threads, st);
+    case FAM_ALL: return resident_fam<T, FAM_ALL>(threads, st);
+    default: return resident_fam<T, FAM_ADJ>(threads, st);
   }
 }
 
@@ -1603,29 +1623,34 @@ int resident_any(int fam, int threads) {
 
 cudaError_t launch_family(int dtype, int family, const Ctx& ctx,
                           const Item* items, int nitems, int threads, int grid,
-                          cudaStream_t s) {
+                          int stage, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
-  return dtype == 1 ? launch_any<double>(family, ctx, items, nitems, threads, grid, s)
-                    : launch_any<float>(family, ctx, items, nitems, threads, grid, s);
+  Ctx c = ctx;
+  c.stage_warp = stage;
+  return dtype == 1 ? launch_any<double>(family, c, items, nitems, threads, grid, stage, s)
+                    : launch_any<float>(family, c, items, nitems, threads, grid, stage, s);
 }
 
 cudaError_t launch_persistent(int dtype, int family, const Ctx& ctx, const Item* items,
                               int nitems, int threads, int ctas_per_sm, int sms,
-                              unsigned* counter, cudaStream_t s) {
+                              unsigned* counter, int stage, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
-  return dtype == 1
-             ? persist_any<double>(family, ctx, items, nitems, threads, ctas_per_sm, sms, counter, s)
-             : persist_any<float>(family, ctx, items, nitems, threads, ctas_per_sm, sms, counter, s);
+  Ctx c = ctx;
+  c.stage_warp = stage;
+  return dtype == 1 ? persist_any<double>(family, c, items, nitems, threads, ctas_per_sm, sms,
+                                          counter, stage, s)
+                    : persist_any<float>(family, c, items, nitems, threads, ctas_per_sm, sms,
+                                         counter, stage, s);
 }
 
-int persistent_fit(int dtype, int family, int threads) {
-  return dtype == 1 ? persist_fit_any<double>(family, threads)
-                    : persist_fit_any<float>(family, threads);
+int persistent_fit(int dtype, int family, int threads, int stage) {
+  return dtype == 1 ? persist_fit_any<double>(family, threads, stage)
+                    : persist_fit_any<float>(family, threads, stage);
 }
 
-int resident_ctas(int dtype, int family, int threads) {
-  return dtype == 1 ? resident_any<double>(family, threads)
-                    : resident_any<float>(family, threads);
+int resident_ctas(int dtype, int family, int threads, int stage) {
+  return dtype == 1 ? resident_any<double>(family, threads, stage)
+                    : resident_any<float>(family, threads, stage);
 }
 
 }  // namespace bcg

@@ -149,8 +149,10 @@ struct bc_plan {
   std::vector<int4> itp_idx;
   std::vector<double> itp_w, itp_m;
   std::vector<int32_t> itp_box;  // staged interpolation: node 0 in its tile's box
-  std::vector<int32_t> csr_box;  // staged CSR entries: box index | selector << 16
-  std::vector<int32_t> adj_box;  // staged transpose entries: box index | selector << 16
+  // staged CSR / transpose entries: the value's place in one level of its
+  // tile's stage, selector * (box cells) + box index
+  std::vector<int32_t> csr_box;
+  std::vector<int32_t> adj_box;
   // user CSR rows stored as ELL blocks (one width per sub-matrix)
   std::vector<int32_t> csr_nnz;
   std::vector<int32_t> csr_slot, csr_off;
@@ -193,6 +195,9 @@ struct bc_plan {
   std::vector<Item> items, adj_items, adj_zero, adj_add;
   std::vector<Item> fam_items[kFamilies];  // batched form: per family, sub-matrix order
   std::vector<Item> all_items;  // persistent form: every forward item, longest first
+  // per family (FAM_ADJ: also the adjoint gather) and FAM_ALL: bytes of a
+  // warp's shared-memory stage that the list's staged tiles need (0: none)
+  int staged[kFamilies + 1] = {0, 0, 0, 0, 0};
   std::vector<int> sub_begin, sub_end;
   int type_begin[5] = {0, 0, 0, 0, 0}, type_end[5] = {0, 0, 0, 0, 0};
   // device
@@ -1115,7 +1120,7 @@ int finish_tile(const bc_plan* P, const TileBox& T, int q0, int nq, const Item& 
   const int64_t org = cell_offset(S, T.imin, T.jmin, 0);
   if (org > INT32_MAX) return -1;
   for (const TileBox::Ent& x : T.ents)
-    boxes.push_back({x.e, ((x.i - T.imin) + (x.j - T.jmin) * bw) | (x.sel << 16)});
+    boxes.push_back({x.e, (x.i - T.imin) + (x.j - T.jmin) * bw + x.sel * bw * bh});
   for (int l0 = 0; l0 < L; l0 += nl) {
     Item it = proto;
     it.mode = MODE_TILE;
@@ -1487,6 +1492,16 @@ void build_items(bc_plan* P) {
     r0 = r1;
   }
   P->adj_items.insert(P->adj_items.begin(), P->adj_add.begin(), P->adj_add.end());
+  // the shared-memory stage each launch requests per warp
+  auto stage_of = [](const std::vector<Item>& v) {
+    int b = 0;
+    for (const Item& it : v)
+      if (it.mode == MODE_TILE) b = std::max(b, it.kind == IK_CSR ? kStageBytesCsr : kStageBytesRows);
+    return b;
+  };
+  for (int f = 0; f < kFamilies; ++f) P->staged[f] = stage_of(P->fam_items[f]);
+  P->staged[FAM_ADJ] = std::max(P->staged[FAM_ADJ], stage_of(P->adj_items));
+  P->staged[FAM_ALL] = std::max(stage_of(P->all_items), stage_of(P->items));
 }
 
 // The adjoint of a unit copy is an add: a data value read by exactly one
@@ -2292,7 +2307,7 @@ bc_status plan_create_impl(const bc_grid* grid, const bc_submatrix* subs, int32_
 // what fits), or 0 for a plain grid with one warp per item
 int stream_grid(const bc_plan* P, int fam) {
   if (P->opts.ctas_per_sm <= 0) return 0;
-  const int fit = resident_ctas(P->dtype, fam, P->opts.threads);
+  const int fit = resident_ctas(P->dtype, fam, P->opts.threads, P->staged[fam]);
   return std::min(P->opts.ctas_per_sm, fit) * P->num_sms;
 }
 
@@ -2324,7 +2339,7 @@ void persistent_split(bc_plan* P, int per_sm[kFamilies]) {
     total += bytes[f];
   }
   for (int f = 0; f < kFamilies; ++f) {
-    const int fit = persistent_fit(P->dtype, f, P->opts.threads);
+    const int fit = persistent_fit(P->dtype, f, P->opts.threads, P->staged[f]);
     per_sm[f] = total > 0 ? std::max(1, (int)(fit * bytes[f] / total)) : 1;
   }
 }
@@ -2357,10 +2372,11 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
           (e = cudaEventRecord(P->ev_join[kFamilies - 2], ys)) != cudaSuccess)
         return cuda_fail(e, "Sync rows");
     }
+    const int st = P->staged[FAM_ALL];
     e = single ? launch_family(P->dtype, FAM_ALL, c, P->d_all, (int)P->all_items.size(), T,
-                               stream_grid(P, FAM_ALL), s)
+                               stream_grid(P, FAM_ALL), st, s)
                : launch_persistent(P->dtype, FAM_ALL, c, P->d_all, (int)P->all_items.size(), T,
-                                   P->opts.ctas_per_sm, P->num_sms, ctr, s);
+                                   P->opts.ctas_per_sm, P->num_sms, ctr, st, s);
     if (sync && e == cudaSuccess) e = cudaStreamWaitEvent(s, P->ev_join[kFamilies - 2], 0);
   } else if (form == BC_FORM_BATCHED) {
     // one launch per kernel family, the families side by side
@@ -2385,9 +2401,9 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
       if (t > 0 && (e = cudaStreamWaitEvent(st, P->ev_fork, 0)) != cudaSuccess) break;
       const int f = fams[t];
       e = ctr ? launch_persistent(P->dtype, f, c, P->d_fam[f], (int)P->fam_items[f].size(), T,
-                                  split[f], P->num_sms, ctr + kCtrWords * f, st)
+                                  split[f], P->num_sms, ctr + kCtrWords * f, P->staged[f], st)
               : launch_family(P->dtype, f, c, P->d_fam[f], (int)P->fam_items[f].size(), T,
-                              stream_grid(P, f), st);
+                              stream_grid(P, f), P->staged[f], st);
       if (e == cudaSuccess && t > 0) e = cudaEventRecord(P->ev_join[t - 1], st);
     }
     for (int t = 1; t < nf && e == cudaSuccess; ++t)
@@ -2396,12 +2412,12 @@ bc_status launch_forward(bc_plan* P, void* const* slots, int form, cudaStream_t 
   } else if (form == BC_FORM_TYPEWIDE) {
     for (int k = 0; k < 5 && e == cudaSuccess; ++k)
       e = launch_family(P->dtype, family_of_kind(k), c, P->d_items + P->type_begin[k],
-                        P->type_end[k] - P->type_begin[k], T, 0, s);
+                        P->type_end[k] - P->type_begin[k], T, 0, P->staged[FAM_ALL], s);
   } else if (form == BC_FORM_PER_BC) {
     for (size_t si = 0; si < P->subs.size() && e == cudaSuccess; ++si)
       e = launch_family(P->dtype, family_of_kind(P->subs[si].kind), c,
                         P->d_items + P->sub_begin[si], P->sub_end[si] - P->sub_begin[si], T,
-                        0, s);
+                        0, P->staged[FAM_ALL], s);
   } else {
     return fail(BC_ERR_INVALID_ARG, "unknown form %d", form);
   }
@@ -2695,11 +2711,11 @@ int64_t check_forward_list(WorkCheck& W, const std::vector<Item>& items, bool va
           int64_t off = P->csr_off[e];
           if (it.mode == MODE_TILE) {
             // a staged row reads its column from the tile's box
-            const int32_t bx = P->csr_box[e];
-            const int idx = bx & 0xffff;
-            slot = (bx >> 16) ? it.bsrc2 : it.bsrc;
+            const int32_t bx = P->csr_box[e], A = it.bw * it.bh;
+            const int idx = bx % A;
+            slot = bx / A ? it.bsrc2 : it.bsrc;
             off = it.borg + (int64_t)(idx % it.bw) * it.bs0 + (int64_t)(idx / it.bw) * it.bs1;
-            if (idx >= it.bw * it.bh || slot < 0)
+            if (bx < 0 || bx >= (it.bsrc2 >= 0 ? 2 : 1) * A || slot < 0)
               W.problem("a staged CSR entry lies outside its box", it.dst_slot, E);
           }
           const int64_t ls = it.src_slot >= 0 ? it.src_ls : W.ls_of_slot(slot);
@@ -2805,11 +2821,11 @@ int64_t check_adjoint_lists(WorkCheck& W, const std::vector<Item>& adj_items) {
         int64_t go = P->aent_off[(size_t)e];
         if (it.mode == MODE_TILE) {
           // a staged row reads its ghost value from the tile's box
-          const int32_t bx = P->adj_box[(size_t)e];
-          const int idx = bx & 0xffff;
-          gs = (bx >> 16) ? it.bsrc2 : it.bsrc;
+          const int32_t bx = P->adj_box[(size_t)e], A = it.bw * it.bh;
+          const int idx = bx % A;
+          gs = bx / A ? it.bsrc2 : it.bsrc;
           go = it.borg + (int64_t)(idx % it.bw) * it.bs0 + (int64_t)(idx / it.bw) * it.bs1;
-          if (idx >= it.bw * it.bh || gs < 0)
+          if (bx < 0 || bx >= (it.bsrc2 >= 0 ? 2 : 1) * A || gs < 0)
             W.problem("a staged transpose entry lies outside its box", it.dst_slot, P->arow_off[tr]);
         }
         const int64_t order = col_key(gs, go);
@@ -2981,12 +2997,12 @@ bc_status bc_apply_adjoint(bc_plan* plan, void* const* slot_ptrs, void* stream) 
   // Sync columns, then the zero pass over the ghost values they read
   if (e == cudaSuccess)
     e = launch_family(plan->dtype, FAM_ADJ, c, plan->d_adj, (int)plan->adj_items.size(), T,
-                      stream_grid(plan, FAM_ADJ), s);
+                      stream_grid(plan, FAM_ADJ), plan->staged[FAM_ADJ], s);
   if (e == cudaSuccess)
     e = launch_sync(plan->dtype, SYNC_ADJOINT, plan->sync_ctx, slot_ptrs, c.slot_ls, s);
   if (e == cudaSuccess)
     e = launch_family(plan->dtype, FAM_STRUCT, c, plan->d_adj_zero,
-                      (int)plan->adj_zero.size(), T, stream_grid(plan, FAM_STRUCT), s);
+                      (int)plan->adj_zero.size(), T, stream_grid(plan, FAM_STRUCT), 0, s);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   return BC_OK;
 }

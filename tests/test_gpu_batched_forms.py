@@ -110,6 +110,34 @@ def test_level_chunks(chunk, mode):
     assert np.array_equal(bits(adj), bits(adj0))
 
 
+@pytest.mark.parametrize("threads", [64, 512])
+@pytest.mark.parametrize("mode", [F, FP, S1])
+@pytest.mark.parametrize("vector", [False, True])
+def test_staged_tiles_match_per_lane_rows(threads, mode, vector):
+    """Staged tiles (levels outermost: a warp's box of source values, or of
+    ghost cotangents, copied to shared memory) against the per-lane rows:
+    reconstruction-and-quadrature CSR rows and their transpose, or panel-edge
+    interpolation with rotation; forward and adjoint bit-identical (the same
+    sums in the same order) and the forward against the oracle.  512 threads
+    ask for 64 KB of dynamic shared memory in the CSR kernels."""
+    if vector:
+        w = synth.cubed_sphere(24, 3, 6, 9, ("h", "u", "v"), "f32", seed=41)
+    else:
+        w = synth.cubed_sphere(24, 3, 4, 9, ("h", "u", "v"), "f32", seed=41, quad=2)
+    cot = synth.cotangent_like(w, 42)
+    res = []
+    for unstaged in (0, 1):
+        opts = {"batch_mode": mode, "threads": threads, "unstaged_rows": unstaged}
+        plan, out = _forward(w, opts, 1, "outermost")
+        adj = _adjoint(w, plan, cot, 1, "outermost")
+        res.append((plan.stats()["nitems"], flat(out), flat(adj)))
+    assert res[0][0] != res[1][0]  # the default plan does stage some tiles
+    assert np.array_equal(bits(res[0][1]), bits(res[1][1]))
+    assert np.array_equal(bits(res[0][2]), bits(res[1][2]))
+    _, out = _forward(w, {"batch_mode": mode, "threads": threads}, 1, "outermost")
+    compare(w, out, op=build_operator(w))
+
+
 @pytest.mark.parametrize("mode", [P, FP])
 def test_persistent_launches_on_several_streams(mode):
     """Applies of one persistent plan alternating over three streams (one
