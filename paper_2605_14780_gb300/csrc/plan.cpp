@@ -890,6 +890,13 @@ void emit_units(std::vector<Item>& out, Item proto, int vol, int L, int mode, in
 #ifndef BC_RUN_ITEM
 #define BC_RUN_ITEM 256  // values of a run item per unit of units_per_lane
 #endif
+#ifndef BC_FLAT_UPL_MAX
+// largest units_per_lane of per-value (flat) items: one 8-value step per
+// lane (512-block workload, levels innermost: the structured kernel alone
+// 39.0 -> 30.3 us; items of 1024 values of the 2-cell edge strips of
+// blocks with few levels ran up to 39 us each, the kernel's tail)
+#define BC_FLAT_UPL_MAX 1
+#endif
 #ifndef BC_RUN_MIN_AVG
 #define BC_RUN_MIN_AVG 16  // shortest average run (values) worth a run table
 #endif
@@ -905,7 +912,9 @@ bool build_runs(bc_plan* P, const Sub& s, bool lev_fast, int cap, int& r0, int& 
   const int L = B.nlevels;
   const int64_t dls = L > 1 ? B.level_stride : 0;
   const int64_t sls = map ? (P->blocks[s.src_block].nlevels > 1 ? P->blocks[s.src_block].level_stride : 0) : 0;
-  if (lev_fast && (dls != 1 || (map && sls != 1))) return false;
+  // levels fastest: each cell's levels must be contiguous in the ghost and
+  // in the source (a one-level block has nothing to check)
+  if (lev_fast && L > 1 && (dls != 1 || (map && sls != 1))) return false;
   struct Run {
     int64_t d, s, n;
   };
@@ -1256,7 +1265,7 @@ void build_items(bc_plan* P) {
   const int small = (int)std::min<int64_t>(
       1 << 30, std::max<int64_t>(32, (total_values + want_items - 1) / want_items + 31) / 32 * 32);
   const int per_chunk_item = 32 * upl;
-  const int per_flat_item = std::min(32 * kFlatUnroll * upl, small);
+  const int per_flat_item = std::min(32 * kFlatUnroll * std::min(upl, BC_FLAT_UPL_MAX), small);
   // table-driven kinds (interpolation, CSR, transpose): one unit per lane, so
   // a warp's dependent table -> data chains run side by side, not in series
   const int per_table_item = 32;
