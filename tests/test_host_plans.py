@@ -426,6 +426,28 @@ def test_work_lists_replay_against_rows(name, make, opts, layout):
     assert n > 0 and bad == 0, msg
 
 
+@pytest.mark.parametrize("opts", [{}, {"level_chunk": 4}, {"batch_mode": bc.BC_BATCH_SINGLE},
+                                  {"threads": 512}])
+def test_staged_tiles_replay_against_rows(opts):
+    """Levels outermost, reconstruction-and-quadrature rows on a 6 x 24^2
+    sphere: the plan stages CSR tiles (16-row tiles where 32 rows' boxes are
+    too large) and transpose tiles; every staged entry's box word, replayed
+    on the host, names its row's column, with the per-lane plan as the
+    control (fewer items)."""
+    from paper_2605_14780_gb300 import specs
+    w = synth.cubed_sphere(24, 3, 4, 9, ("h", "u", "v"), "f32", seed=41, quad=2)
+    blocks = [specs.contiguous_block(b) for b in w["blocks"]]
+    stats = []
+    for unstaged in (0, 1):
+        plan = bc.Plan(blocks, specs.submatrices(w), w["dtype"],
+                       dict(HOST, unstaged_rows=unstaged, **opts))
+        n, bad, msg = plan.check_work()
+        assert n > 0 and bad == 0, msg
+        st = plan.stats()
+        stats.append((st["nitems"], st["nitems_adjoint"]))
+    assert stats[0][0] != stats[1][0] and stats[0][1] != stats[1][1]
+
+
 @pytest.mark.parametrize("stencil", [bc.star_stencil(2, 1), bc.box_stencil(2, 2)])
 def test_work_lists_of_pruned_plans(stencil):
     w = synth.batching(nblocks=12, side_lo=2, side_hi=30, lev_lo=1, lev_hi=9, h=2, seed=6,
