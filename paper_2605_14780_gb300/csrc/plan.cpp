@@ -1006,7 +1006,7 @@ bool emit_tiles(bc_plan* P, const Sub& s, const Item& proto, int chunk, int nc,
   std::vector<std::pair<int, int32_t>> boxes;  // (row, itp_box) to write on success
   for (int q0 = 0; q0 < s.vol; q0 += kTileCells) {
     const int nq = std::min(kTileCells, s.vol - q0);
-    int base = -1, axis_of_step = -1;
+    int base = -1;
     int imin = INT_MAX, imax = INT_MIN, jmin = INT_MAX, jmax = INT_MIN;
     struct Node0 {
       int i, j, rows, snap;
@@ -1026,7 +1026,6 @@ bool emit_tiles(bc_plan* P, const Sub& s, const Item& proto, int chunk, int nc,
       if (np == 1 || ix.z == S.stride[0]) ax = 0;
       else if (ix.z == S.stride[1]) ax = 1;
       else return false;
-      (void)axis_of_step;
       const int i1 = ax == 0 ? i + np - 1 : i, j1 = ax == 1 ? j + np - 1 : j;
       imin = std::min(imin, i);
       imax = std::max(imax, i1);
